@@ -1,0 +1,111 @@
+/*
+ * mhd.h -- C ABI of the GB300 constrained-transport MHD step library (libmhd.so).
+ *
+ * The library advances the cell-centred conserved state and the face-centred magnetic field
+ * of one uniform, triply periodic patch by one step of the second-order constrained-transport
+ * (CT) MHD method of "Magnetising the QUOKKA code" (Sec. 2): reconstruction of primitive
+ * states (Sec. 2.2), Riemann fluxes (Sec. 2.2), edge EMFs from a compute scheme and the LD04
+ * average (Sec. 2.3, Eqs. q26, fs18, b25a-*, alpha-edge, ld04), a constant-eta Ohmic EMF with
+ * its Joule energy flux (Sec. 2.4, Eqs. current-stencil, emf-update), the discrete Stokes
+ * update of the face field (Eqs. dbdt:discrete, rk:increment-bfield) and RK2-SSP with
+ * first-order flux correction (Sec. 2.5, Eqs. rk:increment-state, rk1:update, rk2:update).
+ * Every computation runs in FP64 CUDA kernels on the device; nothing falls back to the host.
+ *
+ * Memory layout (all arrays are caller-owned DEVICE memory, float64, x fastest):
+ *   cell X = (i, j, k), 0 <= i < nx, ... ; linear index X = (k*ny + j)*nx + i
+ *   cons : [5][nz][ny][nx]  rho, rho*u0, rho*u1, rho*u2, e_tot        (Eq. state:conserved)
+ *   b0   : [nz][ny][nx]     b0 on the x0-face of cell X at i - 1/2    (Sec. 2.1)
+ *   b1   : [nz][ny][nx]     b1 on the x1-face at j - 1/2
+ *   b2   : [nz][ny][nx]     b2 on the x2-face at k - 1/2
+ * Periodicity means face i = nx is face i = 0.
+ *
+ * Errors: every call returns an mhd_status; no call traps on the device. Argument errors are
+ * detected on the host before any launch. mhd_last_error() gives a message for the last
+ * failure on a context. Calls are asynchronous on the context's stream unless stated.
+ */
+#ifndef MHD_GB300_H
+#define MHD_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MHD_OK = 0,
+  MHD_ERR_ARG = 1,         /* bad argument (null pointer, size, dt <= 0, eta < 0, scheme bits) */
+  MHD_ERR_CUDA = 2,        /* a CUDA runtime call failed; see mhd_last_error */
+  MHD_ERR_NONFINITE = 3,   /* a non-finite value was produced and flux correction was off */
+  MHD_ERR_UNSUPPORTED = 4, /* a scheme the paper names but does not define (B25b, PPM-EP) */
+  MHD_ERR_TIMEOUT = 5      /* a bounded device wait gave up (persistent batched kernel) */
+} mhd_status;
+
+/* Scheme bit field (Sec. 2.2-2.5). Reconstruction in bits 0-3, Riemann solver in bits 4-7,
+ * EMF compute in bits 8-11, EMF averaging in bits 12-15, flags above. */
+enum {
+  MHD_RECON_PC = 0,          /* piecewise constant (Sec. 2.2) */
+  MHD_RECON_PLM_MC = 1,      /* piecewise linear, monotonised-central limiter */
+  MHD_RECON_PLM_MINMOD = 2,  /* piecewise linear, minmod limiter */
+  MHD_RECON_PPM = 3,         /* piecewise parabolic, Colella & Woodward 1984 limiting */
+  MHD_RECON_PPM_EP = 4,      /* extremum-preserving PPM: not defined in the paper -> UNSUPPORTED */
+  MHD_RIEMANN_HLL = 0 << 4,  /* two-wave HLL with the Eq. (alpha-pm) speeds */
+  MHD_RIEMANN_HLLD = 1 << 4, /* Miyoshi & Kusano 2005 HLLD */
+  MHD_RIEMANN_LLF = 2 << 4,  /* local Lax-Friedrichs (Rusanov) */
+  MHD_EMF_Q26 = 0 << 8,      /* the paper's new compute scheme, Eqs. (q26-facevel), (q26) */
+  MHD_EMF_FS18 = 1 << 8,     /* Felker & Stone 2018, Eqs. (fs18-average), (fs18) */
+  MHD_EMF_B25A = 2 << 8,     /* Balsara 2025a, Eqs. (b25a-b-avg), (b25a-emf-centre), (b25a-average) */
+  MHD_AVG_LD04 = 0 << 12,    /* Londrillo & Del Zanna 2004 2D-HLL average, Eq. (ld04) */
+  MHD_AVG_B25B = 1 << 12,    /* Balsara 2025b 2D Riemann solver: not defined -> UNSUPPORTED */
+  MHD_FOFC_OFF = 1 << 16     /* disable first-order flux correction */
+};
+
+typedef struct {
+  int nx, ny, nz;          /* cells per direction, each >= 1 */
+  double dx, dy, dz;       /* cell widths, > 0 */
+  double gamma;            /* adiabatic index, > 1 */
+  int fofc_criteria;       /* bit 0: rho <= 0, bit 1: p <= 0 invalidate a cell; 0 means 3.
+                              A non-finite value always invalidates a cell. */
+} mhd_config;
+
+typedef struct {
+  double *cons;            /* [5][nz][ny][nx], device */
+  double *b0, *b1, *b2;    /* [nz][ny][nx] each, device */
+} mhd_state;
+
+typedef struct mhd_ctx mhd_ctx; /* opaque: owns the scratch of one patch size and a stream */
+
+/* Create a context for one patch size. `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream); all work of the context is enqueued on it. Allocates the step's scratch
+ * (about 60 doubles per cell) with cudaMalloc on the current device. *out is NULL on error. */
+mhd_status mhd_create(const mhd_config *cfg, void *cuda_stream, mhd_ctx **out);
+
+/* Free the context and its scratch (synchronises the stream first). NULL is ignored. */
+void mhd_destroy(mhd_ctx *ctx);
+
+/* One full step of size dt in place (Sec. 2.5): stage 1, flux correction, stage 2, flux
+ * correction; state->cons/b* hold S^{n+1} when the stream reaches the end of the call.
+ * dt > 0 is fixed within the step, eta >= 0 is the constant Ohmic resistivity (Eq.
+ * resistivity:ohms-law; eta = 0 reduces exactly to the ideal scheme). Asynchronous. */
+mhd_status mhd_step(mhd_ctx *ctx, const mhd_state *state, double dt, int scheme, double eta);
+
+/* Largest stable step (Sec. 2.4, Eq. resistivity:cfl): dt = cfl * dx_min / max over cells of
+ * max(max_d (|u_d| + c_fm,d) dx_min / dx_d, 2 eta / dx_min). Synchronous (reads one double). */
+mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double eta, double *dt_out);
+
+/* Discrete divergence diagnostic (Sec. 2.1; Sec. 4.6 validation): max over cells of
+ * |sum_d (b_d(+1/2) - b_d(-1/2)) / dx_d| and max over faces of |b_d|. Synchronous. */
+mhd_status mhd_divb(mhd_ctx *ctx, const mhd_state *state, double *max_abs_divb, double *max_abs_b);
+
+/* Cells flagged invalid by first-order flux correction in stage 1 and stage 2 of the last
+ * mhd_step (Sec. 2.5). Synchronous. */
+mhd_status mhd_stats(mhd_ctx *ctx, long long *fofc_cells_stage1, long long *fofc_cells_stage2);
+
+/* Message of the last failure on ctx ("" if none). Valid until the next call on ctx. */
+const char *mhd_last_error(const mhd_ctx *ctx);
+
+/* Message for a failure of mhd_create or mhd_batch_create, which return no context. */
+const char *mhd_create_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_GB300_H */

@@ -1,0 +1,276 @@
+// mhd_api.cu -- host side of the C ABI declared in include/mhd.h: context and scratch
+// management, argument checks, and the launch sequence of one RK2 + FOFC step (Sec. 2.5).
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/mhd.h"
+#include "mhd_device.cuh"
+#include "mhd_internal.cuh"
+
+struct mhd_ctx {
+  mhd::Dev base;
+  cudaStream_t stream;
+  void* scratch;
+  size_t scratch_bytes;
+  double* U1;
+  double* B1[3];
+  int seg;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+mhd_status fail(mhd_ctx* c, mhd_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+mhd_status cuda_check(mhd_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MHD_OK;
+  return fail(c, MHD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct Decoded {
+  int recon, rs, emf, avg;
+  bool fofc;
+};
+
+mhd_status decode(mhd_ctx* c, int scheme, Decoded& d) {
+  d.recon = scheme & 0xf;
+  d.rs = (scheme >> 4) & 0xf;
+  d.emf = (scheme >> 8) & 0xf;
+  d.avg = (scheme >> 12) & 0xf;
+  d.fofc = !(scheme & MHD_FOFC_OFF);
+  if (scheme & ~(0xffff | MHD_FOFC_OFF)) return fail(c, MHD_ERR_ARG, "unknown scheme bits");
+  if (d.recon == MHD_RECON_PPM_EP)
+    return fail(c, MHD_ERR_UNSUPPORTED, "PPM-EP is cited but not defined in the paper");
+  if (d.avg == 1) return fail(c, MHD_ERR_UNSUPPORTED, "B25b averaging is cited but not defined in the paper");
+  if (d.recon > 3 || d.rs > 2 || d.emf > 2 || d.avg > 1) return fail(c, MHD_ERR_ARG, "scheme field out of range");
+  return MHD_OK;
+}
+
+bool state_ok(const mhd_state* s) { return s && s->cons && s->b0 && s->b1 && s->b2; }
+
+// one RK stage: prim -> faces -> edges -> update -> flags -> flux correction
+void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc) {
+  cudaStream_t st = c->stream;
+  mhd::launch_prim(D, st);
+  for (int dir = 0; dir < 3; ++dir) mhd::launch_face(D, dir, sc.recon, sc.rs, c->seg, st);
+  mhd::launch_edges(D, sc.recon, c->seg, st);
+  mhd::launch_update(D, st);
+  mhd::launch_flag(D, st);
+  if (sc.fofc) mhd::launch_fofc(D, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mhd_create_error(void) { return g_create_err.c_str(); }
+
+const char* mhd_last_error(const mhd_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
+  g_create_err.clear();
+  if (!out) { g_create_err = "out is NULL"; return MHD_ERR_ARG; }
+  *out = nullptr;
+  if (!cfg) { g_create_err = "cfg is NULL"; return MHD_ERR_ARG; }
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || !(cfg->dx > 0) || !(cfg->dy > 0) ||
+      !(cfg->dz > 0) || !(cfg->gamma > 1.0)) {
+    g_create_err = "invalid box: need n >= 1, dx > 0, gamma > 1";
+    return MHD_ERR_ARG;
+  }
+  const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  if (N > (1LL << 31) - 1) {
+    g_create_err = "box larger than 2^31 - 1 cells";
+    return MHD_ERR_ARG;
+  }
+  mhd_ctx* c = new mhd_ctx();
+  c->stream = (cudaStream_t)cuda_stream;
+  c->seg = 64;
+  mhd::Dev& D = c->base;
+  std::memset(&D, 0, sizeof(D));
+  D.n[0] = cfg->nx; D.n[1] = cfg->ny; D.n[2] = cfg->nz;
+  D.N = N;
+  D.stride[0] = 1; D.stride[1] = cfg->nx; D.stride[2] = (long long)cfg->nx * cfg->ny;
+  D.h[0] = cfg->dx; D.h[1] = cfg->dy; D.h[2] = cfg->dz;
+  for (int d = 0; d < 3; ++d) D.hinv[d] = 1.0 / D.h[d];
+  D.gam = cfg->gamma;
+  D.gm1inv = 1.0 / (cfg->gamma - 1.0);
+  D.fofc_criteria = cfg->fofc_criteria ? cfg->fofc_criteria : 3;
+  // scratch, in doubles per cell: U1 5, B1 3, P 8, F 15, Ap/Am/Us 9, Epart 12, E 3,
+  // VL/VR 18, Xpart 24, Ec 3, EfL 6, EfB 6  -> 112; + flags (1 byte) + counters
+  const size_t nd = 112;
+  const size_t bytes = nd * sizeof(double) * (size_t)N + (size_t)N + 256 + 64;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    g_create_err = std::string("cudaMalloc of scratch failed: ") + cudaGetErrorString(e);
+    delete c;
+    return MHD_ERR_CUDA;
+  }
+  c->scratch = p;
+  c->scratch_bytes = bytes;
+  double* q = (double*)p;
+  auto take = [&](size_t k) { double* r = q; q += k * (size_t)N; return r; };
+  c->U1 = take(5);
+  for (int d = 0; d < 3; ++d) c->B1[d] = take(1);
+  D.P = take(8);
+  D.F = take(15);
+  D.Ap = take(3);
+  D.Am = take(3);
+  D.Us = take(3);
+  D.Epart = take(12);
+  D.E = take(3);
+  D.VL = take(9);
+  D.VR = take(9);
+  D.Xpart = take(24);
+  D.Ec = take(3);
+  D.EfL = take(6);
+  D.EfB = take(6);
+  D.counters = (unsigned long long*)q;  // 8 counters, 64 bytes
+  D.flag = (unsigned char*)(q + 8);
+  e = cudaMemsetAsync(p, 0, bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    g_create_err = std::string("scratch initialisation failed: ") + cudaGetErrorString(e);
+    cudaFree(p);
+    delete c;
+    return MHD_ERR_CUDA;
+  }
+  *out = c;
+  return MHD_OK;
+}
+
+void mhd_destroy(mhd_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->scratch);
+  delete ctx;
+}
+
+mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme, double eta) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state)) return fail(ctx, MHD_ERR_ARG, "state has a NULL array");
+  if (!(dt > 0) || !(dt < 1e300)) return fail(ctx, MHD_ERR_ARG, "dt must be finite and > 0");
+  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
+  Decoded sc;
+  mhd_status s = decode(ctx, scheme, sc);
+  if (s != MHD_OK) return s;
+  if (sc.emf != mhd::EMF_Q26) return fail(ctx, MHD_ERR_UNSUPPORTED, "EMF compute scheme not built");
+
+  mhd::Dev D = ctx->base;
+  const long long N = D.N;
+  D.dt = dt;
+  D.eta = eta;
+  D.resistive = eta != 0.0;
+  D.emf = sc.emf;
+  if (!sc.fofc) D.fofc_criteria = 0;  // flags then count only non-finite cells
+  D.U0 = state->cons;
+  D.B0[0] = state->b0; D.B0[1] = state->b1; D.B0[2] = state->b2;
+  cudaStream_t st = ctx->stream;
+  s = cuda_check(ctx, cudaMemsetAsync(D.counters, 0, 4 * sizeof(unsigned long long), st), "cudaMemsetAsync");
+  if (s != MHD_OK) return s;
+
+  // stage 1: S^{n+1/2} = S^n + D^n  (Eq. rk1:update), written to scratch
+  D.Uin = D.U0;
+  for (int d = 0; d < 3; ++d) D.Bin[d] = D.B0[d];
+  D.Uout = ctx->U1;
+  for (int d = 0; d < 3; ++d) D.Bout[d] = ctx->B1[d];
+  D.combine = 0;
+  D.stage = 0;
+  run_stage(ctx, D, sc);
+
+  // stage 2: S^{n+1} = S^n + D(F_rk), F_rk = (F^n + F^{n+1/2}) / 2  (Eq. rk2:update); the
+  // update reads only S^n and the fluxes, so it may overwrite the stage-1 scratch in place.
+  D.Uin = ctx->U1;
+  for (int d = 0; d < 3; ++d) D.Bin[d] = ctx->B1[d];
+  D.combine = 1;
+  D.stage = 1;
+  run_stage(ctx, D, sc);
+
+  s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
+  if (s != MHD_OK) return s;
+  s = cuda_check(ctx, cudaMemcpyAsync(state->cons, ctx->U1, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                 "cudaMemcpyAsync");
+  if (s != MHD_OK) return s;
+  double* bout[3] = {state->b0, state->b1, state->b2};
+  for (int d = 0; d < 3; ++d) {
+    s = cuda_check(ctx, cudaMemcpyAsync(bout[d], ctx->B1[d], N * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                   "cudaMemcpyAsync");
+    if (s != MHD_OK) return s;
+  }
+  return MHD_OK;
+}
+
+mhd_status mhd_stats(mhd_ctx* ctx, long long* s1, long long* s2) {
+  if (!ctx) return MHD_ERR_ARG;
+  unsigned long long h[2] = {0, 0};
+  mhd_status s = cuda_check(ctx, cudaMemcpyAsync(h, ctx->base.counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream),
+                            "cudaMemcpyAsync");
+  if (s != MHD_OK) return s;
+  s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  if (s1) *s1 = (long long)h[0];
+  if (s2) *s2 = (long long)h[1];
+  return MHD_OK;
+}
+
+static mhd_status read_counters(mhd_ctx* ctx, unsigned long long* h, int n) {
+  mhd_status s = cuda_check(ctx, cudaMemcpyAsync(h, ctx->base.counters + 2, n * sizeof(unsigned long long),
+                                                 cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+  if (s != MHD_OK) return s;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+}
+
+mhd_status mhd_max_dt(mhd_ctx* ctx, const mhd_state* state, double cfl, double eta, double* dt_out) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state) || !dt_out) return fail(ctx, MHD_ERR_ARG, "NULL argument");
+  if (!(cfl > 0) || !(eta >= 0)) return fail(ctx, MHD_ERR_ARG, "need cfl > 0 and eta >= 0");
+  const mhd::Dev& D = ctx->base;
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, sizeof(unsigned long long), ctx->stream),
+                            "cudaMemsetAsync");
+  if (s != MHD_OK) return s;
+  mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
+  mhd::launch_maxspeed(D, state->cons, B, D.counters + 2, ctx->stream);
+  s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
+  if (s != MHD_OK) return s;
+  unsigned long long h = 0;
+  s = read_counters(ctx, &h, 1);
+  if (s != MHD_OK) return s;
+  double smax;
+  std::memcpy(&smax, &h, sizeof(double));
+  const double hmin = std::fmin(D.h[0], std::fmin(D.h[1], D.h[2]));
+  const double sres = 2.0 * eta / hmin;
+  if (sres > smax) smax = sres;
+  if (!(smax > 0) || !(smax < 1e300)) return fail(ctx, MHD_ERR_NONFINITE, "signal speed is zero or not finite");
+  *dt_out = cfl * hmin / smax;
+  return MHD_OK;
+}
+
+mhd_status mhd_divb(mhd_ctx* ctx, const mhd_state* state, double* max_abs_divb, double* max_abs_b) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state) || !max_abs_divb || !max_abs_b) return fail(ctx, MHD_ERR_ARG, "NULL argument");
+  const mhd::Dev& D = ctx->base;
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 2 * sizeof(unsigned long long), ctx->stream),
+                            "cudaMemsetAsync");
+  if (s != MHD_OK) return s;
+  mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
+  mhd::launch_divb(D, B, D.counters + 2, ctx->stream);
+  s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
+  if (s != MHD_OK) return s;
+  unsigned long long h[2] = {0, 0};
+  s = read_counters(ctx, h, 2);
+  if (s != MHD_OK) return s;
+  std::memcpy(max_abs_divb, &h[0], sizeof(double));
+  std::memcpy(max_abs_b, &h[1], sizeof(double));
+  return MHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// mhd_internal.cuh -- parameters shared by the kernel translation units and the host API.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mhd {
+
+// three device pointers passed by value
+struct Ptr3 {
+  const double* p[3];
+};
+
+// Everything one stage's kernels need, passed by value. Arrays are SoA over the N cells of a
+// periodic box, x fastest; face arrays and edge arrays use the cell's linear index (the face or
+// edge at the cell's lower half-index, as documented in include/mhd.h).
+struct Dev {
+  int n[3];
+  long long N;
+  long long stride[3];  // 1, nx, nx*ny
+  double h[3];
+  double hinv[3];
+  double gam, gm1inv;
+  double dt, eta;
+  int resistive;        // eta != 0
+  int combine;          // stage 2: store (old + new) / 2 into fluxes and EMFs
+  int fofc_criteria;    // bit 0 rho <= 0, bit 1 p <= 0
+  int emf;              // EMF compute scheme
+  // S^n (caller, read only), stage input, stage output
+  const double* U0;
+  const double* B0[3];
+  const double* Uin;
+  const double* Bin[3];
+  double* Uout;
+  double* Bout[3];
+  // scratch
+  double* P;      // [8][N] rho, u0, u1, u2, p, bc0, bc1, bc2 of the stage input
+  double* F;      // [3][5][N] face fluxes (flux of cons[v] across the d-face at X - d/2)
+  double* Ap;     // [3][N] alpha+ on d-faces
+  double* Am;     // [3][N] alpha-
+  double* Us;     // [3][N] Q26 face-normal velocity u_d^*
+  double* Epart;  // [3][4][N] per e-edge: b_a^B, b_a^T, u_a^B, u_a^T (reconstructed along c)
+  double* E;      // [3][N] edge EMFs
+  // FS18 / B25a extras
+  double* VL;     // [3][3][N] FS18: left velocity states on d-faces, component k
+  double* VR;     // [3][3][N]
+  double* Xpart;  // [3][8][N] FS18/B25a per e-edge corner partials of the a-faces sweep
+  double* Ec;     // [3][N] B25a cell-centred EMF of the stage input
+  double* EfL;    // [3][2][N] B25a e-EMF on a-faces (L/R) for order (a then c)
+  double* EfB;    // [3][2][N] B25a e-EMF on c-faces (B/T) for order (c then a)
+  unsigned char* flag;         // [N]
+  unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
+  int stage;      // 0 or 1 (which counter the flux correction reads)
+};
+
+// launchers (each enqueues on `st`)
+void launch_prim(const Dev& d, cudaStream_t st);
+void launch_face(const Dev& d, int dir, int recon, int rs, int seg, cudaStream_t st);
+void launch_edges(const Dev& d, int recon, int seg, cudaStream_t st);
+void launch_update(const Dev& d, cudaStream_t st);
+void launch_flag(const Dev& d, cudaStream_t st);
+void launch_fofc(const Dev& d, cudaStream_t st);
+void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st);
+void launch_divb(const Dev& d, Ptr3 B, unsigned long long* out, cudaStream_t st);
+
+}  // namespace mhd

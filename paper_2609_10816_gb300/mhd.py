@@ -1,0 +1,163 @@
+"""Thin ctypes binding of libmhd.so (include/mhd.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels. PyTorch supplies device memory and
+the stream. If the library is missing or cannot load, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmhd.so")
+
+# scheme bits (include/mhd.h)
+RECON = {"pc": 0, "plm_mc": 1, "plm_minmod": 2, "ppm": 3, "ppm_ep": 4}
+RIEMANN = {"hll": 0 << 4, "hlld": 1 << 4, "llf": 2 << 4}
+EMF = {"q26": 0 << 8, "fs18": 1 << 8, "b25a": 2 << 8}
+AVG = {"ld04": 0 << 12, "b25b": 1 << 12}
+FOFC_OFF = 1 << 16
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_TIMEOUT = range(6)
+_NAMES = ["OK", "ARG", "CUDA", "NONFINITE", "UNSUPPORTED", "TIMEOUT"]
+
+
+def scheme(recon="plm_mc", riemann="hll", emf="q26", avg="ld04", fofc=True) -> int:
+    return RECON[recon] | RIEMANN[riemann] | EMF[emf] | AVG[avg] | (0 if fofc else FOFC_OFF)
+
+
+class MHDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mhd error {_NAMES[code] if 0 <= code < 6 else code}: {msg}")
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("fofc_criteria", ctypes.c_int),
+    ]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [("cons", ctypes.c_void_p), ("b0", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("b2", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmhd.so (raises if it is absent: build it with paper_2609_10816_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2609_10816_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    d = ctypes.c_double
+    L.mhd_create.argtypes = [P(_Config), vp, P(vp)]
+    L.mhd_create.restype = ctypes.c_int
+    L.mhd_destroy.argtypes = [vp]
+    L.mhd_destroy.restype = None
+    L.mhd_step.argtypes = [vp, P(_State), d, ctypes.c_int, d]
+    L.mhd_step.restype = ctypes.c_int
+    L.mhd_max_dt.argtypes = [vp, P(_State), d, d, P(d)]
+    L.mhd_max_dt.restype = ctypes.c_int
+    L.mhd_divb.argtypes = [vp, P(_State), P(d), P(d)]
+    L.mhd_divb.restype = ctypes.c_int
+    L.mhd_stats.argtypes = [vp, P(ctypes.c_longlong), P(ctypes.c_longlong)]
+    L.mhd_stats.restype = ctypes.c_int
+    L.mhd_last_error.argtypes = [vp]
+    L.mhd_last_error.restype = ctypes.c_char_p
+    L.mhd_create_error.argtypes = []
+    L.mhd_create_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check_field(t: torch.Tensor, shape, name):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class State:
+    """Device state of one periodic box: cons (5, nz, ny, nx) and b (3, nz, ny, nx), float64."""
+
+    def __init__(self, cons: torch.Tensor, b: torch.Tensor):
+        self.cons = cons
+        self.b = b
+
+    def c(self) -> _State:
+        return _State(self.cons.data_ptr(), self.b[0].data_ptr(), self.b[1].data_ptr(), self.b[2].data_ptr())
+
+
+class Context:
+    """mhd_create / mhd_destroy for one box size, on a torch CUDA stream."""
+
+    def __init__(self, shape, h, gamma=5.0 / 3.0, stream: torch.cuda.Stream | None = None, fofc_criteria=3):
+        L = lib()
+        self.shape = tuple(int(n) for n in shape)
+        self.h = tuple(float(x) for x in h)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = _Config(self.shape[0], self.shape[1], self.shape[2], self.h[0], self.h[1], self.h[2],
+                      float(gamma), int(fofc_criteria))
+        out = ctypes.c_void_p()
+        rc = L.mhd_create(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(out))
+        if rc != OK:
+            raise MHDError(rc, L.mhd_create_error().decode())
+        self._h = out
+
+    def _err(self, rc):
+        if rc != OK:
+            raise MHDError(rc, lib().mhd_last_error(self._h).decode())
+
+    def _state(self, st: State) -> _State:
+        nx, ny, nz = self.shape
+        _check_field(st.cons, (5, nz, ny, nx), "cons")
+        _check_field(st.b, (3, nz, ny, nx), "b")
+        return st.c()
+
+    def step(self, st: State, dt: float, scheme_bits: int, eta: float = 0.0):
+        s = self._state(st)
+        self._err(lib().mhd_step(self._h, ctypes.byref(s), float(dt), int(scheme_bits), float(eta)))
+
+    def max_dt(self, st: State, cfl: float, eta: float = 0.0) -> float:
+        s = self._state(st)
+        out = ctypes.c_double()
+        self._err(lib().mhd_max_dt(self._h, ctypes.byref(s), float(cfl), float(eta), ctypes.byref(out)))
+        return out.value
+
+    def divb(self, st: State):
+        s = self._state(st)
+        md, mb = ctypes.c_double(), ctypes.c_double()
+        self._err(lib().mhd_divb(self._h, ctypes.byref(s), ctypes.byref(md), ctypes.byref(mb)))
+        return md.value, mb.value
+
+    def stats(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        self._err(lib().mhd_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mhd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def to_device(cons, b, device="cuda") -> State:
+    return State(torch.as_tensor(cons, dtype=torch.float64).to(device).contiguous(),
+                 torch.as_tensor(b, dtype=torch.float64).to(device).contiguous())

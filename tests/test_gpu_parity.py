@@ -1,0 +1,108 @@
+"""CUDA path (libmhd.so through the C ABI) against the CPU oracle, element by element.
+
+Tolerance: relative L1 per stored field per step <= 1e-12 (denominator floored at N times the
+field family's natural scale), the accuracy bar of the method's parity requirement; the face
+field's divergence stays at rounding, max |div b| dx / max |b| <= 1e-13.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_10816_gb300 import inputs
+from paper_2609_10816_gb300 import mhd
+from tests.util import state_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def gpu_step(ctx, cons, b, dt, sch, eta=0.0):
+    st = mhd.to_device(cons, b)
+    ctx.step(st, dt, sch, eta)
+    torch.cuda.synchronize()
+    return st.cons.cpu().numpy(), st.b.cpu().numpy(), ctx.stats()
+
+
+def assert_parity(cg, bg, co, bo, tol=TOL, what=""):
+    errs = state_errors(cg, bg, co, bo)
+    bad = {k: v for k, v in errs.items() if not (v <= tol)}
+    assert not bad, f"{what}: relative L1 above {tol}: {bad}"
+    return errs
+
+
+COMBOS = [(r, s) for r in ("pc", "plm_mc", "plm_minmod", "ppm") for s in ("hll", "hlld", "llf")]
+
+
+@pytest.mark.parametrize("recon,rs", COMBOS)
+@pytest.mark.parametrize("shape", [(8, 8, 8), (70, 9, 5)])
+def test_one_step_all_schemes(gpu_lib, recon, rs, shape):
+    cons, b, info = inputs.random_smooth(shape, seed=11, rough=0.05)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf="q26")
+    dt = oracle.max_dt(cfg, cons, b, 0.3)
+    co, bo, cnt = oracle.step(cfg, cons, b, dt)
+    ctx = mhd.Context(shape, info["h"])
+    cg, bg, cntg = gpu_step(ctx, cons, b, dt, mhd.scheme(recon, rs, "q26"))
+    assert_parity(cg, bg, co, bo, what=f"{recon}/{rs}/{shape}")
+    assert cntg == cnt
+
+
+@pytest.mark.parametrize("shape", [(16, 1, 1), (1, 12, 3), (2, 5, 9), (130, 3, 2)])
+def test_degenerate_and_ragged_boxes(gpu_lib, shape):
+    cons, b, info = inputs.random_smooth(shape, seed=5, rough=0.02)
+    for recon, rs in (("ppm", "hlld"), ("plm_mc", "hll")):
+        cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs)
+        dt = oracle.max_dt(cfg, cons, b, 0.3)
+        co, bo, _ = oracle.step(cfg, cons, b, dt)
+        ctx = mhd.Context(shape, info["h"])
+        cg, bg, _ = gpu_step(ctx, cons, b, dt, mhd.scheme(recon, rs))
+        assert_parity(cg, bg, co, bo, what=f"{recon}/{rs}/{shape}")
+
+
+def test_fast_wave_32cubed_multistep(gpu_lib):
+    """32^3 oblique fast eigenmode, PLM-MC + HLL + Q26 + LD04, CFL 0.3: 10 steps, every step."""
+    shape = (32, 32, 32)
+    cons, b, info = inputs.fast_wave(shape)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon="plm_mc", riemann="hll")
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    co, bo = cons, b
+    sch = mhd.scheme("plm_mc", "hll")
+    for _ in range(10):
+        dt = oracle.max_dt(cfg, co, bo, 0.3)
+        dtg = ctx.max_dt(st, 0.3)
+        assert abs(dtg - dt) <= 1e-14 * dt
+        co, bo, _ = oracle.step(cfg, co, bo, dt)
+        ctx.step(st, dt, sch)
+        torch.cuda.synchronize()
+        assert_parity(st.cons.cpu().numpy(), st.b.cpu().numpy(), co, bo, what="fast wave")
+    md, mb = ctx.divb(st)
+    assert md * info["h"][0] / mb <= 1e-13
+
+
+def test_resistive_step(gpu_lib):
+    shape = (24, 20, 6)
+    cons, b, info = inputs.random_smooth(shape, seed=7, rough=0.02)
+    for recon, rs in (("plm_mc", "hlld"), ("ppm", "hll")):
+        cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, eta=3e-3)
+        dt = oracle.max_dt(cfg, cons, b, 0.3)
+        co, bo, _ = oracle.step(cfg, cons, b, dt)
+        ctx = mhd.Context(shape, info["h"])
+        cg, bg, _ = gpu_step(ctx, cons, b, dt, mhd.scheme(recon, rs), eta=3e-3)
+        assert_parity(cg, bg, co, bo, what=f"eta {recon}/{rs}")
+
+
+def test_max_dt_and_divb(gpu_lib):
+    shape = (20, 12, 7)
+    cons, b, info = inputs.random_smooth(shape, seed=3, rough=0.1)
+    cfg = oracle.Config(shape=shape, h=info["h"], eta=2e-2)
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    for eta in (0.0, 2e-2, 10.0):
+        cfg.eta = eta
+        assert abs(ctx.max_dt(st, 0.3, eta) - oracle.max_dt(cfg, cons, b, 0.3)) <= 1e-14 * oracle.max_dt(cfg, cons, b, 0.3)
+    md, mb = ctx.divb(st)
+    mdo, mbo = oracle.divb(cfg, b)
+    assert mb == mbo
+    assert abs(md - mdo) <= 1e-12 * mbo / min(info["h"])
