@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 CT-MHD step: cell-updates/s (FP64) on the 256^3 decaying-turbulence
+workload, with the live roofline of the dominant kernel, an end-to-end number through the C ABI
+with host buffers, clocks sampled during the timed region, and the CPU oracle as baseline.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+One step = one CFL time step (mhd_max_dt, CFL 0.3) plus one full mhd_step (RK2-SSP, two stages,
+first-order flux correction on) of the whole box. N > 1 (torchrun) runs one independent box per
+GPU (replicas; the path is not sharded) and reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per GB300 (FP64, plain vs batched vs fwd+adjoint), % HBM roofline"
+UNIT = "cell-updates/s"
+
+# Roofline constants: GB300 FP64 = 152 SMs x 2 DFMA/clk x 2 flops at 2070 MHz
+# (the recipe's unit counts and maximum clock; a DFMA microbenchmark measured 1.19 TFLOP/s at
+# ~1990 MHz). Algorithmic FP64 flops per face of the face sweep (reconstruction of 7 primitives
+# along the sweep + Riemann solve + Joule flux), counted by the oracle's op-counting scalar on a
+# 32^3 sample of the same workload (oracle/count_flops.py): PPM + HLLD + Q26, turbulence Mach 5.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FLOPS_PER_FACE = {"ppm/hlld": 316.4, "plm_mc/hll": 249.0, "plm_mc/hlld": 430.9}
+FLOPS_PER_CELL_UPDATE = {"ppm/hlld": 2916.2, "plm_mc/hll": 2325.3, "plm_mc/hlld": 3385.3}
+HBM_PEAK_GBS = 6759.6  # MEASURED_PEAKS.json copy bandwidth
+ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
+# DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel sources it was taken on.
+TRAFFIC = {"face": {"bytes_per_launch": 686.3e6, "cells": 160**3, "src": "40dd8ea10159d6da"}}
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_10816_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n):
+    from paper_2609_10816_gb300 import inputs
+
+    cons, b, info = inputs.turbulence((n, n, n), seed=2, v_rms=5.0)
+    return cons, b, info
+
+
+WORKLOAD_NAME = ("{n}^3 periodic FP64 ideal decaying MHD turbulence: rho=1, B0=(0,0,0.5), p=rho/gamma, "
+                 "seeded solenoidal velocity, E(k)~k^-2 on 1<=|k|<=3, rms Mach 5; PPM+HLLD, Q26 EMF "
+                 "compute + LD04 averaging, RK2-SSP with first-order flux correction, CFL 0.3")
+
+
+def cpu_baseline(budget_s=12.0, n=48):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    import oracle
+
+    cons, b, info = workload(n)
+    cfg = oracle.Config(shape=(n, n, n), h=info["h"], recon="ppm", riemann="hlld", emf="q26")
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        dt = oracle.max_dt(cfg, cons, b, 0.3)
+        cons, b, _ = oracle.step(cfg, cons, b, dt)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n**3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps (CFL dt + RK2/FOFC step) of a {n}^3 box of the same recipe, "
+                      f"PPM+HLLD+Q26+LD04, single thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host, on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = 32
+    cons, b, info = workload(n)
+    import oracle
+
+    cfg = oracle.Config(shape=(n, n, n), h=info["h"], recon="ppm", riemann="hlld", emf="q26")
+    for _ in range(args.warmup):
+        cons, b, _ = oracle.step(cfg, cons, b, oracle.max_dt(cfg, cons, b, 0.3))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cons, b, _ = oracle.step(cfg, cons, b, oracle.max_dt(cfg, cons, b, 0.3))
+    el = time.perf_counter() - t0
+    v = n**3 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME.format(n=256), "sample": f"{n}^3 box per step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed oracle steps of a {n}^3 box of the same recipe"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="box edge of the timed workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2609_10816_gb300 import build, mhd
+
+    build.build()
+    n = args.n
+    cons, b, info = workload(n)
+    N = n**3
+    stream = torch.cuda.current_stream(dev)
+    ctx = mhd.Context((n, n, n), info["h"], stream=stream)
+    st = mhd.to_device(cons, b, dev)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+
+    def one_step():
+        dt = ctx.max_dt(st, 0.3)
+        ctx.step(st, dt, sch)
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region ------------------------------------------------------
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    s1, s2 = ctx.stats()
+    md, mb = ctx.divb(st)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * N * args.steps / (t_max / 1e3)
+
+    # dominant kernel and its live roofline
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    per_launch_s = dom_ms / 1e3 / dom_launches if dom_launches else float("nan")
+    key = "ppm/hlld"
+    if dom == "face":
+        flops_per_launch = FLOPS_PER_FACE[key] * N
+    else:
+        flops_per_launch = float("nan")
+    achieved = flops_per_launch / per_launch_s / 1e12
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] * (N / tr["cells"]) if tr and tr.get("src") == kernel_src_hash() else None
+    launches_timed = sum(v[1] for v in prof.values())
+
+    # ---- end to end through the C ABI with host buffers --------------------------------------
+    cons_h = torch.from_numpy(cons).pin_memory()
+    b_h = torch.from_numpy(b).pin_memory()
+    out_c = torch.empty_like(cons_h).pin_memory()
+    out_b = torch.empty_like(b_h).pin_memory()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        st.cons.copy_(cons_h, non_blocking=True)
+        st.b.copy_(b_h, non_blocking=True)
+        one_step()
+        out_c.copy_(st.cons, non_blocking=True)
+        out_b.copy_(st.b, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * N * args.e2e_steps / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD_NAME.format(n=n),
+            "cells_per_gpu": N,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (state 64 B/cell = %.2f GB per GPU)" % (64 * N / 1e9),
+        },
+        "roofline": {
+            "kernel": dom,
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": traffic,
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (recipe unit counts and max clock)",
+            "algorithmic_flops_per_launch": flops_per_launch,
+            "avg_launch_ms": per_launch_s * 1e3,
+        },
+        "hbm_roofline": {
+            "algorithmic_bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE,
+            "achieved_GBps": value / world * ALG_BYTES_PER_CELL_UPDATE / 1e9,
+            "peak_GBps": HBM_PEAK_GBS,
+            "frac": value / world * ALG_BYTES_PER_CELL_UPDATE / 1e9 / HBM_PEAK_GBS,
+        },
+        "fp64_whole_step": {
+            "algorithmic_flops_per_cell_update": FLOPS_PER_CELL_UPDATE[key],
+            "achieved_TFLOPs": value / world * FLOPS_PER_CELL_UPDATE[key] / 1e12,
+            "frac": value / world * FLOPS_PER_CELL_UPDATE[key] / 1e12 / FP64_PEAK_TFLOPS,
+        },
+        "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+        "e2e": {
+            "value": e2e_value,
+            "unit": UNIT,
+            "h2d_bytes_per_step": int(cons_h.numel() * 8 + b_h.numel() * 8),
+            "d2h_bytes_per_step": int(out_c.numel() * 8 + out_b.numel() * 8),
+        },
+        "gpu_launches": launches_timed,
+        "clocks": clocks,
+        "checks": {"fofc_flagged_last_step": [s1, s2], "max_divb_dx_over_b": md * info["h"][0] / mb},
+        "forms": {"plain_q26": value},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,32 @@ mhd_status mhd_divb(mhd_ctx *ctx, const mhd_state *state, double *max_abs_divb, 
  * mhd_step (Sec. 2.5). Synchronous. */
 mhd_status mhd_stats(mhd_ctx *ctx, long long *fofc_cells_stage1, long long *fofc_cells_stage2);
 
+/* Kernel classes reported by mhd_profile_read (one entry per class; a class may cover several
+ * launches per stage). */
+enum {
+  MHD_K_PRIM = 0,      /* cons -> prim */
+  MHD_K_FACE = 1,      /* reconstruction + Riemann sweeps, 3 launches per stage */
+  MHD_K_EDGE_BT = 2,   /* a-face quantities to edges along c, 3 launches per stage */
+  MHD_K_EDGE_LR = 3,   /* c-face quantities to edges along a + LD04 + eta j, 3 per stage */
+  MHD_K_UPDATE = 4,    /* flux divergence and CT update */
+  MHD_K_FLAG = 5,      /* validity flags */
+  MHD_K_FOFC = 6,      /* first-order flux correction, 3 launches per stage (exit early if no flag) */
+  MHD_K_MAXSPEED = 7,  /* CFL reduction */
+  MHD_K_DIVB = 8,      /* divergence reduction */
+  MHD_K_EXTRA = 9,     /* scheme-specific extras (FS18 / B25a sweeps) */
+  MHD_K_COUNT = 16
+};
+
+/* Start (enable != 0) or stop per-kernel timing on ctx: while enabled, every launch of the
+ * library is bracketed by CUDA events on the context's stream. Starting clears the totals.
+ * Launch counts are kept whether or not timing is enabled. */
+mhd_status mhd_profile(mhd_ctx *ctx, int enable);
+
+/* Synchronise the stream and return, per kernel class, the summed device time in ms of the
+ * launches timed since mhd_profile(ctx, 1) (NULL allowed) and the number of launches since the
+ * context was created or the counts were last read with reset != 0. Arrays hold MHD_K_COUNT. */
+mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches, int reset);
+
 /* Message of the last failure on ctx ("" if none). Valid until the next call on ctx. */
 const char *mhd_last_error(const mhd_ctx *ctx);
 

@@ -69,8 +69,32 @@ inline Dual operator/(Dual a, Dual b) {
 inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 
+// Operation counting (used only to state the algorithmic FP64 work per unit of the method):
+// every +, -, *, / and sqrt of a Cnt adds one to the counter of the current phase; comparisons,
+// negation and |x| are not counted.
+enum { PH_PRIM = 0, PH_RECON = 1, PH_RIEMANN = 2, PH_EDGE = 3, PH_JOULE = 4, PH_UPDATE = 5,
+       PH_FLAG = 6, PH_FO = 7, NPHASE = 8 };
+long long g_ops[NPHASE];
+int g_phase = 0;
+bool g_fo = false;
+inline void set_phase(int p) { g_phase = g_fo ? PH_FO : p; }
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double x) : v(x) {}  // NOLINT: implicit promotion of constants
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_ops[g_phase]; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_ops[g_phase]; return Cnt(a.v - b.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_ops[g_phase]; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_ops[g_phase]; return Cnt(a.v / b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+
 inline double val(double x) { return x; }
 inline double val(const Dual& x) { return x.v; }
+inline double val(const Cnt& x) { return x.v; }
+inline Cnt sqrt_(Cnt a) { ++g_ops[g_phase]; return Cnt(std::sqrt(a.v)); }
 inline double sqrt_(double x) { return std::sqrt(x); }
 inline Dual sqrt_(Dual a) {
   const double s = std::sqrt(a.v);
@@ -130,6 +154,7 @@ template <class T>
 void cons_to_prim(const Grid& g, const std::vector<T>& U, const std::vector<T>& B,
                   std::vector<T>& P) {
   const long N = g.N;
+  set_phase(PH_PRIM);
   P.assign(NPRIM * N, T(0.0));
   for (long X = 0; X < N; ++X) {
     const T rho = U[X];
@@ -408,7 +433,9 @@ void fluxes_and_emfs(const Grid& g, const Scheme<T>& sc, const std::vector<T>& U
     // primitive slots in face order {rho, u_n, u_t1, u_t2, p, b_t1, b_t2}
     const int slot[7] = {P_RHO, P_U + d, P_U + a, P_U + c, P_P, P_B + a, P_B + c};
     std::vector<T> qm[7], qp[7];
+    set_phase(PH_RECON);
     for (int v = 0; v < 7; ++v) recon_field(g, sc.recon, &P[slot[v] * N], d, qm[v], qp[v]);
+    set_phase(PH_RIEMANN);
     for (long X = 0; X < N; ++X) {
       const long Xl = g.sh(X, d, -1);
       T WL[7], WR[7];
@@ -439,6 +466,7 @@ void fluxes_and_emfs(const Grid& g, const Scheme<T>& sc, const std::vector<T>& U
   // --- Sec. 2.3: EMF on every e-edge. For edge direction e, a = e+1 and c = e+2 play the
   // roles of x0 and x1 in the paper's x2-edge description (cyclic permutation).
   std::vector<T> rm, rp, rm2, rp2;
+  set_phase(PH_EDGE);
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3, c = (e + 2) % 3;
     // Fig. (b-common): b_a reconstructed along c (B/T), b_c along a (L/R).
@@ -554,6 +582,7 @@ void fluxes_and_emfs(const Grid& g, const Scheme<T>& sc, const std::vector<T>& U
 
   // --- Sec. 2.4: Joule-heating energy flux eta (j x b) on each face (reading R8).
   if (sc.resistive) {
+    set_phase(PH_JOULE);
     std::vector<T> J(3 * N);
     for (int e = 0; e < 3; ++e) {
       const int a = (e + 1) % 3, c = (e + 2) % 3;
@@ -679,6 +708,7 @@ void step(const Grid& g, const Scheme<T>& sc, int fofc_criteria, std::vector<T>&
   // Stage 1: S^{n+1/2} = S^n + D^n (Eq. rk1:update).
   FluxSet<T> f0;
   fluxes_and_emfs(g, sc, U0, B0, f0);
+  set_phase(PH_UPDATE);
   std::vector<T> U1(5 * N), B1(3 * N);
   for (long X = 0; X < N; ++X)
     for (int v = 0; v < 5; ++v) U1[v * N + X] = U0[v * N + X] + incr_cell(g, f0, v, X, dt);
@@ -688,11 +718,14 @@ void step(const Grid& g, const Scheme<T>& sc, int fofc_criteria, std::vector<T>&
   std::vector<char> flag(N, 0), fmask, emask;
   so.flagged[0] = so.flagged[1] = 0;
   if (fofc_criteria) {
+    set_phase(PH_FLAG);
     for (long X = 0; X < N; ++X)
       flag[X] = cell_invalid(g, U1, B1, X, fofc_criteria) || (user_flags && user_flags[0] && user_flags[0][X]);
     for (long X = 0; X < N; ++X) so.flagged[0] += flag[X];
   }
   if (so.flagged[0] > 0) {
+    g_fo = true;
+    set_phase(PH_FO);
     fluxes_and_emfs(g, fo, U0, B0, ffo);
     have_fo = true;
     build_masks(g, flag, fmask, emask);
@@ -708,11 +741,13 @@ void step(const Grid& g, const Scheme<T>& sc, int fofc_criteria, std::vector<T>&
     for (int d = 0; d < 3; ++d)
       for (long X = 0; X < N; ++X)
         if (face_touched(g, emask, d, X)) B1[d * N + X] = B0[d * N + X] + incr_face(g, f0, d, X, dt);
+    g_fo = false;
   }
 
   // Stage 2: S^{n+1} = S^n + (D^n + D^{n+1/2}) / 2 (Eq. rk2:update).
   FluxSet<T> f1;
   fluxes_and_emfs(g, sc, U1, B1, f1);
+  set_phase(PH_UPDATE);
   for (long X = 0; X < N; ++X)
     for (int v = 0; v < 5; ++v)
       U[v * N + X] = U0[v * N + X] + 0.5 * (incr_cell(g, f0, v, X, dt) + incr_cell(g, f1, v, X, dt));
@@ -721,12 +756,15 @@ void step(const Grid& g, const Scheme<T>& sc, int fofc_criteria, std::vector<T>&
       B[d * N + X] = B0[d * N + X] + 0.5 * (incr_face(g, f0, d, X, dt) + incr_face(g, f1, d, X, dt));
 
   if (fofc_criteria) {
+    set_phase(PH_FLAG);
     std::fill(flag.begin(), flag.end(), 0);
     for (long X = 0; X < N; ++X)
       flag[X] = cell_invalid(g, U, B, X, fofc_criteria) || (user_flags && user_flags[1] && user_flags[1][X]);
     for (long X = 0; X < N; ++X) so.flagged[1] += flag[X];
   }
   if (so.flagged[1] > 0) {
+    g_fo = true;
+    set_phase(PH_FO);
     if (!have_fo) fluxes_and_emfs(g, fo, U0, B0, ffo);
     build_masks(g, flag, fmask, emask);
     // RK-averaged fluxes, replaced outright by the cached first-order ones on masked faces.
@@ -747,6 +785,7 @@ void step(const Grid& g, const Scheme<T>& sc, int fofc_criteria, std::vector<T>&
     for (int d = 0; d < 3; ++d)
       for (long X = 0; X < N; ++X)
         if (face_touched(g, emask, d, X)) B[d * N + X] = B0[d * N + X] + incr_face(g, fm, d, X, dt);
+    g_fo = false;
   }
 }
 
@@ -908,6 +947,25 @@ int oracle_steps_jvp(const oracle_cfg* c, double* cons, double* b, double* dcons
   for (long i = 0; i < 5 * N; ++i) { cons[i] = U[i].v; dcons[i] = U[i].t; }
   for (long i = 0; i < 3 * N; ++i) { b[i] = B[i].v; db[i] = B[i].t; }
   return 0;
+}
+
+// FP64 operations (+, -, *, /, sqrt) of one step, by phase: prim, face reconstruction, Riemann
+// solves, edge EMFs, Joule flux, update, flags, first-order correction. Returns the phase count.
+int oracle_count_ops(const oracle_cfg* c, const double* cons, const double* b, double dt,
+                     long long* ops_by_phase, long long* counts) {
+  Grid g = make_grid(c->n, c->h, c->gamma);
+  const long N = g.N;
+  std::vector<Cnt> U(5 * N), B(3 * N);
+  for (long i = 0; i < 5 * N; ++i) U[i] = Cnt(cons[i]);
+  for (long i = 0; i < 3 * N; ++i) B[i] = Cnt(b[i]);
+  for (int p = 0; p < NPHASE; ++p) g_ops[p] = 0;
+  g_fo = false;
+  const Scheme<Cnt> sc = {c->recon, c->riemann, c->emf, Cnt(c->eta), c->eta != 0.0};
+  StepOut so;
+  step(g, sc, c->fofc_criteria, U, B, dt, so);
+  for (int p = 0; p < NPHASE; ++p) ops_by_phase[p] = g_ops[p];
+  if (counts) { counts[0] = so.flagged[0]; counts[1] = so.flagged[1]; }
+  return NPHASE;
 }
 
 }  // extern "C"

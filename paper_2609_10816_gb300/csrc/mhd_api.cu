@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/mhd.h"
 #include "mhd_device.cuh"
@@ -17,6 +18,13 @@ struct mhd_ctx {
   double* B1[3];
   int seg;
   std::string err;
+  // profiling: launch counts per kernel class, and (when enabled) event pairs per launch
+  long long launches[MHD_K_COUNT];
+  bool prof;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  size_t ev_next;
 };
 
 namespace {
@@ -54,15 +62,46 @@ mhd_status decode(mhd_ctx* c, int scheme, Decoded& d) {
 
 bool state_ok(const mhd_state* s) { return s && s->cons && s->b0 && s->b1 && s->b2; }
 
+cudaEvent_t next_event(mhd_ctx* c) {
+  if (c->ev_next == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_next++];
+}
+
+// Brackets the launches of one kernel class with events when profiling is on.
+struct Timed {
+  mhd_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Timed(mhd_ctx* c_, int cls_, int nlaunch) : c(c_), cls(cls_) {
+    c->launches[cls] += nlaunch;
+    if (c->prof && (a = next_event(c))) cudaEventRecord(a, c->stream);
+  }
+  ~Timed() {
+    if (!a) return;
+    cudaEvent_t b = next_event(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({cls, a, b});
+  }
+};
+
 // one RK stage: prim -> faces -> edges -> update -> flags -> flux correction
 void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc) {
   cudaStream_t st = c->stream;
-  mhd::launch_prim(D, st);
-  for (int dir = 0; dir < 3; ++dir) mhd::launch_face(D, dir, sc.recon, sc.rs, c->seg, st);
-  mhd::launch_edges(D, sc.recon, c->seg, st);
-  mhd::launch_update(D, st);
-  mhd::launch_flag(D, st);
-  if (sc.fofc) mhd::launch_fofc(D, st);
+  { Timed t(c, MHD_K_PRIM, 1); mhd::launch_prim(D, st); }
+  for (int dir = 0; dir < 3; ++dir) {
+    Timed t(c, MHD_K_FACE, 1);
+    mhd::launch_face(D, dir, sc.recon, sc.rs, c->seg, st);
+  }
+  { Timed t(c, MHD_K_EDGE_BT, 3); mhd::launch_edges_bt(D, sc.recon, c->seg, st); }
+  { Timed t(c, MHD_K_EDGE_LR, 3); mhd::launch_edges_lr(D, sc.recon, c->seg, st); }
+  { Timed t(c, MHD_K_UPDATE, 1); mhd::launch_update(D, st); }
+  { Timed t(c, MHD_K_FLAG, 1); mhd::launch_flag(D, st); }
+  if (sc.fofc) { Timed t(c, MHD_K_FOFC, 3); mhd::launch_fofc(D, st); }
 }
 
 }  // namespace
@@ -91,6 +130,9 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   mhd_ctx* c = new mhd_ctx();
   c->stream = (cudaStream_t)cuda_stream;
   c->seg = 64;
+  for (int k = 0; k < MHD_K_COUNT; ++k) c->launches[k] = 0;
+  c->prof = false;
+  c->ev_next = 0;
   mhd::Dev& D = c->base;
   std::memset(&D, 0, sizeof(D));
   D.n[0] = cfg->nx; D.n[1] = cfg->ny; D.n[2] = cfg->nz;
@@ -148,8 +190,39 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
 void mhd_destroy(mhd_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   cudaFree(ctx->scratch);
   delete ctx;
+}
+
+mhd_status mhd_profile(mhd_ctx* ctx, int enable) {
+  if (!ctx) return MHD_ERR_ARG;
+  mhd_status s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  ctx->prof = enable != 0;
+  ctx->recs.clear();
+  ctx->ev_next = 0;
+  return MHD_OK;
+}
+
+mhd_status mhd_profile_read(mhd_ctx* ctx, double* total_ms, long long* launches, int reset) {
+  if (!ctx) return MHD_ERR_ARG;
+  mhd_status s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  if (total_ms) {
+    for (int k = 0; k < MHD_K_COUNT; ++k) total_ms[k] = 0.0;
+    for (const auto& r : ctx->recs) {
+      float ms = 0.f;
+      s = cuda_check(ctx, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+      if (s != MHD_OK) return s;
+      total_ms[r.cls] += ms;
+    }
+  }
+  if (launches)
+    for (int k = 0; k < MHD_K_COUNT; ++k) launches[k] = ctx->launches[k];
+  if (reset)
+    for (int k = 0; k < MHD_K_COUNT; ++k) ctx->launches[k] = 0;
+  return MHD_OK;
 }
 
 mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme, double eta) {
@@ -237,7 +310,10 @@ mhd_status mhd_max_dt(mhd_ctx* ctx, const mhd_state* state, double cfl, double e
                             "cudaMemsetAsync");
   if (s != MHD_OK) return s;
   mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
-  mhd::launch_maxspeed(D, state->cons, B, D.counters + 2, ctx->stream);
+  {
+    Timed t(ctx, MHD_K_MAXSPEED, 1);
+    mhd::launch_maxspeed(D, state->cons, B, D.counters + 2, ctx->stream);
+  }
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
   unsigned long long h = 0;
@@ -262,7 +338,10 @@ mhd_status mhd_divb(mhd_ctx* ctx, const mhd_state* state, double* max_abs_divb, 
                             "cudaMemsetAsync");
   if (s != MHD_OK) return s;
   mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
-  mhd::launch_divb(D, B, D.counters + 2, ctx->stream);
+  {
+    Timed t(ctx, MHD_K_DIVB, 1);
+    mhd::launch_divb(D, B, D.counters + 2, ctx->stream);
+  }
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
   unsigned long long h[2] = {0, 0};

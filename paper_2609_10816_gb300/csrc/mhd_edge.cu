@@ -106,13 +106,17 @@ __global__ void __launch_bounds__(128) k_edge_lr(Dev D, int e, int seg) {
 }
 
 template <int RC>
-static void launch_edges_t(const Dev& d, int seg, cudaStream_t st) {
+static void launch_bt_t(const Dev& d, int seg, cudaStream_t st) {
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int c = (e + 2) % 3;
     const long long th = sweep_threads(d, c, seg);
     k_edge_bt<RC><<<(unsigned)((th + bs - 1) / bs), bs, 0, st>>>(d, e, seg);
   }
+}
+template <int RC>
+static void launch_lr_t(const Dev& d, int seg, cudaStream_t st) {
+  const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3;
     const long long th = sweep_threads(d, a, seg);
@@ -120,12 +124,20 @@ static void launch_edges_t(const Dev& d, int seg, cudaStream_t st) {
   }
 }
 
-void launch_edges(const Dev& d, int recon, int seg, cudaStream_t st) {
+void launch_edges_bt(const Dev& d, int recon, int seg, cudaStream_t st) {
   switch (recon) {
-    case REC_PC: launch_edges_t<REC_PC>(d, seg, st); break;
-    case REC_PLM_MC: launch_edges_t<REC_PLM_MC>(d, seg, st); break;
-    case REC_PLM_MINMOD: launch_edges_t<REC_PLM_MINMOD>(d, seg, st); break;
-    default: launch_edges_t<REC_PPM>(d, seg, st); break;
+    case REC_PC: launch_bt_t<REC_PC>(d, seg, st); break;
+    case REC_PLM_MC: launch_bt_t<REC_PLM_MC>(d, seg, st); break;
+    case REC_PLM_MINMOD: launch_bt_t<REC_PLM_MINMOD>(d, seg, st); break;
+    default: launch_bt_t<REC_PPM>(d, seg, st); break;
+  }
+}
+void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st) {
+  switch (recon) {
+    case REC_PC: launch_lr_t<REC_PC>(d, seg, st); break;
+    case REC_PLM_MC: launch_lr_t<REC_PLM_MC>(d, seg, st); break;
+    case REC_PLM_MINMOD: launch_lr_t<REC_PLM_MINMOD>(d, seg, st); break;
+    default: launch_lr_t<REC_PPM>(d, seg, st); break;
   }
 }
 

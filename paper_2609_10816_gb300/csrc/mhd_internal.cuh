@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/mhd.h"
+
 namespace mhd {
 
 // three device pointers passed by value
@@ -54,7 +56,8 @@ struct Dev {
 // launchers (each enqueues on `st`)
 void launch_prim(const Dev& d, cudaStream_t st);
 void launch_face(const Dev& d, int dir, int recon, int rs, int seg, cudaStream_t st);
-void launch_edges(const Dev& d, int recon, int seg, cudaStream_t st);
+void launch_edges_bt(const Dev& d, int recon, int seg, cudaStream_t st);
+void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_update(const Dev& d, cudaStream_t st);
 void launch_flag(const Dev& d, cudaStream_t st);
 void launch_fofc(const Dev& d, cudaStream_t st);

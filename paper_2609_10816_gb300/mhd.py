@@ -21,6 +21,8 @@ AVG = {"ld04": 0 << 12, "b25b": 1 << 12}
 FOFC_OFF = 1 << 16
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_UNSUPPORTED, ERR_TIMEOUT = range(6)
+KERNELS = ["prim", "face", "edge_bt", "edge_lr", "update", "flag", "fofc", "maxspeed", "divb", "extra"]
+K_COUNT = 16
 _NAMES = ["OK", "ARG", "CUDA", "NONFINITE", "UNSUPPORTED", "TIMEOUT"]
 
 
@@ -77,6 +79,10 @@ def lib():
     L.mhd_last_error.restype = ctypes.c_char_p
     L.mhd_create_error.argtypes = []
     L.mhd_create_error.restype = ctypes.c_char_p
+    L.mhd_profile.argtypes = [vp, ctypes.c_int]
+    L.mhd_profile.restype = ctypes.c_int
+    L.mhd_profile_read.argtypes = [vp, P(d), P(ctypes.c_longlong), ctypes.c_int]
+    L.mhd_profile_read.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -145,6 +151,16 @@ class Context:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._err(lib().mhd_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def profile(self, enable: bool):
+        self._err(lib().mhd_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, reset: bool = False):
+        """{kernel class: (total ms of timed launches, launches)}."""
+        ms = (ctypes.c_double * K_COUNT)()
+        n = (ctypes.c_longlong * K_COUNT)()
+        self._err(lib().mhd_profile_read(self._h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNELS)}
 
     def close(self):
         if getattr(self, "_h", None):
