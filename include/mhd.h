@@ -128,8 +128,30 @@ mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches,
 /* Message of the last failure on ctx ("" if none). Valid until the next call on ctx. */
 const char *mhd_last_error(const mhd_ctx *ctx);
 
-/* Message for a failure of mhd_create or mhd_batch_create, which return no context. */
+/* Message for a failure of a call that returns no context (mhd_create, mhd_step_noalloc). */
 const char *mhd_create_error(void);
+
+/* Largest box (nx * ny * nz) that mhd_step_noalloc accepts. */
+#define MHD_NOALLOC_MAX_CELLS 32768
+
+/* mhd_step without any device allocation, for callers that cannot let a library allocate:
+ * code recorded inside a CUDA stream capture (where cudaMalloc is not allowed), applications
+ * whose memory manager owns all device memory, and loops that cannot afford cudaMalloc's
+ * implicit synchronisation. The paper has no counterpart: this is a deployment variant of
+ * mhd_step, with the same arguments and results, for boxes of at most MHD_NOALLOC_MAX_CELLS
+ * cells and the Q26 EMF compute (FS18/B25a -> MHD_ERR_UNSUPPORTED). Larger boxes are rejected
+ * with MHD_ERR_ARG (message from mhd_create_error) before any device work.
+ *
+ * The step's scratch is one fixed device array (about 14.5 MB) built into libmhd.so; every GPU
+ * that loads the library holds it until the process exits. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with that device current), so make the
+ * first call on each device before any stream capture. All calls share the one array and the
+ * array keeps the last call's contents (the call clears what must start at zero): calls whose
+ * work overlaps on the GPU (other streams, other host threads without ordering) race and give
+ * wrong results. The caller passes inputs and outputs (state, in place) and the stream;
+ * errors as for mhd_step. Asynchronous on `cuda_stream`. */
+mhd_status mhd_step_noalloc(const mhd_config *cfg, const mhd_state *state, double dt, int scheme,
+                            double eta, void *cuda_stream);
 
 #ifdef __cplusplus
 }

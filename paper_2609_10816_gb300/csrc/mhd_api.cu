@@ -106,6 +106,8 @@ void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc) {
 
 }  // namespace
 
+void mhd::set_call_error(const char* msg) { g_create_err = msg; }
+
 extern "C" {
 
 const char* mhd_create_error(void) { return g_create_err.c_str(); }

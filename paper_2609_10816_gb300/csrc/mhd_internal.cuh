@@ -53,6 +53,9 @@ struct Dev {
   int stage;      // 0 or 1 (which counter the flux correction reads)
 };
 
+// message reported by mhd_create_error() for calls that have no context
+void set_call_error(const char* msg);
+
 // launchers (each enqueues on `st`)
 void launch_prim(const Dev& d, cudaStream_t st);
 void launch_face(const Dev& d, int dir, int recon, int rs, int seg, cudaStream_t st);
