@@ -125,6 +125,13 @@ mhd_status mhd_profile(mhd_ctx *ctx, int enable);
  * context was created or the counts were last read with reset != 0. Arrays hold MHD_K_COUNT. */
 mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches, int reset);
 
+/* Self-check of the reciprocal, reciprocal square root and square root that the kernels use in
+ * place of IEEE division and sqrt (hardware approximation + one third-order Newton correction):
+ * on n pseudo-random positive inputs spread over [2^-40, 2^40] it returns in max_rel_err[0..2]
+ * the largest relative differences from CUDA's IEEE 1/x, 1/sqrt(x) and sqrt(x). Synchronous.
+ * The paper has no counterpart. */
+mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
+
 /* Message of the last failure on ctx ("" if none). Valid until the next call on ctx. */
 const char *mhd_last_error(const mhd_ctx *ctx);
 

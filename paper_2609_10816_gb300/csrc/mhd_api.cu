@@ -354,4 +354,22 @@ mhd_status mhd_divb(mhd_ctx* ctx, const mhd_state* state, double* max_abs_divb, 
   return MHD_OK;
 }
 
+mhd_status mhd_math_check(mhd_ctx* ctx, long long n, double* max_rel_err) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!max_rel_err || n < 1 || n > (1LL << 40)) return fail(ctx, MHD_ERR_ARG, "need 1 <= n <= 2^40 and an output");
+  const mhd::Dev& D = ctx->base;
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 3 * sizeof(unsigned long long), ctx->stream),
+                            "cudaMemsetAsync");
+  if (s != MHD_OK) return s;
+  mhd::launch_math_check(n, D.counters + 2, ctx->stream);
+  s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
+  if (s != MHD_OK) return s;
+  unsigned long long h[3] = {0, 0, 0};
+  s = read_counters(ctx, h, 3);
+  if (s != MHD_OK) return s;
+  for (int k = 0; k < 3; ++k) std::memcpy(&max_rel_err[k], &h[k], sizeof(double));
+  return MHD_OK;
+}
+
 }  // extern "C"

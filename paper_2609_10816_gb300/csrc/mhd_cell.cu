@@ -301,6 +301,32 @@ __global__ void __launch_bounds__(256) k_divb(Dev D, Ptr3 Bp, unsigned long long
   block_max_atomic(mb, out + 1);
 }
 
+// relative error of rcp / rsqrt_ / sqrt_ against IEEE division and sqrt on hashed inputs
+__global__ void __launch_bounds__(256) k_math_check(long long n, unsigned long long* out) {
+  const long long i = cell_id();
+  double er = 0.0, es = 0.0, eq = 0.0;
+  if (i < n) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z ^= z >> 31;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 29;
+    const long long mant = (long long)(z & 0x000fffffffffffffull);
+    const long long ex = 1023 - 40 + (long long)((z >> 52) % 81);
+    const double x = dfrom((ex << 52) | mant);
+    const double r0 = 1.0 / x, s0 = sqrt(x), q0 = 1.0 / s0;
+    er = vabs(rcp(x) - r0) / r0;
+    es = vabs(rsqrt_(x) - q0) / q0;
+    eq = vabs(sqrt_(x) - s0) / s0;
+  }
+  block_max_atomic(er, out);
+  block_max_atomic(es, out + 1);
+  block_max_atomic(eq, out + 2);
+}
+
+void launch_math_check(long long n, unsigned long long* out, cudaStream_t st) {
+  k_math_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, out);
+}
+
 static unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 void launch_prim(const Dev& d, cudaStream_t st) { k_prim<<<blocks_for(d.N, 256), 256, 0, st>>>(d); }

@@ -52,7 +52,30 @@ __device__ __forceinline__ double sgnd(double x) {
 __device__ __forceinline__ bool finite_d(double x) {
   return ((dbits(x) >> 52) & 0x7ff) != 0x7ff;
 }
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+// Reciprocal, reciprocal square root and square root without the IEEE divide/sqrt sequences
+// (which cost several FP64 issue slots each). The hardware's approximate reciprocal (about
+// 2^-23 relative error) is refined by one third-order Newton step on f(y) = 1/y - x, i.e. the
+// truncated series y = y0 (1 + e + e^2) with e = 1 - x y0; the approximate reciprocal square
+// root likewise by the series of (1 - e)^(-1/2): y = y0 (1 + e/2 + 3 e^2 / 8), e = 1 - x y0^2.
+// Both leave an error of a few ulp (checked against IEEE division and sqrt by mhd_math_check).
+// Inputs are positive normal numbers on every path that uses them.
+__device__ __forceinline__ double rcp(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+__device__ __forceinline__ double rsqrt_(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x * y, y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
+// sqrt(x) = x / sqrt(x) for x > 0, and 0 for x = 0 (where the product would be 0 * inf)
+__device__ __forceinline__ double sqrt_(double x) {
+  const double r = x * rsqrt_(x);
+  return is_zero(x) ? 0.0 : r;
+}
 
 // ------------------------------------------------------------------------------------------
 // Periodic line of points along one axis
@@ -103,87 +126,96 @@ __device__ __forceinline__ double half_slope_minmod(double dl, double dr) {
 
 template <int R> struct RecPLM {
   static constexpr int LB = 2, LA = 1;
-  double qa, qb, aRprev;  // q[m-1], q[m], upper value of point m-1
-  __device__ __forceinline__ double hs(double dl, double dr) const {
-    return R == REC_PLM_MC ? half_slope_mc(dl, dr) : half_slope_minmod(dl, dr);
+  double qb, dl, aRprev;  // q[m], q[m] - q[m-1], upper value of point m-1
+  __device__ __forceinline__ double hs(double a, double b) const {
+    return R == REC_PLM_MC ? half_slope_mc(a, b) : half_slope_minmod(a, b);
   }
   __device__ __forceinline__ void init(const double* q) {
-    aRprev = q[1] + hs(q[1] - q[0], q[2] - q[1]);
-    qa = q[1];
+    const double e0 = q[1] - q[0], e1 = q[2] - q[1];
+    aRprev = q[1] + hs(e0, e1);
     qb = q[2];
+    dl = e1;
   }
   __device__ __forceinline__ void step(double qn, double& L, double& Rt) {
-    const double h = hs(qb - qa, qn - qb);
+    const double dr = qn - qb;
+    const double h = hs(dl, dr);
     L = aRprev;
     Rt = qb - h;
     aRprev = qb + h;
-    qa = qb;
     qb = qn;
+    dl = dr;
   }
 };
 template <> struct Rec<REC_PLM_MC> : RecPLM<REC_PLM_MC> {};
 template <> struct Rec<REC_PLM_MINMOD> : RecPLM<REC_PLM_MINMOD> {};
 
 // Colella & Woodward 1984: van Leer limited slope (their Eqs. 1.7-1.8), interface value
-// (Eq. 1.6) and monotonicity constraints (Eq. 1.10).
-__device__ __forceinline__ double vl_slope(double qm, double q0, double qp) {
-  const double dl = q0 - qm, dr = qp - q0;
+// (Eq. 1.6) and monotonicity constraints (Eq. 1.10), arranged to reuse the one-sided
+// differences: the slope is carried doubled, dq2 = 2 dq = sgn min(|dl + dr|, 4|dl|, 4|dr|), the
+// interface value between points 0 and 1 is q0 + (q1 - q0)/2 - (dq2_1 - dq2_0)/12, and with
+// s1 = aR - a, s2 = a - aL the constraint quantities are aR - aL = s1 + s2 and
+// 6 (a - (aL + aR)/2) = 3 (s2 - s1), the corrections 3a - 2aR = a - 2 s1, 3a - 2aL = a + 2 s2.
+__device__ __forceinline__ double vl_slope2(double dl, double dr) {
   if (!same_sign(dl, dr)) return 0.0;
-  const double dc = 0.5 * (qp - qm);
-  const double m = pmin(vabs(dc), 2.0 * pmin(vabs(dl), vabs(dr)));
-  return with_sign(m, dc);
+  const double s = dl + dr;
+  const double m = pmin(vabs(s), 4.0 * pmin(vabs(dl), vabs(dr)));
+  return with_sign(m, s);
 }
-__device__ __forceinline__ double ppm_iface(double q0, double q1, double d0, double d1) {
-  return fma(-(d1 - d0), 1.0 / 6.0, 0.5 * (q0 + q1));
+__device__ __forceinline__ double ppm_iface(double q0, double dq, double d20, double d21) {
+  return fma(-(d21 - d20), 1.0 / 12.0, fma(0.5, dq, q0));
 }
 __device__ __forceinline__ void ppm_mono(double a, double& aL, double& aR) {
-  if (!same_sign(aR - a, a - aL)) {
+  const double s1 = aR - a, s2 = a - aL;
+  if (!same_sign(s1, s2)) {
     aL = a;
     aR = a;
     return;
   }
-  const double da = aR - aL;
-  const double a6 = 6.0 * fma(-0.5, aL + aR, a);
+  const double da = s1 + s2;
+  const double a6 = 3.0 * (s2 - s1);
   const double p1 = da * a6, p2 = da * da;
   if (vgt(p1, p2)) {
-    aL = fma(-2.0, aR, 3.0 * a);
+    aL = fma(-2.0, s1, a);
   } else if (vgt(-p2, p1)) {
-    aR = fma(-2.0, aL, 3.0 * a);
+    aR = fma(2.0, s2, a);
   }
 }
 
 template <> struct Rec<REC_PPM> {
   static constexpr int LB = 3, LA = 2;
-  double q0, q1, q2;  // q[m-1], q[m], q[m+1]
-  double d1;          // slope of point m
+  double q1, q2;      // q[m], q[m+1]
+  double dq;          // q[m+1] - q[m]
+  double d1;          // doubled slope of point m
   double f1;          // interface value at m - 1/2
   double aRprev;      // upper value of point m-1
   __device__ __forceinline__ void init(const double* v) {  // v = q[m0-3 .. m0+1]
-    const double da = vl_slope(v[0], v[1], v[2]);
-    const double db = vl_slope(v[1], v[2], v[3]);
-    const double dc = vl_slope(v[2], v[3], v[4]);
-    const double fa = ppm_iface(v[1], v[2], da, db);
-    const double fb = ppm_iface(v[2], v[3], db, dc);
+    const double e0 = v[1] - v[0], e1 = v[2] - v[1], e2 = v[3] - v[2], e3 = v[4] - v[3];
+    const double da = vl_slope2(e0, e1);
+    const double db = vl_slope2(e1, e2);
+    const double dc = vl_slope2(e2, e3);
+    const double fa = ppm_iface(v[1], e1, da, db);
+    const double fb = ppm_iface(v[2], e2, db, dc);
     double aL = fa, aR = fb;
     ppm_mono(v[2], aL, aR);
     aRprev = aR;
-    q0 = v[2];
     q1 = v[3];
     q2 = v[4];
+    dq = e3;
     d1 = dc;
     f1 = fb;
   }
   __device__ __forceinline__ void step(double qn, double& L, double& R) {
-    const double d2 = vl_slope(q1, q2, qn);
-    const double f2 = ppm_iface(q1, q2, d1, d2);
+    const double dn = qn - q2;
+    const double d2 = vl_slope2(dq, dn);
+    const double f2 = ppm_iface(q1, dq, d1, d2);
     double aL = f1, aR = f2;
     ppm_mono(q1, aL, aR);
     L = aRprev;
     R = aL;
     aRprev = aR;
-    q0 = q1;
     q1 = q2;
     q2 = qn;
+    dq = dn;
     d1 = d2;
     f1 = f2;
   }
@@ -230,23 +262,77 @@ __device__ __forceinline__ void phys(const FaceState& s, double bn, double gam, 
   const double sum = fma(b2, rinv, a2);
   double disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
   disc = pmax(disc, 0.0);
-  o.cf = sqrt(0.5 * (sum + sqrt(disc)));
+  o.cf = sqrt_(0.5 * (sum + sqrt_(disc)));
 }
 
+// HLL-type two-state flux; inv = 1 / (ap + am), or 0 when ap + am = 0 (then the left flux).
 __device__ __forceinline__ void two_state(const PhysFlux& L, const PhysFlux& R, double ap,
-                                          double am, double* F) {
-  const double sum = ap + am;
-  if (is_zero(sum)) {
+                                          double am, double inv, bool zero, double* F) {
+  if (zero) {
     for (int v = 0; v < 5; ++v) F[v] = L.F[v];
     return;
   }
-  const double inv = rcp(sum);
-  const double apam = ap * am;
-  for (int v = 0; v < 5; ++v)
-    F[v] = (fma(ap, L.F[v], am * R.F[v]) - apam * (R.U[v] - L.U[v])) * inv;
+  const double wl = ap * inv, wr = am * inv, wd = ap * am * inv;
+  for (int v = 0; v < 5; ++v) F[v] = fma(wl, L.F[v], fma(wr, R.F[v], -wd * (R.U[v] - L.U[v])));
 }
 
-// Miyoshi & Kusano (2005) HLLD without the Minoshima fixes.
+// Star state on one side of the contact (MK05 Eqs. 43-48).
+struct Star {
+  double rs, vs, ws, bys, bzs, es;
+};
+__device__ __forceinline__ void star_state(const FaceState& q, const PhysFlux& ph, double S, double SM,
+                                           double ptS, double bn, double bn2, Star& o) {
+  const double su = S - q.u;
+  const double ssm = S - SM;
+  const double ssminv = rcp(ssm);
+  const double rsu = q.rho * su;
+  o.rs = rsu * ssminv;
+  const double dd = fma(rsu, ssm, -bn2);
+  const double scale = fma(rsu, su, bn2);
+  if (!vgt(vabs(dd), 1e-12 * scale)) {  // degenerate: no tangential change across the fast wave
+    o.vs = q.v;
+    o.ws = q.w;
+    o.bys = q.by;
+    o.bzs = q.bz;
+  } else {
+    const double ddinv = rcp(dd);
+    const double cv = bn * (SM - q.u) * ddinv;
+    const double cb = fma(rsu, su, -bn2) * ddinv;
+    o.vs = fma(-q.by, cv, q.v);
+    o.ws = fma(-q.bz, cv, q.w);
+    o.bys = q.by * cb;
+    o.bzs = q.bz * cb;
+  }
+  const double vb = fma(q.u, bn, fma(q.v, q.by, q.w * q.bz));
+  const double vbs = fma(SM, bn, fma(o.vs, o.bys, o.ws * o.bzs));
+  o.es = (fma(su, ph.e, -ph.pt * q.u) + fma(ptS, SM, bn * (vb - vbs))) * ssminv;
+}
+
+__device__ __forceinline__ FaceState pick(bool left, const FaceState& a, const FaceState& b) {
+  FaceState r;
+  r.rho = left ? a.rho : b.rho;
+  r.u = left ? a.u : b.u;
+  r.v = left ? a.v : b.v;
+  r.w = left ? a.w : b.w;
+  r.p = left ? a.p : b.p;
+  r.by = left ? a.by : b.by;
+  r.bz = left ? a.bz : b.bz;
+  return r;
+}
+__device__ __forceinline__ void pick(bool left, const PhysFlux& a, const PhysFlux& b, PhysFlux& r) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    r.U[v] = left ? a.U[v] : b.U[v];
+    r.F[v] = left ? a.F[v] : b.F[v];
+  }
+  r.pt = left ? a.pt : b.pt;
+  r.e = left ? a.e : b.e;
+}
+
+// Miyoshi & Kusano (2005) HLLD without the Minoshima fixes. The face x/t = 0 lies on the side of
+// the contact given by sgn(S_M); only that side's star state is formed, and the other side's star
+// state and the double-star state (MK05 Eqs. 49-63) only when the face lies inside that side's
+// rotational wave. Same values as forming all four states and selecting.
 __device__ __forceinline__ void hlld(const FaceState& sl, const FaceState& sr, double bn,
                                      const PhysFlux& L, const PhysFlux& R, double SL, double SR,
                                      double* F) {
@@ -261,93 +347,61 @@ __device__ __forceinline__ void hlld(const FaceState& sl, const FaceState& sr, d
   const double sluL = SL - sl.u, sruR = SR - sr.u;
   const double mL = sluL * sl.rho, mR = sruR * sr.rho;  // mass fluxes through the outer waves
   const double dinv = rcp(mR - mL);
-  const double SM = ((mR * sr.u - mL * sl.u) + (L.pt - R.pt)) * dinv;
-  const double ptS = (mR * L.pt - mL * R.pt + mL * mR * (sr.u - sl.u)) * dinv;
+  const double SM = ((mR * sr.u - mL * sl.u) + (L.pt - R.pt)) * dinv;  // MK05 Eq. 38
+  const double ptS = (mR * L.pt - mL * R.pt + mL * mR * (sr.u - sl.u)) * dinv;  // MK05 Eq. 41
   const double bn2 = bn * bn;
-  const FaceState* st[2] = {&sl, &sr};
-  const PhysFlux* ph[2] = {&L, &R};
-  const double S[2] = {SL, SR};
-  double Us[2][5], rS[2], vS[2], wS[2], byS[2], bzS[2];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const FaceState& q = *st[s];
-    const double su = S[s] - q.u;
-    const double ssm = S[s] - SM;
-    const double ssminv = rcp(ssm);
-    const double rsu = q.rho * su;
-    const double rs = rsu * ssminv;
-    const double dd = fma(rsu, ssm, -bn2);
-    const double scale = fma(rsu, su, bn2);
-    double vs, ws, bys, bzs;
-    if (!vgt(vabs(dd), 1e-12 * scale)) {
-      vs = q.v;
-      ws = q.w;
-      bys = q.by;
-      bzs = q.bz;
-    } else {
-      const double ddinv = rcp(dd);
-      const double cv = bn * (SM - q.u) * ddinv;
-      const double cb = fma(rsu, su, -bn2) * ddinv;
-      vs = fma(-q.by, cv, q.v);
-      ws = fma(-q.bz, cv, q.w);
-      bys = q.by * cb;
-      bzs = q.bz * cb;
-    }
-    const double vb = fma(q.u, bn, fma(q.v, q.by, q.w * q.bz));
-    const double vbs = fma(SM, bn, fma(vs, bys, ws * bzs));
-    const double es = (fma(su, ph[s]->e, -ph[s]->pt * q.u) + fma(ptS, SM, bn * (vb - vbs))) * ssminv;
-    rS[s] = rs;
-    vS[s] = vs;
-    wS[s] = ws;
-    byS[s] = bys;
-    bzS[s] = bzs;
-    Us[s][0] = rs;
-    Us[s][1] = rs * SM;
-    Us[s][2] = rs * vs;
-    Us[s][3] = rs * ws;
-    Us[s][4] = es;
-  }
-  const double sqL = sqrt(rS[0]), sqR = sqrt(rS[1]);
   const double abn = vabs(bn);
-  const double SsL = SM - abn * rcp(sqL);
-  const double SsR = SM + abn * rcp(sqR);
-  const double sb = sgnd(bn);
-  const double inv = rcp(sqL + sqR);
-  const double vss = fma(sqL, vS[0], fma(sqR, vS[1], (byS[1] - byS[0]) * sb)) * inv;
-  const double wss = fma(sqL, wS[0], fma(sqR, wS[1], (bzS[1] - bzS[0]) * sb)) * inv;
-  const double sLR = sqL * sqR;
-  const double byss = fma(sqL, byS[1], fma(sqR, byS[0], sLR * (vS[1] - vS[0]) * sb)) * inv;
-  const double bzss = fma(sqL, bzS[1], fma(sqR, bzS[0], sLR * (wS[1] - wS[0]) * sb)) * inv;
-  const double vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
-  // choose the region of the fan that contains the face (x/t = 0)
-  int side;     // 0 left, 1 right
-  bool dstar;   // double-star region
-  if (ge0(SsL)) { side = 0; dstar = false; }
-  else if (ge0(SM)) { side = 0; dstar = true; }
-  else if (ge0(SsR)) { side = 1; dstar = true; }
-  else { side = 1; dstar = false; }
-  const PhysFlux& P = side ? R : L;
-  const double Sx = side ? SR : SL;
+  const bool left = ge0(SM);
+  const FaceState q = pick(left, sl, sr);
+  PhysFlux P;
+  pick(left, L, R, P);
+  const double S = left ? SL : SR;
+  Star a;
+  star_state(q, P, S, SM, ptS, bn, bn2, a);
+  const double isqa = rsqrt_(a.rs);
+  const double Ss = left ? SM - abn * isqa : SM + abn * isqa;  // MK05 Eq. 51
+  const double Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
   double Fs[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) Fs[v] = fma(Sx, Us[side][v] - P.U[v], P.F[v]);
+  for (int v = 0; v < 5; ++v) Fs[v] = fma(S, Usa[v] - P.U[v], P.F[v]);
+  const bool dstar = left ? !ge0(Ss) : ge0(Ss);
   if (!dstar) {
     for (int v = 0; v < 5; ++v) F[v] = Fs[v];
     return;
   }
-  const double sq = side ? sqR : sqL;
-  const double sgn_side = side ? 1.0 : -1.0;
-  const double vbs = fma(SM, bn, fma(vS[side], byS[side], wS[side] * bzS[side]));
-  const double rs = rS[side];
+  // inside the rotational wave of this side: the other side's star state and the double star
+  const FaceState qo = pick(!left, sl, sr);
+  PhysFlux Po;
+  pick(!left, L, R, Po);
+  Star b;
+  star_state(qo, Po, left ? SR : SL, SM, ptS, bn, bn2, b);
+  const double isqb = rsqrt_(b.rs);
+  const double rsL = left ? a.rs : b.rs, rsR = left ? b.rs : a.rs;
+  const double vsL = left ? a.vs : b.vs, vsR = left ? b.vs : a.vs;
+  const double wsL = left ? a.ws : b.ws, wsR = left ? b.ws : a.ws;
+  const double bysL = left ? a.bys : b.bys, bysR = left ? b.bys : a.bys;
+  const double bzsL = left ? a.bzs : b.bzs, bzsR = left ? b.bzs : a.bzs;
+  const double iL = left ? isqa : isqb, iR = left ? isqb : isqa;
+  const double sqL = rsL * iL, sqR = rsR * iR;
+  const double sb = sgnd(bn);
+  const double inv = rcp(sqL + sqR);
+  const double vss = fma(sqL, vsL, fma(sqR, vsR, (bysR - bysL) * sb)) * inv;
+  const double wss = fma(sqL, wsL, fma(sqR, wsR, (bzsR - bzsL) * sb)) * inv;
+  const double sLR = sqL * sqR;
+  const double byss = fma(sqL, bysR, fma(sqR, bysL, sLR * (vsR - vsL) * sb)) * inv;
+  const double bzss = fma(sqL, bzsR, fma(sqR, bzsL, sLR * (wsR - wsL) * sb)) * inv;
+  const double vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
+  const double sq = left ? sqL : sqR;
+  const double sgn_side = left ? -1.0 : 1.0;
+  const double vbs = fma(SM, bn, fma(a.vs, a.bys, a.ws * a.bzs));
   double Uss[5];
-  Uss[0] = rs;
-  Uss[1] = rs * SM;
-  Uss[2] = rs * vss;
-  Uss[3] = rs * wss;
-  Uss[4] = fma(sgn_side * sq, (vbs - vbss) * sb, Us[side][4]);
-  const double Ss = side ? SsR : SsL;
+  Uss[0] = a.rs;
+  Uss[1] = a.rs * SM;
+  Uss[2] = a.rs * vss;
+  Uss[3] = a.rs * wss;
+  Uss[4] = fma(sgn_side * sq, (vbs - vbss) * sb, a.es);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = fma(Ss, Uss[v] - Us[side][v], Fs[v]);
+  for (int v = 0; v < 5; ++v) F[v] = fma(Ss, Uss[v] - Usa[v], Fs[v]);
 }
 
 // Full face solve: flux of {rho, m_n, m_t1, m_t2, e}, alpha+/-, and the Q26 face velocity.
@@ -358,27 +412,29 @@ __device__ __forceinline__ void riemann(const FaceState& sl, const FaceState& sr
   PhysFlux L, R;
   phys(sl, bn, gam, gm1inv, L);
   phys(sr, bn, gam, gm1inv, R);
+  double SL = 0.0, SR = 0.0;
   if (RS == RS_LLF) {
     const double a = pmax(vabs(sl.u) + L.cf, vabs(sr.u) + R.cf);
     ap = a;
     am = a;
-    two_state(L, R, ap, am, F);
   } else {
     // Eq. (alpha-pm) = MK05 Eq. 67 speeds
     const double cmax = pmax(L.cf, R.cf);
     const double umax = vmax(sl.u, sr.u), umin = vmin(sl.u, sr.u);
-    const double SR = umax + cmax;
-    const double SL = umin - cmax;
+    SR = umax + cmax;
+    SL = umin - cmax;
     ap = vmax(0.0, SR);
     am = vmax(0.0, cmax - umin);
-    if (RS == RS_HLL)
-      two_state(L, R, ap, am, F);
-    else
-      hlld(sl, sr, bn, L, R, SL, SR, F);
   }
-  // Eq. (q26-facevel)
   const double sum = ap + am;
-  ustar = is_zero(sum) ? sl.u : fma(ap, sl.u, am * sr.u) * rcp(sum);
+  const bool zero = is_zero(sum);
+  const double inv = zero ? 0.0 : rcp(sum);
+  if (RS == RS_HLLD)
+    hlld(sl, sr, bn, L, R, SL, SR, F);
+  else
+    two_state(L, R, ap, am, inv, zero, F);
+  // Eq. (q26-facevel)
+  ustar = zero ? sl.u : fma(ap, sl.u, am * sr.u) * inv;
 }
 
 }  // namespace mhd

@@ -66,5 +66,6 @@ void launch_flag(const Dev& d, cudaStream_t st);
 void launch_fofc(const Dev& d, cudaStream_t st);
 void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st);
 void launch_divb(const Dev& d, Ptr3 B, unsigned long long* out, cudaStream_t st);
+void launch_math_check(long long n, unsigned long long* out, cudaStream_t st);
 
 }  // namespace mhd

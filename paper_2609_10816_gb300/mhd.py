@@ -79,6 +79,8 @@ def lib():
     L.mhd_last_error.restype = ctypes.c_char_p
     L.mhd_create_error.argtypes = []
     L.mhd_create_error.restype = ctypes.c_char_p
+    L.mhd_math_check.argtypes = [vp, ctypes.c_longlong, P(d)]
+    L.mhd_math_check.restype = ctypes.c_int
     L.mhd_profile.argtypes = [vp, ctypes.c_int]
     L.mhd_profile.restype = ctypes.c_int
     L.mhd_profile_read.argtypes = [vp, P(d), P(ctypes.c_longlong), ctypes.c_int]
@@ -151,6 +153,12 @@ class Context:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._err(lib().mhd_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def math_check(self, n: int = 1 << 22):
+        """Largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE."""
+        out = (ctypes.c_double * 3)()
+        self._err(lib().mhd_math_check(self._h, int(n), out))
+        return tuple(out)
 
     def profile(self, enable: bool):
         self._err(lib().mhd_profile(self._h, 1 if enable else 0))

@@ -106,3 +106,10 @@ def test_max_dt_and_divb(gpu_lib):
     mdo, mbo = oracle.divb(cfg, b)
     assert mb == mbo
     assert abs(md - mdo) <= 1e-12 * mbo / min(info["h"])
+
+
+def test_fast_reciprocal_and_sqrt_against_ieee(gpu_lib):
+    """The kernels' reciprocal / rsqrt / sqrt stay within a few ulp of CUDA's IEEE results."""
+    ctx = mhd.Context((4, 4, 4), (1, 1, 1))
+    er, es, eq = ctx.math_check(1 << 22)
+    assert er <= 4 * 2.0**-53 and es <= 4 * 2.0**-53 and eq <= 4 * 2.0**-53, (er, es, eq)
