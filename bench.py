@@ -178,6 +178,7 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="box edge of the timed workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--q26-only", action="store_true", help="skip the FS18 / B25a comparison runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -256,6 +257,29 @@ def main():
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] * (N / tr["cells"]) if tr and tr.get("src") == kernel_src_hash() else None
     launches_timed = sum(v[1] for v in prof.values())
+
+    # ---- the comparison EMF compute schemes on the same workload (Sec. 3.6) -----------------
+    forms = {"plain_q26": value}
+    if not args.q26_only:
+        for emf in ("fs18", "b25a"):
+            sch_e = mhd.scheme("ppm", "hlld", emf)
+            st_e = mhd.to_device(cons, b, dev)
+            for _ in range(2):
+                ctx.step(st_e, ctx.max_dt(st_e, 0.3), sch_e)
+            barrier()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(args.steps):
+                ctx.step(st_e, ctx.max_dt(st_e, 0.3), sch_e)
+            g1.record(stream)
+            barrier()
+            ms_e = g0.elapsed_time(g1)
+            if dist is not None:
+                t = torch.tensor([ms_e], device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ms_e = float(t.item())
+            forms[f"plain_{emf}"] = world * N * args.steps / (ms_e / 1e3)
+            del st_e
 
     # ---- end to end through the C ABI with host buffers --------------------------------------
     cons_h = torch.from_numpy(cons).pin_memory()
@@ -338,7 +362,7 @@ def main():
         "gpu_launches": launches_timed,
         "clocks": clocks,
         "checks": {"fofc_flagged_last_step": [s1, s2], "max_divb_dx_over_b": md * info["h"][0] / mb},
-        "forms": {"plain_q26": value},
+        "forms": forms,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -97,7 +97,7 @@ void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc) {
     Timed t(c, MHD_K_FACE, 1);
     mhd::launch_face(D, dir, sc.recon, sc.rs, c->seg, st);
   }
-  { Timed t(c, MHD_K_EDGE_BT, 3); mhd::launch_edges_bt(D, sc.recon, c->seg, st); }
+  { Timed t(c, MHD_K_EDGE_BT, sc.emf == mhd::EMF_B25A ? 9 : 3); mhd::launch_edges_bt(D, sc.recon, c->seg, st); }
   { Timed t(c, MHD_K_EDGE_LR, 3); mhd::launch_edges_lr(D, sc.recon, c->seg, st); }
   { Timed t(c, MHD_K_UPDATE, 1); mhd::launch_update(D, st); }
   { Timed t(c, MHD_K_FLAG, 1); mhd::launch_flag(D, st); }
@@ -236,7 +236,6 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
   Decoded sc;
   mhd_status s = decode(ctx, scheme, sc);
   if (s != MHD_OK) return s;
-  if (sc.emf != mhd::EMF_Q26) return fail(ctx, MHD_ERR_UNSUPPORTED, "EMF compute scheme not built");
 
   mhd::Dev D = ctx->base;
   const long long N = D.N;
