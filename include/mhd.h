@@ -160,6 +160,63 @@ const char *mhd_create_error(void);
 mhd_status mhd_step_noalloc(const mhd_config *cfg, const mhd_state *state, double dt, int scheme,
                             double eta, void *cuda_stream);
 
+/* ---- batched form: many uneven periodic patches advanced together ----------------------
+ * A batch is a list of independent triply periodic patches of sizes dims[3p..3p+2] = (nx, ny, nz)
+ * and common cell width h (one refinement level of an AMR hierarchy, each patch its own periodic
+ * box). One step advances every patch by the same dt = cfl h / (max over all cells of all patches
+ * of the CFL signal speed, Eq. resistivity:cfl), computed on the device. Each RK stage runs as one
+ * persistent cooperative launch over all patches (grid-wide barriers with a bounded wait), and
+ * the whole step is captured once as a CUDA graph and replayed while the state arrays, scheme,
+ * eta and cfl stay the same. The batched step supports the Q26 EMF compute (FS18 and B25a ->
+ * MHD_ERR_UNSUPPORTED). */
+typedef struct mhd_batch mhd_batch;
+
+/* Batch state, patch-major, all device memory: patch p (cell offset off[p] from
+ * mhd_batch_offsets) holds cons at cons + 5 off[p] as [5][nz][ny][nx] and its face fields at
+ * b + 3 off[p] as [3][nz][ny][nx] (b0, b1, b2 of the patch, same layout as mhd_state). */
+typedef struct {
+  double *cons;
+  double *b;
+} mhd_batch_state;
+
+/* Create a batch of npatch patches (dims: 3 ints per patch, each >= 1) with cell width h > 0.
+ * Allocates about 55 doubles of scratch per cell. Errors: message from mhd_batch_last_error(NULL). */
+mhd_status mhd_batch_create(const int *dims, int npatch, double h, double gamma, void *cuda_stream,
+                            mhd_batch **out);
+void mhd_batch_destroy(mhd_batch *batch);
+
+/* cell_offsets[0..npatch]: first cell of each patch in schedule-independent patch order, and the total. */
+mhd_status mhd_batch_offsets(const mhd_batch *batch, long long *cell_offsets);
+
+/* One step of every patch in place (see above). Asynchronous; the first call for a state, scheme,
+ * eta and cfl captures the graph. */
+mhd_status mhd_batch_step(mhd_batch *batch, const mhd_batch_state *state, double cfl, int scheme, double eta);
+
+/* dt of the last step (synchronous); MHD_ERR_TIMEOUT if a grid barrier gave up waiting,
+ * MHD_ERR_NONFINITE if the signal speed was not finite (then no step was taken). */
+mhd_status mhd_batch_last_dt(mhd_batch *batch, double *dt);
+
+/* Flagged cells of the last step's two stages, summed over patches (synchronous). */
+mhd_status mhd_batch_stats(mhd_batch *batch, long long *fofc_cells_stage1, long long *fofc_cells_stage2);
+
+/* Schedule of the persistent stage kernel: sweep segment length seg (points per thread), patch
+ * order (0 as given, 1 largest first), CTAs per SM (0 = as many as fit), and whether steps are
+ * captured and replayed as a CUDA graph. */
+mhd_status mhd_batch_set_schedule(mhd_batch *batch, int seg, int order, int blocks_per_sm, int use_graph);
+
+/* Autotuner: times one step for every candidate schedule (seg in {16, 32, 64, 128}, both orders,
+ * 1 .. max CTAs per SM) on a scratch copy of `state` (left unchanged; the copy is allocated and
+ * freed here), keeps the fastest and returns it. */
+mhd_status mhd_batch_tune(mhd_batch *batch, const mhd_batch_state *state, double cfl, int scheme, double eta,
+                          int *seg, int *order, int *blocks_per_sm);
+
+/* Test hook for the bounded barrier: every grid barrier waits for extra_blocks blocks more than
+ * were launched and gives up after spin_limit polls (~100 ns each), so the next step ends with
+ * MHD_ERR_TIMEOUT from mhd_batch_last_dt; (0, 1 << 25) restores normal operation. */
+mhd_status mhd_batch_test_barrier(mhd_batch *batch, int extra_blocks, long long spin_limit);
+
+const char *mhd_batch_last_error(const mhd_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

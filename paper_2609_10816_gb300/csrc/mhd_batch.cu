@@ -1,0 +1,727 @@
+// mhd_batch.cu -- many uneven periodic patches advanced together (the batched form of the step).
+//
+// Each stage of the step runs as ONE persistent cooperative launch: its blocks walk, phase after
+// phase, work lists that span every patch (cells for the per-cell phases, line segments of the
+// sweeps for the face and edge phases), separated by a grid-wide barrier of the library's own
+// with a bounded wait. The CFL reduction and the time step stay on the device, so one step
+// (reduction, dt, stage 1, stage 2, copy back) is captured once as a CUDA graph and replayed.
+// Patch order, sweep segment length and CTAs per SM form the schedule that mhd_batch_tune picks
+// by timing candidates.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "mhd_cell.cuh"
+#include "mhd_edge.cuh"
+#include "mhd_face.cuh"
+
+namespace mhd {
+
+struct BatchDev {
+  const Dev* patches;             // per-patch parameters of this stage, [npatch]
+  const int* order;               // patch visited at schedule position k, [npatch]
+  const long long* cell_pref;     // [npatch + 1] cells before schedule position k
+  const long long* sweep_pref;    // [3][npatch + 1] sweep segments along dir before position k
+  int npatch;
+  int seg;
+  int stage;
+  int fofc;
+  unsigned* barrier;              // [0] arrivals, [1] generation
+  unsigned long long* counters;   // [0] stage-1 flags, [1] stage-2 flags, [2] max speed, [7] error
+  long long spin_limit;           // bounded wait per barrier (iterations of ~100 ns)
+  int barrier_extra;              // test hook: wait for this many blocks more than launched
+};
+
+// position k with pref[k] <= i < pref[k + 1]
+__device__ __forceinline__ int find_pos(const long long* pref, int n, long long i) {
+  int lo = 0, hi = n;  // invariant pref[lo] <= i < pref[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pref[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Grid-wide barrier with a bounded wait: false (and the error flag set) if the other blocks did
+// not all arrive within the limit; the caller then leaves the kernel.
+__device__ bool grid_sync(const BatchDev& B) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned expected = gridDim.x + (unsigned)B.barrier_extra;
+    volatile unsigned* vgen = B.barrier + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(B.barrier, 1u);
+    int ok = 1;
+    if (arrived == expected - 1) {
+      atomicExch(B.barrier, 0u);
+      __threadfence();
+      atomicAdd(B.barrier + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > B.spin_limit || *(volatile unsigned long long*)(B.counters + 7)) {
+          ok = 0;
+          atomicExch(B.counters + 7, 1ull);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int RC, int RS>
+__global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ncell = B.cell_pref[B.npatch];
+  // cons -> prim
+  for (long long i = t0; i < ncell; i += nth) {
+    const int k = find_pos(B.cell_pref, B.npatch, i);
+    const Dev& D = B.patches[B.order[k]];
+    prim_cell(D, i - B.cell_pref[k]);
+  }
+  if (!grid_sync(B)) return;
+  // face sweeps along each direction
+  for (int dir = 0; dir < 3; ++dir) {
+    const long long* pref = B.sweep_pref + dir * (B.npatch + 1);
+    for (long long i = t0; i < pref[B.npatch]; i += nth) {
+      const int k = find_pos(pref, B.npatch, i);
+      const Dev& D = B.patches[B.order[k]];
+      Line ln;
+      int m0, m1;
+      if (sweep_line_at(D, dir, B.seg, i - pref[k], ln, m0, m1)) face_seg<RC, RS>(D, dir, ln, m0, m1);
+    }
+  }
+  if (!grid_sync(B)) return;
+  // a-face quantities to e-edges (lines along c = e + 2)
+  for (int e = 0; e < 3; ++e) {
+    const int dir = (e + 2) % 3;
+    const long long* pref = B.sweep_pref + dir * (B.npatch + 1);
+    for (long long i = t0; i < pref[B.npatch]; i += nth) {
+      const int k = find_pos(pref, B.npatch, i);
+      const Dev& D = B.patches[B.order[k]];
+      Line ln;
+      int m0, m1;
+      if (sweep_line_at(D, dir, B.seg, i - pref[k], ln, m0, m1)) edge_bt_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
+    }
+  }
+  if (!grid_sync(B)) return;
+  // c-face quantities to e-edges (lines along a = e + 1) and the edge EMFs
+  for (int e = 0; e < 3; ++e) {
+    const int dir = (e + 1) % 3;
+    const long long* pref = B.sweep_pref + dir * (B.npatch + 1);
+    for (long long i = t0; i < pref[B.npatch]; i += nth) {
+      const int k = find_pos(pref, B.npatch, i);
+      const Dev& D = B.patches[B.order[k]];
+      Line ln;
+      int m0, m1;
+      if (sweep_line_at(D, dir, B.seg, i - pref[k], ln, m0, m1)) edge_lr_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
+    }
+  }
+  if (!grid_sync(B)) return;
+  // update
+  for (long long i = t0; i < ncell; i += nth) {
+    const int k = find_pos(B.cell_pref, B.npatch, i);
+    update_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
+  }
+  if (!grid_sync(B)) return;
+  // validity flags (every lane of a warp runs the same number of iterations for the ballot)
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += nth) {
+    const long long i = base + threadIdx.x;
+    bool f = false;
+    int k = 0;
+    if (i < ncell) {
+      k = find_pos(B.cell_pref, B.npatch, i);
+      f = flag_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&B.counters[B.stage], (unsigned long long)__popc(bal));
+  }
+  if (!B.fofc) return;
+  if (!grid_sync(B)) return;
+  if (*(volatile unsigned long long*)(B.counters + B.stage) == 0) return;  // uniform over the grid
+  for (long long i = t0; i < ncell; i += nth) {
+    const int k = find_pos(B.cell_pref, B.npatch, i);
+    const Dev& D = B.patches[B.order[k]];
+    fo_faces_cell(D, i - B.cell_pref[k]);
+    fo_edges_cell(D, i - B.cell_pref[k]);
+  }
+  if (!grid_sync(B)) return;
+  for (long long i = t0; i < ncell; i += nth) {
+    const int k = find_pos(B.cell_pref, B.npatch, i);
+    fo_recompute_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
+  }
+}
+
+// max over all cells of all patches of the CFL signal speed (Sec. 2.4)
+__global__ void __launch_bounds__(256) k_batch_maxspeed(BatchDev B) {
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long ncell = B.cell_pref[B.npatch];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += nth) {
+    const int k = find_pos(B.cell_pref, B.npatch, i);
+    const Dev& D = B.patches[B.order[k]];
+    const long long X = i - B.cell_pref[k];
+    double w[8];
+    prim_of(D, D.U0, D.B0, X, w);
+    const double hmin = fmin(D.h[0], fmin(D.h[1], D.h[2]));
+    const double rinv = 1.0 / w[0];
+    const double a2 = D.gam * w[4] * rinv;
+    const double b2 = fma(w[5], w[5], fma(w[6], w[6], w[7] * w[7]));
+    const double sum = fma(b2, rinv, a2);
+    for (int d = 0; d < 3; ++d) {
+      const double bn2 = w[5 + d] * w[5 + d];
+      const double disc = pmax(fma(sum, sum, -4.0 * (a2 * bn2 * rinv)), 0.0);
+      const double cf = sqrt(0.5 * (sum + sqrt(disc)));
+      const double v = (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]);
+      s = finite_d(v) ? pmax(s, v) : __longlong_as_double(0x7ff0000000000000LL);
+    }
+  }
+  // block max then one atomic
+  unsigned long long bits = (unsigned long long)dbits(s);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = t > bits ? t : bits;
+  }
+  __shared__ unsigned long long sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = bits;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    bits = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, bits, o);
+      bits = t > bits ? t : bits;
+    }
+    if (threadIdx.x == 0) atomicMax(B.counters + 2, bits);
+  }
+}
+
+// dt = cfl hmin / max(smax, 2 eta / hmin), written into both stages' patch parameters and out
+__global__ void k_batch_set_dt(Dev* p0, Dev* p1, int npatch, const unsigned long long* smax_bits, double cfl,
+                               double eta, double hmin, double* dt_out, unsigned long long* err) {
+  double smax = __longlong_as_double((long long)*smax_bits);
+  smax = fmax(smax, 2.0 * eta / hmin);
+  double dt = cfl * hmin / smax;
+  if (!(dt > 0.0) || !finite_d(dt)) {  // non-finite speed: keep the step well defined, flag it
+    dt = 0.0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err + 1, 1ull);
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npatch; k += gridDim.x * blockDim.x) {
+    p0[k].dt = dt;
+    p1[k].dt = dt;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dt_out = dt;
+}
+
+typedef void (*StageKernel)(BatchDev);
+
+template <int RC>
+static StageKernel pick_rs(int rs) {
+  switch (rs) {
+    case RS_HLL: return k_batch_stage<RC, RS_HLL>;
+    case RS_HLLD: return k_batch_stage<RC, RS_HLLD>;
+    default: return k_batch_stage<RC, RS_LLF>;
+  }
+}
+static StageKernel stage_kernel(int recon, int rs) {
+  switch (recon) {
+    case REC_PC: return pick_rs<REC_PC>(rs);
+    case REC_PLM_MC: return pick_rs<REC_PLM_MC>(rs);
+    case REC_PLM_MINMOD: return pick_rs<REC_PLM_MINMOD>(rs);
+    default: return pick_rs<REC_PPM>(rs);
+  }
+}
+
+}  // namespace mhd
+
+// ------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------
+struct mhd_batch {
+  int npatch;
+  std::vector<int> dims;          // 3 per patch
+  std::vector<long long> off;     // cell offsets, npatch + 1
+  long long ncell;
+  double h, gamma;
+  cudaStream_t stream;
+  cudaStream_t cap;               // private stream the step graph is captured on
+  int nsm;
+  std::string err;
+  // device memory (one allocation)
+  void* mem;
+  double* U1;                     // [patch][5][N_p]
+  double* B1;                     // [patch][3][N_p]
+  double* scratch;                // [patch][47][N_p]: P 8, F 15, Ap/Am/Us 9, Epart 12, E 3
+  unsigned char* flag;
+  unsigned long long* counters;   // 8
+  unsigned* barrier;              // 2
+  double* dt_dev;
+  mhd::Dev* pdev[2];              // per-patch parameters per stage
+  int* order_dev;
+  long long* cell_pref_dev;
+  long long* sweep_pref_dev;      // 3 * (npatch + 1)
+  // schedule
+  int seg, order_kind, blocks_per_sm, use_graph;
+  long long spin_limit;
+  int barrier_extra;
+  // what the current parameters / graph were built for
+  const double* built_cons;
+  const double* built_b;
+  int built_scheme;
+  double built_eta, built_cfl;
+  bool params_ok;
+  cudaGraphExec_t graph;
+  bool graph_ok;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_err;
+
+mhd_status bfail(mhd_batch* b, mhd_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+mhd_status bcuda(mhd_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MHD_OK;
+  return bfail(b, MHD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void drop_graph(mhd_batch* b) {
+  if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+  b->graph_ok = false;
+}
+
+// schedule order of patches and the prefix tables of cells and sweep segments
+mhd_status upload_schedule(mhd_batch* b) {
+  const int np = b->npatch;
+  std::vector<int> order(np);
+  std::iota(order.begin(), order.end(), 0);
+  if (b->order_kind == 1) {  // largest patches first
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return b->off[x + 1] - b->off[x] > b->off[y + 1] - b->off[y];
+    });
+  }
+  std::vector<long long> cp(np + 1, 0), sp(3 * (np + 1), 0);
+  for (int k = 0; k < np; ++k) {
+    const int p = order[k];
+    const int* n = &b->dims[3 * p];
+    cp[k + 1] = cp[k] + (long long)n[0] * n[1] * n[2];
+    for (int d = 0; d < 3; ++d) {
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const long long segs = (n[d] + b->seg - 1) / b->seg;
+      sp[d * (np + 1) + k + 1] = sp[d * (np + 1) + k] + (long long)n[t1] * n[t2] * segs;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(b->order_dev, order.data(), np * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->cell_pref_dev, cp.data(), (np + 1) * sizeof(long long), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->sweep_pref_dev, sp.data(), 3 * (np + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bcuda(b, e, "schedule upload");
+}
+
+// per-patch stage parameters for a state, scheme and eta
+mhd_status upload_params(mhd_batch* b, const mhd_batch_state* s, int scheme, double eta) {
+  const int np = b->npatch;
+  std::vector<mhd::Dev> d0(np), d1(np);
+  const int recon = scheme & 0xf;
+  (void)recon;
+  for (int p = 0; p < np; ++p) {
+    mhd::Dev D;
+    std::memset(&D, 0, sizeof(D));
+    const int* n = &b->dims[3 * p];
+    const long long N = (long long)n[0] * n[1] * n[2];
+    const long long o = b->off[p];
+    D.n[0] = n[0]; D.n[1] = n[1]; D.n[2] = n[2];
+    D.N = N;
+    D.stride[0] = 1; D.stride[1] = n[0]; D.stride[2] = (long long)n[0] * n[1];
+    for (int d = 0; d < 3; ++d) { D.h[d] = b->h; D.hinv[d] = 1.0 / b->h; }
+    D.gam = b->gamma;
+    D.gm1inv = 1.0 / (b->gamma - 1.0);
+    D.eta = eta;
+    D.resistive = eta != 0.0;
+    D.fofc_criteria = (scheme & MHD_FOFC_OFF) ? 0 : 3;
+    D.emf = mhd::EMF_Q26;
+    D.U0 = s->cons + 5 * o;
+    for (int d = 0; d < 3; ++d) D.B0[d] = s->b + 3 * o + d * N;
+    double* q = b->scratch + 47 * o;
+    D.P = q; q += 8 * N;
+    D.F = q; q += 15 * N;
+    D.Ap = q; q += 3 * N;
+    D.Am = q; q += 3 * N;
+    D.Us = q; q += 3 * N;
+    D.Epart = q; q += 12 * N;
+    D.E = q;
+    D.flag = b->flag + o;
+    D.counters = b->counters;
+    double* U1 = b->U1 + 5 * o;
+    double* B1 = b->B1 + 3 * o;
+    D.Uout = U1;
+    for (int d = 0; d < 3; ++d) D.Bout[d] = B1 + d * N;
+    // stage 1 reads S^n, stage 2 reads S^{n+1/2}; both write the scratch state
+    mhd::Dev A = D;
+    A.Uin = A.U0;
+    for (int d = 0; d < 3; ++d) A.Bin[d] = A.B0[d];
+    A.combine = 0;
+    A.stage = 0;
+    mhd::Dev C = D;
+    C.Uin = U1;
+    for (int d = 0; d < 3; ++d) C.Bin[d] = B1 + d * N;
+    C.combine = 1;
+    C.stage = 1;
+    d0[p] = A;
+    d1[p] = C;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->pdev[0], d0.data(), np * sizeof(mhd::Dev), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->pdev[1], d1.data(), np * sizeof(mhd::Dev), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return bcuda(b, e, "parameter upload");
+}
+
+mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc) {
+  mhd::BatchDev B;
+  B.patches = b->pdev[stage];
+  B.order = b->order_dev;
+  B.cell_pref = b->cell_pref_dev;
+  B.sweep_pref = b->sweep_pref_dev;
+  B.npatch = b->npatch;
+  B.seg = b->seg;
+  B.stage = stage;
+  B.fofc = fofc ? 1 : 0;
+  B.barrier = b->barrier;
+  B.counters = b->counters;
+  B.spin_limit = b->spin_limit;
+  B.barrier_extra = b->barrier_extra;
+  return B;
+}
+
+// enqueue one whole step on the stream (also used for graph capture)
+mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta,
+                        cudaStream_t st) {
+  const bool fofc = !(scheme & MHD_FOFC_OFF);
+  const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf;
+  mhd::StageKernel k = mhd::stage_kernel(recon, rs);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0);
+  if (e != cudaSuccess) return bcuda(b, e, "occupancy query");
+  if (per_sm < 1) return bfail(b, MHD_ERR_CUDA, "stage kernel cannot be resident");
+  const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, per_sm) : per_sm;
+  const unsigned grid = (unsigned)(b->nsm * bps);
+  e = cudaMemsetAsync(b->counters, 0, 8 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
+  mhd::BatchDev B0 = batch_dev(b, 0, fofc);
+  mhd::k_batch_maxspeed<<<b->nsm * 8, 256, 0, st>>>(B0);
+  mhd::k_batch_set_dt<<<(b->npatch + 255) / 256, 256, 0, st>>>(
+      b->pdev[0], b->pdev[1], b->npatch, b->counters + 2, cfl, eta, b->h, b->dt_dev, b->counters + 6);
+  for (int stage = 0; stage < 2; ++stage) {
+    mhd::BatchDev B = batch_dev(b, stage, fofc);
+    void* args[] = {&B};
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof(lc));
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(128);
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelExC(&lc, (const void*)k, args);
+    if (e != cudaSuccess) return bcuda(b, e, "cooperative stage launch");
+  }
+  e = cudaMemcpyAsync(s->cons, b->U1, 5 * b->ncell * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->b, b->B1, 3 * b->ncell * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return bcuda(b, e, "batch step enqueue");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mhd_batch_last_error(const mhd_batch* b) { return b ? b->err.c_str() : g_batch_create_err.c_str(); }
+
+mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma, void* cuda_stream, mhd_batch** out) {
+  g_batch_create_err.clear();
+  if (!out) return MHD_ERR_ARG;
+  *out = nullptr;
+  if (!dims || npatch < 1 || !(h > 0) || !(gamma > 1.0)) {
+    g_batch_create_err = "need dims, npatch >= 1, h > 0, gamma > 1";
+    return MHD_ERR_ARG;
+  }
+  mhd_batch* b = new mhd_batch();
+  b->npatch = npatch;
+  b->dims.assign(dims, dims + 3 * npatch);
+  b->off.assign(npatch + 1, 0);
+  for (int p = 0; p < npatch; ++p) {
+    const int* n = &dims[3 * p];
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1) {
+      g_batch_create_err = "every patch needs n >= 1 cells per direction";
+      delete b;
+      return MHD_ERR_ARG;
+    }
+    b->off[p + 1] = b->off[p] + (long long)n[0] * n[1] * n[2];
+  }
+  b->ncell = b->off[npatch];
+  if (b->ncell > (1LL << 34)) {
+    g_batch_create_err = "batch too large";
+    delete b;
+    return MHD_ERR_ARG;
+  }
+  b->h = h;
+  b->gamma = gamma;
+  b->stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    g_batch_create_err = "cudaStreamCreateWithFlags failed";
+    delete b;
+    return MHD_ERR_CUDA;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  b->seg = 64;
+  b->order_kind = 1;
+  b->blocks_per_sm = 0;
+  b->use_graph = 1;
+  b->spin_limit = 1LL << 25;  // ~3 s of waiting before a barrier gives up
+  b->barrier_extra = 0;
+  b->graph_ok = false;
+  b->params_ok = false;
+  const long long C = b->ncell;
+  size_t bytes = (size_t)C * (5 + 3 + 47) * sizeof(double) + (size_t)C + 16 * 256 +
+                 2 * npatch * sizeof(mhd::Dev) + npatch * sizeof(int) + 4 * (npatch + 1) * sizeof(long long);
+  cudaError_t e = cudaMalloc(&b->mem, bytes);
+  if (e != cudaSuccess) {
+    g_batch_create_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    cudaStreamDestroy(b->cap);
+    delete b;
+    return MHD_ERR_CUDA;
+  }
+  char* q = (char*)b->mem;
+  auto take = [&](size_t n) { char* r = q; q += (n + 255) / 256 * 256; return r; };
+  b->U1 = (double*)take(C * 5 * sizeof(double));
+  b->B1 = (double*)take(C * 3 * sizeof(double));
+  b->scratch = (double*)take(C * 47 * sizeof(double));
+  b->counters = (unsigned long long*)take(8 * sizeof(unsigned long long));
+  b->barrier = (unsigned*)take(2 * sizeof(unsigned));
+  b->dt_dev = (double*)take(sizeof(double));
+  b->pdev[0] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
+  b->pdev[1] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
+  b->order_dev = (int*)take(npatch * sizeof(int));
+  b->cell_pref_dev = (long long*)take((npatch + 1) * sizeof(long long));
+  b->sweep_pref_dev = (long long*)take(3 * (npatch + 1) * sizeof(long long));
+  b->flag = (unsigned char*)q;
+  if ((size_t)(q - (char*)b->mem) + C > bytes) {  // layout check (padding consumed the slack)
+    cudaFree(b->mem);
+    cudaStreamDestroy(b->cap);
+    g_batch_create_err = "internal layout error";
+    delete b;
+    return MHD_ERR_CUDA;
+  }
+  e = cudaMemsetAsync(b->mem, 0, bytes, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    cudaFree(b->mem);
+    cudaStreamDestroy(b->cap);
+    g_batch_create_err = std::string("init: ") + cudaGetErrorString(e);
+    delete b;
+    return MHD_ERR_CUDA;
+  }
+  mhd_status s = upload_schedule(b);
+  if (s != MHD_OK) {
+    g_batch_create_err = b->err;
+    cudaFree(b->mem);
+    cudaStreamDestroy(b->cap);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return MHD_OK;
+}
+
+void mhd_batch_destroy(mhd_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  cudaStreamDestroy(b->cap);
+  cudaFree(b->mem);
+  delete b;
+}
+
+mhd_status mhd_batch_offsets(const mhd_batch* b, long long* cell_offsets) {
+  if (!b || !cell_offsets) return MHD_ERR_ARG;
+  for (int p = 0; p <= b->npatch; ++p) cell_offsets[p] = b->off[p];
+  return MHD_OK;
+}
+
+mhd_status mhd_batch_set_schedule(mhd_batch* b, int seg, int order, int blocks_per_sm, int use_graph) {
+  if (!b) return MHD_ERR_ARG;
+  if (seg < 1 || seg > 4096 || order < 0 || order > 1 || blocks_per_sm < 0)
+    return bfail(b, MHD_ERR_ARG, "need 1 <= seg <= 4096, order 0/1, blocks_per_sm >= 0");
+  mhd_status s = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  b->seg = seg;
+  b->order_kind = order;
+  b->blocks_per_sm = blocks_per_sm;
+  b->use_graph = use_graph ? 1 : 0;
+  drop_graph(b);
+  return upload_schedule(b);
+}
+
+mhd_status mhd_batch_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta) {
+  if (!b) return MHD_ERR_ARG;
+  b->err.clear();
+  if (!s || !s->cons || !s->b) return bfail(b, MHD_ERR_ARG, "state has a NULL array");
+  if (!(cfl > 0) || !(cfl < 1e300)) return bfail(b, MHD_ERR_ARG, "cfl must be finite and > 0");
+  if (!(eta >= 0) || !(eta < 1e300)) return bfail(b, MHD_ERR_ARG, "eta must be finite and >= 0");
+  if (scheme & ~(0xffff | MHD_FOFC_OFF)) return bfail(b, MHD_ERR_ARG, "unknown scheme bits");
+  const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf, emf = (scheme >> 8) & 0xf, avg = (scheme >> 12) & 0xf;
+  if (recon == MHD_RECON_PPM_EP || avg == 1)
+    return bfail(b, MHD_ERR_UNSUPPORTED, "PPM-EP and B25b are cited but not defined in the paper");
+  if (recon > 3 || rs > 2 || emf > 2 || avg > 1) return bfail(b, MHD_ERR_ARG, "scheme field out of range");
+  if (emf != mhd::EMF_Q26) return bfail(b, MHD_ERR_UNSUPPORTED, "the batched step runs the Q26 EMF compute");
+  const bool same = b->params_ok && b->built_cons == s->cons && b->built_b == s->b && b->built_scheme == scheme &&
+                    b->built_eta == eta && b->built_cfl == cfl;
+  if (!same) {
+    drop_graph(b);
+    mhd_status st = upload_params(b, s, scheme, eta);
+    if (st != MHD_OK) return st;
+    b->built_cons = s->cons;
+    b->built_b = s->b;
+    b->built_scheme = scheme;
+    b->built_eta = eta;
+    b->built_cfl = cfl;
+    b->params_ok = true;
+  }
+  if (!b->use_graph) return enqueue_step(b, s, cfl, scheme, eta, b->stream);
+  if (!b->graph_ok) {
+    // capture on the private stream (capture is not allowed on the legacy default stream); the
+    // graph is then launched on the caller's stream
+    mhd_status st = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (st != MHD_OK) return st;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaStreamBeginCapture");
+    st = enqueue_step(b, s, cfl, scheme, eta, b->cap);
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st != MHD_OK) {
+      if (e == cudaSuccess) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
+    b->graph_ok = true;
+  }
+  return bcuda(b, cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+}
+
+mhd_status mhd_batch_last_dt(mhd_batch* b, double* dt) {
+  if (!b || !dt) return MHD_ERR_ARG;
+  unsigned long long h[8];
+  cudaError_t e = cudaMemcpyAsync(dt, b->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  mhd_status s = bcuda(b, e, "read dt");
+  if (s != MHD_OK) return s;
+  if (h[7]) return bfail(b, MHD_ERR_TIMEOUT, "a grid barrier of the batched stage gave up waiting");
+  if (h[6]) return bfail(b, MHD_ERR_NONFINITE, "signal speed not finite: no step taken");
+  return MHD_OK;
+}
+
+mhd_status mhd_batch_stats(mhd_batch* b, long long* s1, long long* s2) {
+  if (!b) return MHD_ERR_ARG;
+  unsigned long long h[8];
+  cudaError_t e = cudaMemcpyAsync(h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  mhd_status s = bcuda(b, e, "read counters");
+  if (s != MHD_OK) return s;
+  if (s1) *s1 = (long long)h[0];
+  if (s2) *s2 = (long long)h[1];
+  if (h[7]) return bfail(b, MHD_ERR_TIMEOUT, "a grid barrier of the batched stage gave up waiting");
+  return MHD_OK;
+}
+
+mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta, int* seg_out,
+                          int* order_out, int* bps_out) {
+  if (!b || !s || !s->cons || !s->b) return MHD_ERR_ARG;
+  // time one step per candidate on a scratch copy of the state (the caller's state is unchanged)
+  double* cpy = nullptr;
+  cudaError_t e = cudaMalloc(&cpy, 8 * b->ncell * sizeof(double));
+  if (e != cudaSuccess) return bcuda(b, e, "cudaMalloc");
+  mhd_batch_state t = {cpy, cpy + 5 * b->ncell};
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::stage_kernel(scheme & 0xf, (scheme >> 4) & 0xf), 128, 0);
+  const int segs[] = {16, 32, 64, 128};
+  float best = 1e30f;
+  int bs = 64, bo = 1, bb = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  mhd_status st = MHD_OK;
+  const int saved_graph = b->use_graph;
+  for (int seg : segs)
+    for (int order = 0; order < 2 && st == MHD_OK; ++order)
+      for (int bps = 1; bps <= std::max(1, per_sm) && st == MHD_OK; ++bps) {
+        st = mhd_batch_set_schedule(b, seg, order, bps, 0);
+        if (st != MHD_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == MHD_OK; ++rep) {  // first run warms up
+          cudaMemcpyAsync(cpy, s->cons, 5 * b->ncell * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+          cudaMemcpyAsync(cpy + 5 * b->ncell, s->b, 3 * b->ncell * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+          cudaEventRecord(e0, b->stream);
+          st = mhd_batch_step(b, &t, cfl, scheme, eta);
+          cudaEventRecord(e1, b->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (st == MHD_OK) {
+          double dt;
+          st = mhd_batch_last_dt(b, &dt);
+        }
+        if (st == MHD_OK && ms < best) {
+          best = ms;
+          bs = seg;
+          bo = order;
+          bb = bps;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->params_ok = false;  // parameters pointed at the copy
+  cudaFree(cpy);
+  if (st != MHD_OK) return st;
+  st = mhd_batch_set_schedule(b, bs, bo, bb, saved_graph);
+  if (seg_out) *seg_out = bs;
+  if (order_out) *order_out = bo;
+  if (bps_out) *bps_out = bb;
+  return st;
+}
+
+mhd_status mhd_batch_test_barrier(mhd_batch* b, int extra_blocks, long long spin_limit) {
+  if (!b || extra_blocks < 0 || spin_limit < 1) return MHD_ERR_ARG;
+  b->barrier_extra = extra_blocks;
+  b->spin_limit = spin_limit;
+  drop_graph(b);
+  b->params_ok = false;
+  return MHD_OK;
+}
+
+}  // extern "C"

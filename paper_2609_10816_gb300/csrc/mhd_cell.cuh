@@ -1,0 +1,229 @@
+// mhd_cell.cuh -- per-cell operations: conserved -> primitive (Sec. 2.2), the update increments
+// (Eqs. rk:increment-state, rk:increment-bfield), the validity flags and first-order flux
+// correction (Sec. 2.5).
+#pragma once
+#include "mhd_device.cuh"
+#include "mhd_index.cuh"
+#include "mhd_internal.cuh"
+
+namespace mhd {
+
+__device__ __forceinline__ long long cell_id() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// ---- cons -> prim (Eq. state:primitive), with the face-averaged cell field ----------------
+__device__ __forceinline__ void prim_of(const Dev& D, const double* U, const double* const* B,
+                                        long long X, double* w) {
+  const long long N = D.N;
+  const double rho = U[X];
+  const double rinv = rcp(rho);
+  const double u0 = U[N + X] * rinv, u1 = U[2 * N + X] * rinv, u2 = U[3 * N + X] * rinv;
+  const double b0 = 0.5 * (B[0][X] + B[0][shift(D, X, 0, 1)]);
+  const double b1 = 0.5 * (B[1][X] + B[1][shift(D, X, 1, 1)]);
+  const double b2 = 0.5 * (B[2][X] + B[2][shift(D, X, 2, 1)]);
+  const double u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
+  const double b2s = fma(b0, b0, fma(b1, b1, b2 * b2));
+  const double eint = U[4 * N + X] - 0.5 * fma(rho, u2s, b2s);
+  w[0] = rho; w[1] = u0; w[2] = u1; w[3] = u2;
+  w[4] = (D.gam - 1.0) * eint;
+  w[5] = b0; w[6] = b1; w[7] = b2;
+}
+
+__device__ __forceinline__ void prim_cell(const Dev& D, long long X) {
+  double w[8];
+  prim_of(D, D.Uin, D.Bin, X, w);
+#pragma unroll
+  for (int v = 0; v < 8; ++v) D.P[v * D.N + X] = w[v];
+}
+
+// ---- update: S_out = S^n + D(F, E) --------------------------------------------------------
+__device__ __forceinline__ double incr_cell(const Dev& D, int v, long long X, const long long* Xp) {
+  const long long N = D.N;
+  const double* F0 = D.F + (0 * 5 + v) * N;
+  const double* F1 = D.F + (1 * 5 + v) * N;
+  const double* F2 = D.F + (2 * 5 + v) * N;
+  const double acc = fma(F0[X] - F0[Xp[0]], D.hinv[0],
+                         fma(F1[X] - F1[Xp[1]], D.hinv[1], (F2[X] - F2[Xp[2]]) * D.hinv[2]));
+  return D.dt * acc;
+}
+__device__ __forceinline__ double incr_face(const Dev& D, int d, long long X, const long long* Xp) {
+  const long long N = D.N;
+  const int a = (d + 1) % 3, c = (d + 2) % 3;
+  const double* Ec = D.E + c * N;
+  const double* Ea = D.E + a * N;
+  return D.dt * fma(Ec[X] - Ec[Xp[a]], D.hinv[a], (Ea[Xp[c]] - Ea[X]) * D.hinv[c]);
+}
+
+__device__ __forceinline__ void update_cell(const Dev& D, long long X) {
+  const long long N = D.N;
+  const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
+#pragma unroll
+  for (int v = 0; v < 5; ++v) D.Uout[v * N + X] = D.U0[v * N + X] + incr_cell(D, v, X, Xp);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) D.Bout[d][X] = D.B0[d][X] + incr_face(D, d, X, Xp);
+}
+
+// ---- validity flags (Sec. 2.5) --------------------------------------------------------------
+__device__ __forceinline__ bool invalid_cell(const Dev& D, const double* U, double* const* B, long long X) {
+  const long long N = D.N;
+  bool fin = true;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fin = fin && finite_d(U[v * N + X]);
+  double bc[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double lo = B[d][X], hi = B[d][shift(D, X, d, 1)];
+    fin = fin && finite_d(lo) && finite_d(hi);
+    bc[d] = 0.5 * (lo + hi);
+  }
+  if (!fin) return true;
+  const double rho = U[X];
+  if ((D.fofc_criteria & 1) && le0(rho)) return true;
+  if (D.fofc_criteria & 2) {
+    const double rinv = rcp(rho);
+    const double u0 = U[N + X] * rinv, u1 = U[2 * N + X] * rinv, u2 = U[3 * N + X] * rinv;
+    const double u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
+    const double b2s = fma(bc[0], bc[0], fma(bc[1], bc[1], bc[2] * bc[2]));
+    const double p = (D.gam - 1.0) * (U[4 * N + X] - 0.5 * fma(rho, u2s, b2s));
+    if (!gt0(p)) return true;  // p <= 0 or NaN
+  }
+  return false;
+}
+
+// flag of cell X (written) and whether it is set
+__device__ __forceinline__ bool flag_cell(const Dev& D, long long X) {
+  const unsigned char f = invalid_cell(D, D.Uout, D.Bout, X) ? 1 : 0;
+  D.flag[X] = f;
+  return f != 0;
+}
+
+// warp-aggregated count of flagged cells into counters[stage] (every lane of the warp calls it)
+__device__ __forceinline__ void count_flags(const Dev& D, bool f) {
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&D.counters[D.stage], (unsigned long long)__popc(bal));
+}
+
+// ---- first-order flux correction (Sec. 2.5) -------------------------------------------------
+// First-order (piecewise-constant + LLF) face problem between cells Xl and Xr of S^n.
+__device__ __forceinline__ void fo_face(const Dev& D, int d, long long Xl, long long Xr, long long Xface,
+                                        double* f, double& alpha, double& ustar) {
+  const int a = (d + 1) % 3, c = (d + 2) % 3;
+  double wl[8], wr[8];
+  prim_of(D, D.U0, D.B0, Xl, wl);
+  prim_of(D, D.U0, D.B0, Xr, wr);
+  const FaceState sl = {wl[0], wl[1 + d], wl[1 + a], wl[1 + c], wl[4], wl[5 + a], wl[5 + c]};
+  const FaceState sr = {wr[0], wr[1 + d], wr[1 + a], wr[1 + c], wr[4], wr[5 + a], wr[5 + c]};
+  double ap, am;
+  riemann<RS_LLF>(sl, sr, D.B0[d][Xface], D.gam, D.gm1inv, f, ap, am, ustar);
+  alpha = ap;
+}
+
+__device__ __forceinline__ bool flagged(const Dev& D, long long X) { return D.flag[X] != 0; }
+
+__device__ __forceinline__ void fo_faces_cell(const Dev& D, long long X) {
+  const long long N = D.N;
+  for (int d = 0; d < 3; ++d) {
+    const long long Xl = shift(D, X, d, -1);
+    if (!(flagged(D, X) || flagged(D, Xl))) continue;
+    const int a = (d + 1) % 3, c = (d + 2) % 3;
+    double f[5], al, us;
+    fo_face(D, d, Xl, X, X, f, al, us);
+    if (D.resistive) {
+      // Joule flux from the S^n field (same reading as the high-order faces)
+      auto jedge = [&](int e, long long Y) {
+        const int ae = (e + 1) % 3, ce = (e + 2) % 3;
+        return (D.B0[ce][Y] - D.B0[ce][shift(D, Y, ae, -1)]) * D.hinv[ae] -
+               (D.B0[ae][Y] - D.B0[ae][shift(D, Y, ce, -1)]) * D.hinv[ce];
+      };
+      const long long Xc = shift(D, X, c, 1), Xa = shift(D, X, a, 1);
+      const double ea = 0.5 * D.eta * (jedge(a, X) + jedge(a, Xc));
+      const double ec = 0.5 * D.eta * (jedge(c, X) + jedge(c, Xa));
+      const double* Ba = D.B0[a];
+      const double* Bc = D.B0[c];
+      const double bcbar = 0.25 * (Bc[Xl] + Bc[X] + Bc[shift(D, Xl, c, 1)] + Bc[Xc]);
+      const double babar = 0.25 * (Ba[Xl] + Ba[X] + Ba[shift(D, Xl, a, 1)] + Ba[Xa]);
+      f[4] += fma(ea, bcbar, -ec * babar);
+    }
+    double* F = D.F + 5LL * d * N;
+    F[0 * N + X] = f[0];
+    F[(1 + d) * N + X] = f[1];
+    F[(1 + a) * N + X] = f[2];
+    F[(1 + c) * N + X] = f[3];
+    F[4 * N + X] = f[4];
+  }
+}
+
+// First-order EMF on the e-edge of X: the four cells around it are X, X-a, X-c, X-a-c.
+__device__ __forceinline__ void fo_edges_cell(const Dev& D, long long X) {
+  const long long N = D.N;
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, c = (e + 2) % 3;
+    const long long Xa = shift(D, X, a, -1), Xc = shift(D, X, c, -1), Xac = shift(D, Xa, c, -1);
+    if (!(flagged(D, X) || flagged(D, Xa) || flagged(D, Xc) || flagged(D, Xac))) continue;
+    // a-faces at X - c (between Xac, Xc) and X (between Xa, X); c-faces at X - a (Xac, Xa) and X (Xc, X)
+    double f[5], apaB, apaT, apcL, apcR, uaB, uaT, ucL, ucR;
+    fo_face(D, a, Xac, Xc, Xc, f, apaB, uaB);
+    fo_face(D, a, Xa, X, X, f, apaT, uaT);
+    fo_face(D, c, Xac, Xa, Xa, f, apcL, ucL);
+    fo_face(D, c, Xc, X, X, f, apcR, ucR);
+    const double baB = D.B0[a][Xc], baT = D.B0[a][X];
+    const double bcL = D.B0[c][Xa], bcR = D.B0[c][X];
+    double eLB, eRB, eLT, eRT;
+    if (D.emf == EMF_Q26) {
+      eLB = fma(-uaB, bcL, ucL * baB);
+      eRB = fma(-uaB, bcR, ucR * baB);
+      eLT = fma(-uaT, bcL, ucL * baT);
+      eRT = fma(-uaT, bcR, ucR * baT);
+    } else {
+      // piecewise-constant FS18 / B25a: each corner takes the cell in that corner
+      // (LB = X-a-c, RB = X-c, LT = X-a, RT = X)
+      const long long cellQ[4] = {Xac, Xc, Xa, X};
+      double ec[4];
+      for (int q = 0; q < 4; ++q) {
+        double w[8];
+        prim_of(D, D.U0, D.B0, cellQ[q], w);
+        if (D.emf == EMF_FS18) {
+          const double bcs = (q & 1) ? bcR : bcL;
+          const double bas = (q >> 1) ? baT : baB;
+          ec[q] = fma(-w[1 + a], bcs, w[1 + c] * bas);
+        } else {
+          ec[q] = fma(-w[1 + a], w[5 + c], w[1 + c] * w[5 + a]);
+        }
+      }
+      eLB = ec[0]; eRB = ec[1]; eLT = ec[2]; eRT = ec[3];
+    }
+    const double apa = pmax(apaB, apaT), apc = pmax(apcL, apcR);
+    const double ia = rcp(apa + apa), ic = rcp(apc + apc);
+    const double up = fma(apc, fma(apa, eLB, apa * eRB), apc * fma(apa, eLT, apa * eRT)) * (ia * ic);
+    double emf = fma(apa * apa * ia, bcR - bcL, fma(-apc * apc * ic, baT - baB, up));
+    if (D.resistive) {
+      const double j = (D.B0[c][X] - D.B0[c][Xa]) * D.hinv[a] - (D.B0[a][X] - D.B0[a][Xc]) * D.hinv[c];
+      emf = fma(D.eta, j, emf);
+    }
+    D.E[e * N + X] = emf;
+  }
+}
+
+// Recompute every cell with a masked face and every face with a masked edge.
+__device__ __forceinline__ void fo_recompute_cell(const Dev& D, long long X) {
+  const long long N = D.N;
+  const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
+  const long long Xm[3] = {shift(D, X, 0, -1), shift(D, X, 1, -1), shift(D, X, 2, -1)};
+  bool cell = flagged(D, X);
+  for (int d = 0; d < 3; ++d) cell = cell || flagged(D, Xp[d]) || flagged(D, Xm[d]);
+  if (cell)
+    for (int v = 0; v < 5; ++v) D.Uout[v * N + X] = D.U0[v * N + X] + incr_cell(D, v, X, Xp);
+  // e-edge at Y is masked if one of Y, Y-a, Y-c, Y-a-c is flagged
+  auto edge_masked = [&](int e, long long Y) {
+    const int a = (e + 1) % 3, c = (e + 2) % 3;
+    const long long Ya = shift(D, Y, a, -1), Yc = shift(D, Y, c, -1);
+    return flagged(D, Y) || flagged(D, Ya) || flagged(D, Yc) || flagged(D, shift(D, Ya, c, -1));
+  };
+  for (int d = 0; d < 3; ++d) {
+    const int a = (d + 1) % 3, c = (d + 2) % 3;
+    // the d-face at X is bounded by c-edges at X and X+a, and a-edges at X and X+c
+    if (edge_masked(c, X) || edge_masked(c, Xp[a]) || edge_masked(a, X) || edge_masked(a, Xp[c]))
+      D.Bout[d][X] = D.B0[d][X] + incr_face(D, d, X, Xp);
+  }
+}
+
+}  // namespace mhd

@@ -24,17 +24,18 @@ __host__ __device__ __forceinline__ void sweep_axes(int dir, int& t1, int& t2) {
   t2 = dir == 2 ? 1 : 2;
 }
 
-inline long long sweep_threads(const Dev& D, int dir, int seg) {
+__host__ __device__ inline long long sweep_threads(const Dev& D, int dir, int seg) {
   int t1, t2;
   sweep_axes(dir, t1, t2);
   const long long nseg = (D.n[dir] + seg - 1) / seg;
   return (long long)D.n[t1] * D.n[t2] * nseg;
 }
 
-__device__ __forceinline__ bool sweep_line(const Dev& D, int dir, int seg, Line& ln, int& m0, int& m1) {
+// segment number `tid` of the sweeps along dir (false past the last one)
+__device__ __forceinline__ bool sweep_line_at(const Dev& D, int dir, int seg, long long tid, Line& ln, int& m0,
+                                              int& m1) {
   int t1, t2;
   sweep_axes(dir, t1, t2);
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int n1 = D.n[t1], n2 = D.n[t2], nd = D.n[dir];
   const int nseg = (nd + seg - 1) / seg;
   if (tid >= (long long)n1 * n2 * nseg) return false;
@@ -48,6 +49,10 @@ __device__ __forceinline__ bool sweep_line(const Dev& D, int dir, int seg, Line&
   m0 = s * seg;
   m1 = min(nd, m0 + seg);
   return true;
+}
+
+__device__ __forceinline__ bool sweep_line(const Dev& D, int dir, int seg, Line& ln, int& m0, int& m1) {
+  return sweep_line_at(D, dir, seg, (long long)blockIdx.x * blockDim.x + threadIdx.x, ln, m0, m1);
 }
 
 }  // namespace mhd

@@ -283,11 +283,11 @@ def patch_dims(npatch=1024, seed=4, edges=(16, 24, 32, 48, 64)):
     return rng.choice(np.asarray(edges), size=(npatch, 3))
 
 
-def random_patch(shape, rng, gamma=GAMMA):
+def random_patch(shape, rng, gamma=GAMMA, h=None):
     """Smooth random patch state: rho = 1.25 + 0.75 s (s in [-1, 1]), |u| < 1 from low-k modes,
-    p = 1, b = curl of a random low-k periodic potential."""
+    p = 1, b = curl of a random low-k periodic potential; cell width h (default 1/n per axis)."""
     nx, ny, nz = shape
-    box = Box(shape)
+    box = Box(shape) if h is None else Box(shape, (h * nx, h * ny, h * nz))
     rho = 1.25 + 0.75 * _lowk_field(rng, shape)
     u = [0.55 * _lowk_field(rng, shape) for _ in range(3)]
     p = np.ones((nz, ny, nx))

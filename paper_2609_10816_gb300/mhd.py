@@ -49,6 +49,10 @@ class _State(ctypes.Structure):
                 ("b2", ctypes.c_void_p)]
 
 
+class _BatchState(ctypes.Structure):
+    _fields_ = [("cons", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -85,6 +89,28 @@ def lib():
     L.mhd_profile.restype = ctypes.c_int
     L.mhd_profile_read.argtypes = [vp, P(d), P(ctypes.c_longlong), ctypes.c_int]
     L.mhd_profile_read.restype = ctypes.c_int
+    i = ctypes.c_int
+    ll = ctypes.c_longlong
+    L.mhd_batch_create.argtypes = [P(i), i, d, d, vp, P(vp)]
+    L.mhd_batch_create.restype = i
+    L.mhd_batch_destroy.argtypes = [vp]
+    L.mhd_batch_destroy.restype = None
+    L.mhd_batch_offsets.argtypes = [vp, P(ll)]
+    L.mhd_batch_offsets.restype = i
+    L.mhd_batch_step.argtypes = [vp, P(_BatchState), d, i, d]
+    L.mhd_batch_step.restype = i
+    L.mhd_batch_last_dt.argtypes = [vp, P(d)]
+    L.mhd_batch_last_dt.restype = i
+    L.mhd_batch_stats.argtypes = [vp, P(ll), P(ll)]
+    L.mhd_batch_stats.restype = i
+    L.mhd_batch_set_schedule.argtypes = [vp, i, i, i, i]
+    L.mhd_batch_set_schedule.restype = i
+    L.mhd_batch_tune.argtypes = [vp, P(_BatchState), d, i, d, P(i), P(i), P(i)]
+    L.mhd_batch_tune.restype = i
+    L.mhd_batch_test_barrier.argtypes = [vp, i, ll]
+    L.mhd_batch_test_barrier.restype = i
+    L.mhd_batch_last_error.argtypes = [vp]
+    L.mhd_batch_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -185,3 +211,93 @@ class Context:
 def to_device(cons, b, device="cuda") -> State:
     return State(torch.as_tensor(cons, dtype=torch.float64).to(device).contiguous(),
                  torch.as_tensor(b, dtype=torch.float64).to(device).contiguous())
+
+
+class Batch:
+    """mhd_batch_*: many periodic patches of cell width h advanced together on the device."""
+
+    def __init__(self, dims, h, gamma=5.0 / 3.0, stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        flat = (ctypes.c_int * (3 * len(self.dims)))(*[x for d in self.dims for x in d])
+        out = ctypes.c_void_p()
+        rc = L.mhd_batch_create(flat, len(self.dims), float(h), float(gamma),
+                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(out))
+        if rc != OK:
+            raise MHDError(rc, L.mhd_batch_last_error(None).decode())
+        self._h = out
+        offs = (ctypes.c_longlong * (len(self.dims) + 1))()
+        self._err(L.mhd_batch_offsets(self._h, offs))
+        self.offsets = list(offs)
+        self.ncell = self.offsets[-1]
+
+    def _err(self, rc):
+        if rc != OK:
+            raise MHDError(rc, lib().mhd_batch_last_error(self._h).decode())
+
+    def empty_state(self, device="cuda"):
+        return (torch.zeros(5 * self.ncell, dtype=torch.float64, device=device),
+                torch.zeros(3 * self.ncell, dtype=torch.float64, device=device))
+
+    def pack(self, patches, device="cuda"):
+        """[(cons (5,nz,ny,nx), b (3,nz,ny,nx)) per patch] -> device (cons, b) in batch layout."""
+        import numpy as np
+
+        cons = np.concatenate([np.ascontiguousarray(c, dtype=np.float64).ravel() for c, _ in patches])
+        b = np.concatenate([np.ascontiguousarray(bb, dtype=np.float64).ravel() for _, bb in patches])
+        assert cons.size == 5 * self.ncell and b.size == 3 * self.ncell
+        return torch.from_numpy(cons).to(device), torch.from_numpy(b).to(device)
+
+    def unpack(self, cons, b, p):
+        """Host numpy (cons, b) of patch p."""
+        nx, ny, nz = self.dims[p]
+        o, n = self.offsets[p], nx * ny * nz
+        c = cons[5 * o:5 * (o + n)].reshape(5, nz, ny, nx).cpu().numpy()
+        bb = b[3 * o:3 * (o + n)].reshape(3, nz, ny, nx).cpu().numpy()
+        return c, bb
+
+    def _st(self, cons, b):
+        if cons.dtype != torch.float64 or b.dtype != torch.float64 or not cons.is_cuda or not b.is_cuda:
+            raise TypeError("batch state must be float64 CUDA tensors")
+        if cons.numel() != 5 * self.ncell or b.numel() != 3 * self.ncell:
+            raise ValueError("batch state has the wrong size")
+        return _BatchState(cons.data_ptr(), b.data_ptr())
+
+    def step(self, cons, b, cfl, scheme_bits, eta=0.0):
+        s = self._st(cons, b)
+        self._err(lib().mhd_batch_step(self._h, ctypes.byref(s), float(cfl), int(scheme_bits), float(eta)))
+
+    def last_dt(self):
+        out = ctypes.c_double()
+        self._err(lib().mhd_batch_last_dt(self._h, ctypes.byref(out)))
+        return out.value
+
+    def stats(self):
+        a, c = ctypes.c_longlong(), ctypes.c_longlong()
+        self._err(lib().mhd_batch_stats(self._h, ctypes.byref(a), ctypes.byref(c)))
+        return a.value, c.value
+
+    def set_schedule(self, seg=64, order=1, blocks_per_sm=0, use_graph=True):
+        self._err(lib().mhd_batch_set_schedule(self._h, int(seg), int(order), int(blocks_per_sm), 1 if use_graph else 0))
+
+    def tune(self, cons, b, cfl, scheme_bits, eta=0.0):
+        s = self._st(cons, b)
+        seg, order, bps = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._err(lib().mhd_batch_tune(self._h, ctypes.byref(s), float(cfl), int(scheme_bits), float(eta),
+                                       ctypes.byref(seg), ctypes.byref(order), ctypes.byref(bps)))
+        return {"seg": seg.value, "order": order.value, "blocks_per_sm": bps.value}
+
+    def test_barrier(self, extra_blocks, spin_limit):
+        self._err(lib().mhd_batch_test_barrier(self._h, int(extra_blocks), int(spin_limit)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mhd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,121 @@
+"""Batched patches (mhd_batch_*) against the single-box step and the oracle (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_10816_gb300 import inputs, mhd
+from tests.util import state_errors
+
+pytestmark = pytest.mark.gpu
+
+H = 1.0 / 64
+
+
+def _patches(n, seed, edges=(4, 6, 8, 12, 16)):
+    rng = np.random.default_rng(seed)
+    dims = [tuple(int(x) for x in rng.choice(edges, size=3)) for _ in range(n)]
+    pats = []
+    for d in dims:
+        cons, b, _ = inputs.random_patch(d, rng, h=H)
+        pats.append((cons, b))
+    return dims, pats
+
+
+def _low_pressure_patch(shape, seed=1):
+    cons, b, info = inputs.random_smooth(shape, seed=seed, rough=0.0, h=(H, H, H))
+    rng = np.random.default_rng(seed)
+    rho = cons[0]
+    u = [cons[1 + d] / rho for d in range(3)]
+    x = (np.arange(shape[0]) + 0.5) / shape[0]
+    u[0] = u[0] + 3.0 * np.sin(2 * np.pi * x)[None, None, :] + 0.3 * rng.uniform(-1, 1, rho.shape)
+    return inputs.assemble(rho, u, 1e-3 * np.ones_like(rho), b), b
+
+
+def _plain_step(shape, cons, b, dt, sch, eta):
+    ctx = mhd.Context(shape, (H, H, H))
+    st = mhd.to_device(cons, b)
+    ctx.step(st, dt, sch, eta)
+    torch.cuda.synchronize()
+    out = st.cons.cpu().numpy(), st.b.cpu().numpy(), ctx.stats()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_single_box_steps(gpu_lib, use_graph):
+    dims, pats = _patches(20, seed=3)
+    dims.append((16, 6, 4))
+    pats.append(_low_pressure_patch((16, 6, 4)))  # sets flux-correction flags
+    bt = mhd.Batch(dims, H)
+    bt.set_schedule(seg=8, order=1, blocks_per_sm=0, use_graph=use_graph)
+    cons, b = bt.pack(pats)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    for step in range(2):
+        before = [bt.unpack(cons, b, p) for p in range(len(dims))]
+        bt.step(cons, b, 0.3, sch, 1e-3)
+        dt = bt.last_dt()
+        flagged = bt.stats()
+        tot = [0, 0]
+        for p, d in enumerate(dims):
+            c1, b1 = bt.unpack(cons, b, p)
+            c0, b0 = before[p]
+            cp, bp, fl = _plain_step(d, c0, b0, dt, sch, 1e-3)
+            tot[0] += fl[0]
+            tot[1] += fl[1]
+            assert np.array_equal(c1, cp) and np.array_equal(b1, bp), (step, p, d)
+        assert tuple(tot) == flagged
+    assert flagged[0] + flagged[1] >= 0
+
+
+def test_batch_patches_against_oracle(gpu_lib):
+    dims, pats = _patches(6, seed=9, edges=(6, 8, 10))
+    bt = mhd.Batch(dims, H)
+    cons, b = bt.pack(pats)
+    sch = mhd.scheme("plm_mc", "hlld", "q26")
+    bt.step(cons, b, 0.3, sch, 0.0)
+    dt = bt.last_dt()
+    # the batch dt is the CFL step over all patches
+    cfgs = [oracle.Config(shape=d, h=(H, H, H), recon="plm_mc", riemann="hlld") for d in dims]
+    assert dt == pytest.approx(min(oracle.max_dt(c, *pats[p], 0.3) for p, c in enumerate(cfgs)), rel=1e-14)
+    for p, d in enumerate(dims):
+        co, bo, _ = oracle.step(cfgs[p], *pats[p], dt)
+        c1, b1 = bt.unpack(cons, b, p)
+        errs = state_errors(c1, b1, co, bo)
+        assert all(v <= 1e-12 for v in errs.values()), (p, errs)
+
+
+def test_batch_autotune_keeps_results(gpu_lib):
+    dims, pats = _patches(12, seed=5)
+    bt = mhd.Batch(dims, H)
+    cons, b = bt.pack(pats)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    ref_c, ref_b = cons.clone(), b.clone()
+    choice = bt.tune(cons, b, 0.3, sch)
+    assert choice["seg"] in (16, 32, 64, 128) and choice["order"] in (0, 1) and choice["blocks_per_sm"] >= 1
+    assert torch.equal(cons, ref_c) and torch.equal(b, ref_b)  # tuning leaves the state alone
+    bt.step(cons, b, 0.3, sch)
+    bt.set_schedule(seg=7, order=0, blocks_per_sm=1, use_graph=False)
+    bt.step(ref_c, ref_b, 0.3, sch)
+    torch.cuda.synchronize()
+    assert torch.equal(cons, ref_c) and torch.equal(b, ref_b)  # schedule changes nothing but time
+
+
+def test_batch_barrier_wait_is_bounded(gpu_lib):
+    """A barrier that never completes gives MHD_ERR_TIMEOUT, and the batch stays usable."""
+    dims, pats = _patches(4, seed=2)
+    bt = mhd.Batch(dims, H)
+    cons, b = bt.pack(pats)
+    sch = mhd.scheme("plm_mc", "hll", "q26")
+    bt.test_barrier(1, 2000)  # every barrier waits for one block that is never launched
+    bt.step(cons, b, 0.3, sch)
+    with pytest.raises(mhd.MHDError) as ei:
+        bt.last_dt()
+    assert ei.value.code == mhd.ERR_TIMEOUT
+    bt.test_barrier(0, 1 << 25)
+    c2, b2 = bt.pack(pats)
+    bt.step(c2, b2, 0.3, sch)
+    assert bt.last_dt() > 0
+    cp, bp, _ = _plain_step(dims[0], *pats[0], bt.last_dt(), sch, 0.0)
+    c1, b1 = bt.unpack(c2, b2, 0)
+    assert np.array_equal(c1, cp) and np.array_equal(b1, bp)
