@@ -125,6 +125,17 @@ mhd_status mhd_profile(mhd_ctx *ctx, int enable);
  * context was created or the counts were last read with reset != 0. Arrays hold MHD_K_COUNT. */
 mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches, int reset);
 
+/* Adjoint (vector-Jacobian product) of one mhd_step with a frozen dt: on entry `lam` holds
+ * dL/dS^{n+1} (same layout as the state), on return dL/dS^n; *dL_deta (if not NULL) is increased
+ * by the step's contribution to dL/d(eta). `state` is S^n (unchanged). Limiters, min/max and
+ * Riemann-fan branches are differentiated on the branch the forward step takes (the forward
+ * stage 1 is recomputed inside). The paper has no counterpart; it makes the step usable inside
+ * gradient-based workflows. Covers the Q26 EMF compute and steps in which flux correction
+ * flagged no cell (the caller checks mhd_stats of the forward step); the first call allocates
+ * about 125 doubles per cell of adjoint scratch. Synchronous when dL_deta is not NULL. */
+mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_state *lam, double dt, int scheme,
+                            double eta, double *dL_deta);
+
 /* Self-check of the reciprocal, reciprocal square root and square root that the kernels use in
  * place of IEEE division and sqrt (hardware approximation + one third-order Newton correction):
  * on n pseudo-random positive inputs spread over [2^-40, 2^40] it returns in max_rel_err[0..2]

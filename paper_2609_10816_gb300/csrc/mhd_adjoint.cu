@@ -1,0 +1,386 @@
+// mhd_adjoint.cu -- hand-written adjoint (vector-Jacobian product) of one step.
+//
+// The step is S1 = S0 + D(F(S0)), S2 = S0 + D((F(S0) + F(S1)) / 2), where F(S) collects the face
+// fluxes and edge EMFs of a state and D is the flux divergence / discrete curl (Eqs.
+// rk:increment-state, rk:increment-bfield). Reverse mode runs backwards through this chain; the
+// adjoint of F at a state is assembled from local Jacobians, each obtained with forward-mode
+// dual numbers on the GPU (one tangent per local input), so every limiter, min/max and
+// Riemann-fan branch is differentiated on the branch the forward pass took:
+//   edges   : E = LD04(Q26 corners) from 8 reconstructed edge values and 4 edge speeds, + eta j
+//   edge rec: face fields and face velocities reconstructed to edges (point-wise reconstruction)
+//   faces   : Riemann solve from the 7 + 7 reconstructed states and the normal field
+//   face rec: primitives reconstructed to faces
+//   prim    : conserved variables and the face field to primitives
+// plus the Joule flux and eta j terms, which are bilinear and differentiated by hand. Adjoint
+// contributions that several threads add to the same face are accumulated with atomics.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "mhd_cell.cuh"
+#include "mhd_edge.cuh"
+#include "mhd_face.cuh"
+
+namespace mhd {
+
+__device__ __forceinline__ long long aid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// lower/upper values of point m of `arr` along dir, from the window m-2 .. m+2, with a unit
+// tangent on every window slot that holds point Y (several on lines shorter than the window)
+template <int RC>
+__device__ __forceinline__ void rec_pt(const Dev& D, const double* arr, long long m, int dir, long long Y,
+                                       Dual& aL, Dual& aR) {
+  Dual q[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const long long Z = shift2(D, m, dir, k - 2);
+    q[k] = Dual(arr[Z], Z == Y ? 1.0 : 0.0);
+  }
+  recon_point<RC>(q, aL, aR);
+}
+template <int RC>
+__device__ __forceinline__ void rec_val(const Dev& D, const double* arr, long long m, int dir, double& aL,
+                                        double& aR) {
+  double q[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q[k] = arr[shift2(D, m, dir, k - 2)];
+  recon_point<RC>(q, aL, aR);
+}
+
+// ---- edges: adjoint of E_e from the 8 reconstructed edge values, the edge speeds, eta j ----
+template <int RC>
+__global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
+  const Dev& D = A.D;
+  const long long X = aid();
+  if (X >= D.N) return;
+  const long long N = D.N;
+  double etaacc = 0.0;
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, c = (e + 2) % 3;
+    const double lam = A.lE[e * N + X];
+    if (lam == 0.0) {
+      for (int k = 0; k < 8; ++k) A.lEdge[(8LL * e + k) * N + X] = 0.0;
+      continue;
+    }
+    const long long Xc = shift(D, X, c, -1), Xa = shift(D, X, a, -1);
+    double in[12], dummy;
+    rec_val<RC>(D, D.Bin[a], Xc, c, dummy, in[0]);          // b_a bottom = upper value of a-face X - c
+    rec_val<RC>(D, D.Bin[a], X, c, in[1], dummy);           // b_a top = lower value of a-face X
+    rec_val<RC>(D, D.Us + a * N, Xc, c, dummy, in[2]);      // u_a* bottom
+    rec_val<RC>(D, D.Us + a * N, X, c, in[3], dummy);       // u_a* top
+    rec_val<RC>(D, D.Bin[c], Xa, a, dummy, in[4]);          // b_c left
+    rec_val<RC>(D, D.Bin[c], X, a, in[5], dummy);           // b_c right
+    rec_val<RC>(D, D.Us + c * N, Xa, a, dummy, in[6]);      // u_c* left
+    rec_val<RC>(D, D.Us + c * N, X, a, in[7], dummy);       // u_c* right
+    const double* Apa = D.Ap + a * N;
+    const double* Ama = D.Am + a * N;
+    const double* Apc = D.Ap + c * N;
+    const double* Amc = D.Am + c * N;
+    // Eq. (alpha-edge): the max keeps its first argument on ties (pmax)
+    const bool wa_p = dbits(Apa[Xc]) >= dbits(Apa[X]), wa_m = dbits(Ama[Xc]) >= dbits(Ama[X]);
+    const bool wc_p = dbits(Apc[Xa]) >= dbits(Apc[X]), wc_m = dbits(Amc[Xa]) >= dbits(Amc[X]);
+    in[8] = wa_p ? Apa[Xc] : Apa[X];
+    in[9] = wa_m ? Ama[Xc] : Ama[X];
+    in[10] = wc_p ? Apc[Xa] : Apc[X];
+    in[11] = wc_m ? Amc[Xa] : Amc[X];
+    double g[12];
+#pragma unroll 1
+    for (int i = 0; i < 12; ++i) {
+      Dual v[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = Dual(in[k], k == i ? 1.0 : 0.0);
+      const Dual E = q26_edge_emf(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11]);
+      g[i] = lam * E.t;
+    }
+    for (int k = 0; k < 8; ++k) A.lEdge[(8LL * e + k) * N + X] = g[k];
+    atomicAdd(&A.lAp[a * N + (wa_p ? Xc : X)], g[8]);
+    atomicAdd(&A.lAm[a * N + (wa_m ? Xc : X)], g[9]);
+    atomicAdd(&A.lAp[c * N + (wc_p ? Xa : X)], g[10]);
+    atomicAdd(&A.lAm[c * N + (wc_m ? Xa : X)], g[11]);
+    if (D.resistive) {  // E += eta j, j = (b_c[X] - b_c[X-a]) / h_a - (b_a[X] - b_a[X-c]) / h_c
+      const double* Ba = D.Bin[a];
+      const double* Bc = D.Bin[c];
+      const double j = (Bc[X] - Bc[Xa]) * D.hinv[a] - (Ba[X] - Ba[Xc]) * D.hinv[c];
+      etaacc += lam * j;
+      const double la = D.eta * lam * D.hinv[a], lc = D.eta * lam * D.hinv[c];
+      atomicAdd(&A.lB[c * N + X], la);
+      atomicAdd(&A.lB[c * N + Xa], -la);
+      atomicAdd(&A.lB[a * N + X], -lc);
+      atomicAdd(&A.lB[a * N + Xc], lc);
+    }
+  }
+  if (etaacc != 0.0) atomicAdd(A.lEta, etaacc);
+}
+
+// ---- edge reconstructions: adjoint of the face arrays b_d and u_d* ------------------------
+// Face array of direction d is reconstructed along t1 = d + 1 as the "a" array of e-edges with
+// e = d + 2 (bottom/top slots 0/1 for b, 2/3 for u*), and along t2 = d + 2 as the "c" array of
+// e-edges with e = d + 1 (left/right slots 4/5 for b, 6/7 for u*). Point m's lower value is the
+// top/right value at edge m; its upper value is the bottom/left value at edge m + t.
+// sum over the points m whose window holds Y of d(lower_m)/dY lam_lo[m] + d(upper_m)/dY lam_hi[m+1]
+template <int RC>
+__device__ __forceinline__ double gather_rec(const Dev& D, const double* arr, long long Y, int t,
+                                             const double* lam_lo, const double* lam_hi) {
+  double acc = 0.0;
+  const int nt = D.n[t];
+  const int k0 = nt >= 5 ? -2 : 0, k1 = nt >= 5 ? 2 : nt - 1;  // each distinct point once
+#pragma unroll 1
+  for (int k = k0; k <= k1; ++k) {
+    const long long m = shift2(D, Y, t, k);
+    Dual aL, aR;
+    rec_pt<RC>(D, arr, m, t, Y, aL, aR);
+    acc = fma(aL.t, lam_lo[m], acc);
+    acc = fma(aR.t, lam_hi[shift(D, m, t, 1)], acc);
+  }
+  return acc;
+}
+
+template <int RC>
+__global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
+  const Dev& D = A.D;
+  const long long Y = aid();
+  if (Y >= D.N) return;
+  const long long N = D.N;
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = (d + 1) % 3, e1 = (d + 2) % 3;  // d is "a" of e1, reconstructed along c(e1) = t1
+    const int t2 = (d + 2) % 3, e2 = (d + 1) % 3;  // d is "c" of e2, reconstructed along a(e2) = t2
+    const double* L1 = A.lEdge + 8LL * e1 * N;
+    const double* L2 = A.lEdge + 8LL * e2 * N;
+    double lb = gather_rec<RC>(D, D.Bin[d], Y, t1, L1 + 1 * N, L1 + 0 * N);
+    lb += gather_rec<RC>(D, D.Bin[d], Y, t2, L2 + 5 * N, L2 + 4 * N);
+    double lu = gather_rec<RC>(D, D.Us + d * N, Y, t1, L1 + 3 * N, L1 + 2 * N);
+    lu += gather_rec<RC>(D, D.Us + d * N, Y, t2, L2 + 7 * N, L2 + 6 * N);
+    atomicAdd(&A.lB[d * N + Y], lb);
+    A.lUs[d * N + Y] = lu;
+  }
+}
+
+// ---- faces: adjoint of the Riemann solve -------------------------------------------------
+template <int RC, int RS>
+__global__ void __launch_bounds__(128) k_adj_faces(AdjDev A, int dir) {
+  const Dev& D = A.D;
+  const long long f = aid();
+  if (f >= D.N) return;
+  const long long N = D.N;
+  const int a = (dir + 1) % 3, c = (dir + 2) % 3;
+  const int slot[7] = {0, 1 + dir, 1 + a, 1 + c, 4, 5 + a, 5 + c};
+  double WL[7], WR[7];
+  const long long fl = shift(D, f, dir, -1);
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    double lo, hi;
+    rec_val<RC>(D, D.P + slot[v] * N, fl, dir, lo, WL[v]);
+    rec_val<RC>(D, D.P + slot[v] * N, f, dir, WR[v], hi);
+  }
+  const double bn = D.Bin[dir][f];
+  const double* lF = A.lF + 5LL * dir * N;
+  const double lf[5] = {lF[0 * N + f], lF[(1 + dir) * N + f], lF[(1 + a) * N + f], lF[(1 + c) * N + f],
+                        lF[4 * N + f]};
+  const double lap = A.lAp[dir * N + f], lam_ = A.lAm[dir * N + f], lus = A.lUs[dir * N + f];
+#pragma unroll 1
+  for (int i = 0; i < 15; ++i) {
+    FaceStateT<Dual> sl, sr;
+    Dual* pl = &sl.rho;
+    Dual* pr = &sr.rho;
+    for (int v = 0; v < 7; ++v) {
+      pl[v] = Dual(WL[v], i == v ? 1.0 : 0.0);
+      pr[v] = Dual(WR[v], i == 7 + v ? 1.0 : 0.0);
+    }
+    const Dual b = Dual(bn, i == 14 ? 1.0 : 0.0);
+    Dual F[5], ap, am, us;
+    riemann<RS>(sl, sr, b, D.gam, D.gm1inv, F, ap, am, us);
+    double g = lap * ap.t + lam_ * am.t + lus * us.t;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) g = fma(lf[v], F[v].t, g);
+    if (i < 14)
+      A.lLR[(14LL * dir + i) * N + f] = g;
+    else
+      atomicAdd(&A.lB[dir * N + f], g);
+  }
+}
+
+// ---- Joule flux eta (j x b)_d (bilinear; by hand) ----------------------------------------
+__global__ void __launch_bounds__(128) k_adj_joule(AdjDev A, int d) {
+  const Dev& D = A.D;
+  const long long X = aid();
+  if (X >= D.N || !D.resistive) return;
+  const long long N = D.N;
+  const double lam = A.lF[(5LL * d + 4) * N + X];
+  if (lam == 0.0) return;
+  const int a = (d + 1) % 3, c = (d + 2) % 3;
+  const double* Ba = D.Bin[a];
+  const double* Bc = D.Bin[c];
+  auto jedge = [&](int e, long long Y) {
+    const int ae = (e + 1) % 3, ce = (e + 2) % 3;
+    return (D.Bin[ce][Y] - D.Bin[ce][shift(D, Y, ae, -1)]) * D.hinv[ae] -
+           (D.Bin[ae][Y] - D.Bin[ae][shift(D, Y, ce, -1)]) * D.hinv[ce];
+  };
+  // d j_e(Y) += w  ->  dB scatter
+  auto jadj = [&](int e, long long Y, double w) {
+    const int ae = (e + 1) % 3, ce = (e + 2) % 3;
+    atomicAdd(&A.lB[ce * N + Y], w * D.hinv[ae]);
+    atomicAdd(&A.lB[ce * N + shift(D, Y, ae, -1)], -w * D.hinv[ae]);
+    atomicAdd(&A.lB[ae * N + Y], -w * D.hinv[ce]);
+    atomicAdd(&A.lB[ae * N + shift(D, Y, ce, -1)], w * D.hinv[ce]);
+  };
+  const long long Xc = shift(D, X, c, 1), Xa = shift(D, X, a, 1), Xmd = shift(D, X, d, -1);
+  const long long Xmdc = shift(D, Xmd, c, 1), Xmda = shift(D, Xmd, a, 1);
+  const double ja = 0.5 * (jedge(a, X) + jedge(a, Xc)), jc = 0.5 * (jedge(c, X) + jedge(c, Xa));
+  const double bcbar = 0.25 * (Bc[Xmd] + Bc[X] + Bc[Xmdc] + Bc[Xc]);
+  const double babar = 0.25 * (Ba[Xmd] + Ba[X] + Ba[Xmda] + Ba[Xa]);
+  // flux = eta (ja bcbar - jc babar)
+  atomicAdd(A.lEta, lam * (ja * bcbar - jc * babar));
+  const double wja = 0.5 * D.eta * lam * bcbar, wjc = -0.5 * D.eta * lam * babar;
+  jadj(a, X, wja);
+  jadj(a, Xc, wja);
+  jadj(c, X, wjc);
+  jadj(c, Xa, wjc);
+  const double wbc = 0.25 * D.eta * lam * ja, wba = -0.25 * D.eta * lam * jc;
+  atomicAdd(&A.lB[c * N + Xmd], wbc);
+  atomicAdd(&A.lB[c * N + X], wbc);
+  atomicAdd(&A.lB[c * N + Xmdc], wbc);
+  atomicAdd(&A.lB[c * N + Xc], wbc);
+  atomicAdd(&A.lB[a * N + Xmd], wba);
+  atomicAdd(&A.lB[a * N + X], wba);
+  atomicAdd(&A.lB[a * N + Xmda], wba);
+  atomicAdd(&A.lB[a * N + Xa], wba);
+}
+
+// ---- face reconstructions: adjoint of the primitives --------------------------------------
+template <int RC>
+__global__ void __launch_bounds__(128) k_adj_face_rec(AdjDev A) {
+  const Dev& D = A.D;
+  const long long q = aid();
+  if (q >= D.N) return;
+  const long long N = D.N;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int dir = 0; dir < 3; ++dir) {
+    const int a = (dir + 1) % 3, c = (dir + 2) % 3;
+    const int slot[7] = {0, 1 + dir, 1 + a, 1 + c, 4, 5 + a, 5 + c};
+    const double* lLR = A.lLR + 14LL * dir * N;
+    for (int v = 0; v < 7; ++v)  // point m's lower value = right state of face m, upper = left of face m+1
+      acc[slot[v]] += gather_rec<RC>(D, D.P + slot[v] * N, q, dir, lLR + (7 + v) * N, lLR + v * N);
+  }
+  for (int v = 0; v < 8; ++v) A.lP[v * N + q] = acc[v];
+}
+
+// ---- primitives: adjoint of cons -> prim ------------------------------------------------
+template <class T>
+__device__ __forceinline__ void prim_t(double gam, const T* u, const T* blo, const T* bhi, T* w) {
+  const T rho = u[0];
+  const T rinv = rcp(rho);
+  const T u0 = u[1] * rinv, u1 = u[2] * rinv, u2 = u[3] * rinv;
+  const T b0 = 0.5 * (blo[0] + bhi[0]);
+  const T b1 = 0.5 * (blo[1] + bhi[1]);
+  const T b2 = 0.5 * (blo[2] + bhi[2]);
+  const T u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
+  const T b2s = fma(b0, b0, fma(b1, b1, b2 * b2));
+  const T eint = u[4] - 0.5 * fma(rho, u2s, b2s);
+  w[0] = rho; w[1] = u0; w[2] = u1; w[3] = u2;
+  w[4] = (gam - 1.0) * eint;
+  w[5] = b0; w[6] = b1; w[7] = b2;
+}
+
+__global__ void __launch_bounds__(128) k_adj_prim(AdjDev A) {
+  const Dev& D = A.D;
+  const long long X = aid();
+  if (X >= D.N) return;
+  const long long N = D.N;
+  double lp[8];
+  for (int v = 0; v < 8; ++v) lp[v] = A.lP[v * N + X];
+  double u[5], blo[3], bhi[3];
+  long long Xp[3];
+  for (int v = 0; v < 5; ++v) u[v] = D.Uin[v * N + X];
+  for (int d = 0; d < 3; ++d) {
+    Xp[d] = shift(D, X, d, 1);
+    blo[d] = D.Bin[d][X];
+    bhi[d] = D.Bin[d][Xp[d]];
+  }
+#pragma unroll 1
+  for (int i = 0; i < 11; ++i) {
+    Dual du[5], dl[3], dh[3], w[8];
+    for (int v = 0; v < 5; ++v) du[v] = Dual(u[v], i == v ? 1.0 : 0.0);
+    for (int d = 0; d < 3; ++d) {
+      dl[d] = Dual(blo[d], i == 5 + d ? 1.0 : 0.0);
+      dh[d] = Dual(bhi[d], i == 8 + d ? 1.0 : 0.0);
+    }
+    prim_t(D.gam, du, dl, dh, w);
+    double g = 0.0;
+    for (int v = 0; v < 8; ++v) g = fma(lp[v], w[v].t, g);
+    if (i < 5)
+      A.lU[i * N + X] += g;
+    else if (i < 8)
+      atomicAdd(&A.lB[(i - 5) * N + X], g);
+    else
+      atomicAdd(&A.lB[(i - 8) * N + Xp[i - 8]], g);
+  }
+}
+
+// ---- update: lF, lE = D^T lam (Eqs. rk:increment-state, rk:increment-bfield) ---------------
+// lF = s_old * lF + scale * D^T(lU, lB) (and lE likewise): s_old = 0 overwrites.
+__global__ void __launch_bounds__(256) k_adj_update(Dev D, const double* lU, const double* lB, double* lF,
+                                                    double* lE, double scale, double s_old) {
+  const long long X = aid();
+  if (X >= D.N) return;
+  const long long N = D.N;
+  for (int d = 0; d < 3; ++d) {
+    const long long Xm = shift(D, X, d, -1);
+    const double k = scale * D.dt * D.hinv[d];
+    for (int v = 0; v < 5; ++v) {
+      const double g = k * (lU[v * N + X] - lU[v * N + Xm]);
+      double* t = &lF[(5LL * d + v) * N + X];
+      *t = s_old == 0.0 ? g : fma(s_old, *t, g);
+    }
+  }
+  for (int e = 0; e < 3; ++e) {
+    // E_e enters B_{e+1} as its "c" EMF and B_{e+2} as its "a" EMF (see incr_face)
+    const int d1 = (e + 1) % 3, a1 = (d1 + 1) % 3;  // B_d1[Y]: +dt/h_a1 E_e[Y] - dt/h_a1 E_e[Y + a1]
+    const int d2 = (e + 2) % 3, c2 = (d2 + 2) % 3;  // B_d2[Y]: -dt/h_c2 E_e[Y] + dt/h_c2 E_e[Y + c2]
+    const double g = scale * D.dt *
+                     ((lB[d1 * N + X] - lB[d1 * N + shift(D, X, a1, -1)]) * D.hinv[a1] +
+                      (lB[d2 * N + shift(D, X, c2, -1)] - lB[d2 * N + X]) * D.hinv[c2]);
+    double* t = &lE[e * N + X];
+    *t = s_old == 0.0 ? g : fma(s_old, *t, g);
+  }
+}
+
+template <int RC>
+static void adj_flux_r(const AdjDev& A, int rs, cudaStream_t st) {
+  const unsigned nb = (unsigned)((A.D.N + 127) / 128);
+  k_adj_edges<RC><<<nb, 128, 0, st>>>(A);
+  k_adj_edge_rec<RC><<<nb, 128, 0, st>>>(A);
+  for (int dir = 0; dir < 3; ++dir) {
+    if (rs == RS_HLL) k_adj_faces<RC, RS_HLL><<<nb, 128, 0, st>>>(A, dir);
+    else if (rs == RS_HLLD) k_adj_faces<RC, RS_HLLD><<<nb, 128, 0, st>>>(A, dir);
+    else k_adj_faces<RC, RS_LLF><<<nb, 128, 0, st>>>(A, dir);
+    if (A.D.resistive) k_adj_joule<<<nb, 128, 0, st>>>(A, dir);
+  }
+  k_adj_face_rec<RC><<<nb, 128, 0, st>>>(A);
+  k_adj_prim<<<nb, 128, 0, st>>>(A);
+}
+
+// adjoint of the flux function at A.D's stage input (its P, Ap, Am, Us must be current)
+void launch_adj_flux(const AdjDev& A, int recon, int rs, cudaStream_t st) {
+  switch (recon) {
+    case REC_PC: adj_flux_r<REC_PC>(A, rs, st); break;
+    case REC_PLM_MC: adj_flux_r<REC_PLM_MC>(A, rs, st); break;
+    case REC_PLM_MINMOD: adj_flux_r<REC_PLM_MINMOD>(A, rs, st); break;
+    default: adj_flux_r<REC_PPM>(A, rs, st); break;
+  }
+}
+
+void launch_adj_update(const Dev& D, const double* lU, const double* lB, double* lF, double* lE, double scale,
+                       double s_old, cudaStream_t st) {
+  k_adj_update<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(D, lU, lB, lF, lE, scale, s_old);
+}
+
+__global__ void k_axpy3(long long n, double* y, const double* a, const double* b) {
+  const long long i = aid();
+  if (i < n) y[i] += a[i] + b[i];
+}
+void launch_axpy3(long long n, double* y, const double* a, const double* b, cudaStream_t st) {
+  k_axpy3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, y, a, b);
+}
+
+}  // namespace mhd

@@ -25,6 +25,8 @@ struct mhd_ctx {
   struct Rec { int cls; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   size_t ev_next;
+  // adjoint scratch (allocated on the first mhd_step_adjoint call)
+  double* adj;
 };
 
 namespace {
@@ -135,6 +137,7 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   for (int k = 0; k < MHD_K_COUNT; ++k) c->launches[k] = 0;
   c->prof = false;
   c->ev_next = 0;
+  c->adj = nullptr;
   mhd::Dev& D = c->base;
   std::memset(&D, 0, sizeof(D));
   D.n[0] = cfg->nx; D.n[1] = cfg->ny; D.n[2] = cfg->nz;
@@ -193,6 +196,7 @@ void mhd_destroy(mhd_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->adj) cudaFree(ctx->adj);
   cudaFree(ctx->scratch);
   delete ctx;
 }
@@ -350,6 +354,126 @@ mhd_status mhd_divb(mhd_ctx* ctx, const mhd_state* state, double* max_abs_divb, 
   if (s != MHD_OK) return s;
   std::memcpy(max_abs_divb, &h[0], sizeof(double));
   std::memcpy(max_abs_b, &h[1], sizeof(double));
+  return MHD_OK;
+}
+
+mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_state* lam, double dt, int scheme,
+                            double eta, double* dL_deta) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state) || !state_ok(lam)) return fail(ctx, MHD_ERR_ARG, "state or adjoint has a NULL array");
+  if (!(dt > 0) || !(dt < 1e300)) return fail(ctx, MHD_ERR_ARG, "dt must be finite and > 0");
+  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
+  Decoded sc;
+  mhd_status s = decode(ctx, scheme, sc);
+  if (s != MHD_OK) return s;
+  if (sc.emf != mhd::EMF_Q26) return fail(ctx, MHD_ERR_UNSUPPORTED, "the adjoint covers the Q26 EMF compute");
+  const long long N = ctx->base.N;
+  cudaStream_t st = ctx->stream;
+  // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
+  // lB0 3, lam2 8 (doubles per cell) + eta accumulator
+  const size_t nd = 125;
+  if (!ctx->adj) {
+    s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + 8) * sizeof(double)), "cudaMalloc of adjoint scratch");
+    if (s != MHD_OK) { ctx->adj = nullptr; return s; }
+  }
+  double* q = ctx->adj;
+  auto take = [&](long long k) { double* r = q; q += k * N; return r; };
+  double* lF = take(15);
+  double* lE = take(3);
+  double* lAp = take(3);
+  double* lAm = take(3);
+  double* lUs = take(3);
+  double* lEdge = take(24);
+  double* lLR = take(42);
+  double* lP = take(8);
+  double* lU1 = take(5);
+  double* lB1 = take(3);
+  double* lU0 = take(5);
+  double* lB0 = take(3);
+  double* lamU = take(5);
+  double* lamB = take(3);
+  double* lEta = q;
+
+  mhd::Dev D = ctx->base;
+  D.dt = dt;
+  D.eta = eta;
+  // the resistive terms are linear in eta: their derivative in eta is needed even at eta = 0,
+  // where they add exact zeros to the forward values
+  D.resistive = 1;
+  D.emf = sc.emf;
+  if (!sc.fofc) D.fofc_criteria = 0;
+  D.U0 = state->cons;
+  D.B0[0] = state->b0; D.B0[1] = state->b1; D.B0[2] = state->b2;
+  D.Uout = ctx->U1;
+  for (int d = 0; d < 3; ++d) D.Bout[d] = ctx->B1[d];
+  D.combine = 0;
+  D.stage = 0;
+  const double* lamb[3] = {lam->b0, lam->b1, lam->b2};
+  cudaError_t e = cudaMemsetAsync(D.counters, 0, 4 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lamU, lam->cons, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+    e = cudaMemcpyAsync(lamB + d * N, lamb[d], N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lEta, 0, sizeof(double), st);
+  if ((s = cuda_check(ctx, e, "adjoint set-up")) != MHD_OK) return s;
+
+  // forward stage 1 again: S^{n+1/2} into the context's stage scratch
+  D.Uin = D.U0;
+  for (int d = 0; d < 3; ++d) D.Bin[d] = D.B0[d];
+  run_stage(ctx, D, sc);
+
+  auto adj_dev = [&](const mhd::Dev& Ds, double* lU, double* lB) {
+    mhd::AdjDev A;
+    A.D = Ds;
+    A.lF = lF; A.lE = lE; A.lAp = lAp; A.lAm = lAm; A.lUs = lUs; A.lEdge = lEdge; A.lLR = lLR; A.lP = lP;
+    A.lU = lU; A.lB = lB; A.lEta = lEta;
+    return A;
+  };
+  auto recompute = [&](const mhd::Dev& Ds) {  // P, alpha+-, u* of the stage input
+    mhd::launch_prim(Ds, st);
+    for (int dir = 0; dir < 3; ++dir) mhd::launch_face(Ds, dir, sc.recon, sc.rs, ctx->seg, st);
+  };
+  auto zero = [&](double* p, long long k) { return cudaMemsetAsync(p, 0, k * N * sizeof(double), st); };
+
+  // stage 2 flux function at S^{n+1/2}: adjoint inputs (D^T lam) / 2
+  mhd::Dev D1 = D;
+  D1.Uin = ctx->U1;
+  for (int d = 0; d < 3; ++d) D1.Bin[d] = ctx->B1[d];
+  recompute(D1);
+  mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
+  e = zero(lU1, 5);
+  if (e == cudaSuccess) e = zero(lB1, 3);
+  if (e == cudaSuccess) e = zero(lAp, 6);
+  if ((s = cuda_check(ctx, e, "cudaMemsetAsync")) != MHD_OK) return s;
+  mhd::launch_adj_flux(adj_dev(D1, lU1, lB1), sc.recon, sc.rs, st);
+
+  // stage 1 flux function at S^n: (D^T lam) / 2 + D^T lam_{n+1/2}
+  mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
+  mhd::launch_adj_update(D, lU1, lB1, lF, lE, 1.0, 1.0, st);
+  mhd::Dev D0 = D;
+  recompute(D0);
+  e = zero(lU0, 5);
+  if (e == cudaSuccess) e = zero(lB0, 3);
+  if (e == cudaSuccess) e = zero(lAp, 6);
+  if ((s = cuda_check(ctx, e, "cudaMemsetAsync")) != MHD_OK) return s;
+  mhd::launch_adj_flux(adj_dev(D0, lU0, lB0), sc.recon, sc.rs, st);
+
+  // lam_n = lam_{n+1} + lam_{n+1/2} + (stage-1 part), back into the caller's arrays
+  mhd::launch_axpy3(5 * N, lamU, lU1, lU0, st);
+  mhd::launch_axpy3(3 * N, lamB, lB1, lB0, st);
+  e = cudaMemcpyAsync(lam->cons, lamU, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  double* lamb_out[3] = {lam->b0, lam->b1, lam->b2};
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+    e = cudaMemcpyAsync(lamb_out[d], lamB + d * N, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if ((s = cuda_check(ctx, e, "adjoint write-back")) != MHD_OK) return s;
+  if ((s = cuda_check(ctx, cudaGetLastError(), "kernel launch")) != MHD_OK) return s;
+  if (dL_deta) {
+    double h = 0.0;
+    e = cudaMemcpyAsync(&h, lEta, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if ((s = cuda_check(ctx, e, "read d/deta")) != MHD_OK) return s;
+    *dL_deta += h;
+  }
   return MHD_OK;
 }
 

@@ -11,6 +11,8 @@
 
 namespace mhd {
 
+using ::fma;  // the double overload stays visible beside the Dual one below
+
 enum { REC_PC = 0, REC_PLM_MC = 1, REC_PLM_MINMOD = 2, REC_PPM = 3 };
 enum { RS_HLL = 0, RS_HLLD = 1, RS_LLF = 2 };
 enum { EMF_Q26 = 0, EMF_FS18 = 1, EMF_B25A = 2 };
@@ -77,6 +79,58 @@ __device__ __forceinline__ double sqrt_(double x) {
   return is_zero(x) ? 0.0 : r;
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Forward-mode dual number (value + one tangent) for the adjoint kernels' local Jacobians. Every
+// decision (comparison, min/max, sign, limiter branch) is taken on the value exactly as in the
+// double code, so a derivative is the derivative on the branch the forward pass took.
+// ------------------------------------------------------------------------------------------
+struct Dual {
+  double v, t;
+  __device__ __forceinline__ Dual() {}
+  __device__ __forceinline__ Dual(double x) : v(x), t(0.0) {}  // NOLINT: constants promote
+  __device__ __forceinline__ Dual(double x, double dx) : v(x), t(dx) {}
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.t + b.t); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.t - b.t); }
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.t); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, fma(a.t, b.v, a.v * b.t)); }
+__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+__device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) {
+  return Dual(fma(a.v, b.v, c.v), fma(a.t, b.v, fma(a.v, b.t, c.t)));
+}
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ double val(const Dual& x) { return x.v; }
+__device__ __forceinline__ Dual vmax(Dual a, Dual b) { return okey(a.v) >= okey(b.v) ? a : b; }
+__device__ __forceinline__ Dual vmin(Dual a, Dual b) { return okey(a.v) <= okey(b.v) ? a : b; }
+__device__ __forceinline__ Dual pmax(Dual a, Dual b) { return dbits(a.v) >= dbits(b.v) ? a : b; }
+__device__ __forceinline__ Dual pmin(Dual a, Dual b) { return dbits(a.v) <= dbits(b.v) ? a : b; }
+__device__ __forceinline__ Dual vabs(Dual x) { return dbits(x.v) < 0 ? -x : x; }
+__device__ __forceinline__ bool gt0(const Dual& x) { return gt0(x.v); }
+__device__ __forceinline__ bool lt0(const Dual& x) { return lt0(x.v); }
+__device__ __forceinline__ bool ge0(const Dual& x) { return ge0(x.v); }
+__device__ __forceinline__ bool vgt(const Dual& a, const Dual& b) { return vgt(a.v, b.v); }
+__device__ __forceinline__ bool is_zero(const Dual& x) { return is_zero(x.v); }
+__device__ __forceinline__ bool same_sign(const Dual& a, const Dual& b) { return same_sign(a.v, b.v); }
+__device__ __forceinline__ double sgnd(const Dual& x) { return sgnd(x.v); }
+// |m| with the sign of s
+__device__ __forceinline__ Dual with_sign(Dual m, Dual s) {
+  const bool flip = (dbits(m.v) < 0) != (dbits(s.v) < 0);
+  return Dual(with_sign(m.v, s.v), flip ? -m.t : m.t);
+}
+__device__ __forceinline__ Dual rcp(Dual x) {
+  const double r = rcp(x.v);
+  return Dual(r, -x.t * r * r);
+}
+__device__ __forceinline__ Dual rsqrt_(Dual x) {
+  const double r = rsqrt_(x.v);
+  return Dual(r, -0.5 * x.t * r * r * r);
+}
+__device__ __forceinline__ Dual sqrt_(Dual x) {
+  const double r = sqrt_(x.v);
+  return Dual(r, is_zero(r) ? 0.0 : 0.5 * x.t / r);
+}
+
 // ------------------------------------------------------------------------------------------
 // Periodic line of points along one axis
 // ------------------------------------------------------------------------------------------
@@ -112,15 +166,17 @@ template <> struct Rec<REC_PC> {
 };
 
 // half of the monotonised-central slope: sgn * min(|dl|, |dr|, |dl + dr| / 4)
-__device__ __forceinline__ double half_slope_mc(double dl, double dr) {
-  if (!same_sign(dl, dr)) return 0.0;
-  double m = pmin(vabs(dl), vabs(dr));
+template <class T>
+__device__ __forceinline__ T half_slope_mc(T dl, T dr) {
+  if (!same_sign(dl, dr)) return T(0.0);
+  T m = pmin(vabs(dl), vabs(dr));
   m = pmin(m, 0.25 * vabs(dl + dr));
   return with_sign(m, dl);
 }
 // half of the minmod slope: sgn * min(|dl|, |dr|) / 2
-__device__ __forceinline__ double half_slope_minmod(double dl, double dr) {
-  if (!same_sign(dl, dr)) return 0.0;
+template <class T>
+__device__ __forceinline__ T half_slope_minmod(T dl, T dr) {
+  if (!same_sign(dl, dr)) return T(0.0);
   return with_sign(0.5 * pmin(vabs(dl), vabs(dr)), dl);
 }
 
@@ -155,29 +211,32 @@ template <> struct Rec<REC_PLM_MINMOD> : RecPLM<REC_PLM_MINMOD> {};
 // interface value between points 0 and 1 is q0 + (q1 - q0)/2 - (dq2_1 - dq2_0)/12, and with
 // s1 = aR - a, s2 = a - aL the constraint quantities are aR - aL = s1 + s2 and
 // 6 (a - (aL + aR)/2) = 3 (s2 - s1), the corrections 3a - 2aR = a - 2 s1, 3a - 2aL = a + 2 s2.
-__device__ __forceinline__ double vl_slope2(double dl, double dr) {
-  if (!same_sign(dl, dr)) return 0.0;
-  const double s = dl + dr;
-  const double m = pmin(vabs(s), 4.0 * pmin(vabs(dl), vabs(dr)));
+template <class T>
+__device__ __forceinline__ T vl_slope2(T dl, T dr) {
+  if (!same_sign(dl, dr)) return T(0.0);
+  const T s = dl + dr;
+  const T m = pmin(vabs(s), 4.0 * pmin(vabs(dl), vabs(dr)));
   return with_sign(m, s);
 }
-__device__ __forceinline__ double ppm_iface(double q0, double dq, double d20, double d21) {
-  return fma(-(d21 - d20), 1.0 / 12.0, fma(0.5, dq, q0));
+template <class T>
+__device__ __forceinline__ T ppm_iface(T q0, T dq, T d20, T d21) {
+  return fma(-(d21 - d20), T(1.0 / 12.0), fma(T(0.5), dq, q0));
 }
-__device__ __forceinline__ void ppm_mono(double a, double& aL, double& aR) {
-  const double s1 = aR - a, s2 = a - aL;
+template <class T>
+__device__ __forceinline__ void ppm_mono(T a, T& aL, T& aR) {
+  const T s1 = aR - a, s2 = a - aL;
   if (!same_sign(s1, s2)) {
     aL = a;
     aR = a;
     return;
   }
-  const double da = s1 + s2;
-  const double a6 = 3.0 * (s2 - s1);
-  const double p1 = da * a6, p2 = da * da;
+  const T da = s1 + s2;
+  const T a6 = 3.0 * (s2 - s1);
+  const T p1 = da * a6, p2 = da * da;
   if (vgt(p1, p2)) {
-    aL = fma(-2.0, s1, a);
+    aL = fma(T(-2.0), s1, a);
   } else if (vgt(-p2, p1)) {
-    aR = fma(2.0, s2, a);
+    aR = fma(T(2.0), s2, a);
   }
 }
 
@@ -221,30 +280,55 @@ template <> struct Rec<REC_PPM> {
   }
 };
 
+// Point-wise form of the sweeps (for the adjoint kernels): lower and upper values of point m from
+// q[0..4] = values at m-2 .. m+2, with the same expressions (and therefore the same values and
+// branch decisions) as the sliding windows above.
+template <int R, class T>
+__device__ __forceinline__ void recon_point(const T* q, T& aL, T& aR) {
+  if (R == REC_PC) {
+    aL = q[2];
+    aR = q[2];
+  } else if (R == REC_PLM_MC || R == REC_PLM_MINMOD) {
+    const T dl = q[2] - q[1], dr = q[3] - q[2];
+    const T h = R == REC_PLM_MC ? half_slope_mc(dl, dr) : half_slope_minmod(dl, dr);
+    aL = q[2] - h;
+    aR = q[2] + h;
+  } else {
+    const T e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3];
+    const T d0 = vl_slope2(e0, e1), d1 = vl_slope2(e1, e2), d2 = vl_slope2(e2, e3);
+    aL = ppm_iface(q[1], e1, d0, d1);
+    aR = ppm_iface(q[2], e2, d1, d2);
+    ppm_mono(q[2], aL, aR);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Riemann problem on one face, in the face frame (n, t1, t2).
 // W = {rho, u_n, u_t1, u_t2, p, b_t1, b_t2}; bn = stored face field.
 // ------------------------------------------------------------------------------------------
-struct FaceState {
-  double rho, u, v, w, p, by, bz;
+template <class T> struct FaceStateT {
+  T rho, u, v, w, p, by, bz;
 };
+using FaceState = FaceStateT<double>;
 
-struct PhysFlux {
-  double U[5], F[5];
-  double pt, e, cf;
+template <class T> struct PhysFluxT {
+  T U[5], F[5];
+  T pt, e, cf;
 };
+using PhysFlux = PhysFluxT<double>;
 
 // Ideal-MHD flux of Eq. (mhd:conservation-laws) in the face frame, energy flux with e_tot,
 // and the fast magnetosonic speed of Eq. (waves:fast-speed) along the normal.
-__device__ __forceinline__ void phys(const FaceState& s, double bn, double gam, double gm1inv,
-                                     PhysFlux& o) {
-  const double bn2 = bn * bn;
-  const double b2 = fma(s.by, s.by, fma(s.bz, s.bz, bn2));
-  const double u2 = fma(s.u, s.u, fma(s.v, s.v, s.w * s.w));
-  const double e = fma(s.p, gm1inv, 0.5 * fma(s.rho, u2, b2));
-  const double pt = fma(0.5, b2, s.p);
-  const double ub = fma(s.u, bn, fma(s.v, s.by, s.w * s.bz));
-  const double mu = s.rho * s.u;
+template <class T>
+__device__ __forceinline__ void phys(const FaceStateT<T>& s, T bn, double gam, double gm1inv,
+                                     PhysFluxT<T>& o) {
+  const T bn2 = bn * bn;
+  const T b2 = fma(s.by, s.by, fma(s.bz, s.bz, bn2));
+  const T u2 = fma(s.u, s.u, fma(s.v, s.v, s.w * s.w));
+  const T e = fma(s.p, gm1inv, 0.5 * fma(s.rho, u2, b2));
+  const T pt = fma(0.5, b2, s.p);
+  const T ub = fma(s.u, bn, fma(s.v, s.by, s.w * s.bz));
+  const T mu = s.rho * s.u;
   o.U[0] = s.rho;
   o.U[1] = mu;
   o.U[2] = s.rho * s.v;
@@ -257,59 +341,62 @@ __device__ __forceinline__ void phys(const FaceState& s, double bn, double gam, 
   o.F[4] = fma(e + pt, s.u, -ub * bn);
   o.pt = pt;
   o.e = e;
-  const double rinv = rcp(s.rho);
-  const double a2 = gam * s.p * rinv;
-  const double sum = fma(b2, rinv, a2);
-  double disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
+  const T rinv = rcp(s.rho);
+  const T a2 = gam * s.p * rinv;
+  const T sum = fma(b2, rinv, a2);
+  T disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
   disc = pmax(disc, 0.0);
   o.cf = sqrt_(0.5 * (sum + sqrt_(disc)));
 }
 
 // HLL-type two-state flux; inv = 1 / (ap + am), or 0 when ap + am = 0 (then the left flux).
-__device__ __forceinline__ void two_state(const PhysFlux& L, const PhysFlux& R, double ap,
-                                          double am, double inv, bool zero, double* F) {
+template <class T>
+__device__ __forceinline__ void two_state(const PhysFluxT<T>& L, const PhysFluxT<T>& R, T ap,
+                                          T am, T inv, bool zero, T* F) {
   if (zero) {
     for (int v = 0; v < 5; ++v) F[v] = L.F[v];
     return;
   }
-  const double wl = ap * inv, wr = am * inv, wd = ap * am * inv;
+  const T wl = ap * inv, wr = am * inv, wd = ap * am * inv;
   for (int v = 0; v < 5; ++v) F[v] = fma(wl, L.F[v], fma(wr, R.F[v], -wd * (R.U[v] - L.U[v])));
 }
 
 // Star state on one side of the contact (MK05 Eqs. 43-48).
-struct Star {
-  double rs, vs, ws, bys, bzs, es;
+template <class T> struct StarT {
+  T rs, vs, ws, bys, bzs, es;
 };
-__device__ __forceinline__ void star_state(const FaceState& q, const PhysFlux& ph, double S, double SM,
-                                           double ptS, double bn, double bn2, Star& o) {
-  const double su = S - q.u;
-  const double ssm = S - SM;
-  const double ssminv = rcp(ssm);
-  const double rsu = q.rho * su;
+template <class T>
+__device__ __forceinline__ void star_state(const FaceStateT<T>& q, const PhysFluxT<T>& ph, T S, T SM,
+                                           T ptS, T bn, T bn2, StarT<T>& o) {
+  const T su = S - q.u;
+  const T ssm = S - SM;
+  const T ssminv = rcp(ssm);
+  const T rsu = q.rho * su;
   o.rs = rsu * ssminv;
-  const double dd = fma(rsu, ssm, -bn2);
-  const double scale = fma(rsu, su, bn2);
+  const T dd = fma(rsu, ssm, -bn2);
+  const T scale = fma(rsu, su, bn2);
   if (!vgt(vabs(dd), 1e-12 * scale)) {  // degenerate: no tangential change across the fast wave
     o.vs = q.v;
     o.ws = q.w;
     o.bys = q.by;
     o.bzs = q.bz;
   } else {
-    const double ddinv = rcp(dd);
-    const double cv = bn * (SM - q.u) * ddinv;
-    const double cb = fma(rsu, su, -bn2) * ddinv;
+    const T ddinv = rcp(dd);
+    const T cv = bn * (SM - q.u) * ddinv;
+    const T cb = fma(rsu, su, -bn2) * ddinv;
     o.vs = fma(-q.by, cv, q.v);
     o.ws = fma(-q.bz, cv, q.w);
     o.bys = q.by * cb;
     o.bzs = q.bz * cb;
   }
-  const double vb = fma(q.u, bn, fma(q.v, q.by, q.w * q.bz));
-  const double vbs = fma(SM, bn, fma(o.vs, o.bys, o.ws * o.bzs));
+  const T vb = fma(q.u, bn, fma(q.v, q.by, q.w * q.bz));
+  const T vbs = fma(SM, bn, fma(o.vs, o.bys, o.ws * o.bzs));
   o.es = (fma(su, ph.e, -ph.pt * q.u) + fma(ptS, SM, bn * (vb - vbs))) * ssminv;
 }
 
-__device__ __forceinline__ FaceState pick(bool left, const FaceState& a, const FaceState& b) {
-  FaceState r;
+template <class T>
+__device__ __forceinline__ FaceStateT<T> pick(bool left, const FaceStateT<T>& a, const FaceStateT<T>& b) {
+  FaceStateT<T> r;
   r.rho = left ? a.rho : b.rho;
   r.u = left ? a.u : b.u;
   r.v = left ? a.v : b.v;
@@ -319,7 +406,8 @@ __device__ __forceinline__ FaceState pick(bool left, const FaceState& a, const F
   r.bz = left ? a.bz : b.bz;
   return r;
 }
-__device__ __forceinline__ void pick(bool left, const PhysFlux& a, const PhysFlux& b, PhysFlux& r) {
+template <class T>
+__device__ __forceinline__ void pick(bool left, const PhysFluxT<T>& a, const PhysFluxT<T>& b, PhysFluxT<T>& r) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     r.U[v] = left ? a.U[v] : b.U[v];
@@ -333,9 +421,10 @@ __device__ __forceinline__ void pick(bool left, const PhysFlux& a, const PhysFlu
 // the contact given by sgn(S_M); only that side's star state is formed, and the other side's star
 // state and the double-star state (MK05 Eqs. 49-63) only when the face lies inside that side's
 // rotational wave. Same values as forming all four states and selecting.
-__device__ __forceinline__ void hlld(const FaceState& sl, const FaceState& sr, double bn,
-                                     const PhysFlux& L, const PhysFlux& R, double SL, double SR,
-                                     double* F) {
+template <class T>
+__device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T>& sr, T bn,
+                                     const PhysFluxT<T>& L, const PhysFluxT<T>& R, T SL, T SR,
+                                     T* F) {
   if (gt0(SL)) {
     for (int v = 0; v < 5; ++v) F[v] = L.F[v];
     return;
@@ -344,24 +433,24 @@ __device__ __forceinline__ void hlld(const FaceState& sl, const FaceState& sr, d
     for (int v = 0; v < 5; ++v) F[v] = R.F[v];
     return;
   }
-  const double sluL = SL - sl.u, sruR = SR - sr.u;
-  const double mL = sluL * sl.rho, mR = sruR * sr.rho;  // mass fluxes through the outer waves
-  const double dinv = rcp(mR - mL);
-  const double SM = ((mR * sr.u - mL * sl.u) + (L.pt - R.pt)) * dinv;  // MK05 Eq. 38
-  const double ptS = (mR * L.pt - mL * R.pt + mL * mR * (sr.u - sl.u)) * dinv;  // MK05 Eq. 41
-  const double bn2 = bn * bn;
-  const double abn = vabs(bn);
+  const T sluL = SL - sl.u, sruR = SR - sr.u;
+  const T mL = sluL * sl.rho, mR = sruR * sr.rho;  // mass fluxes through the outer waves
+  const T dinv = rcp(mR - mL);
+  const T SM = ((mR * sr.u - mL * sl.u) + (L.pt - R.pt)) * dinv;  // MK05 Eq. 38
+  const T ptS = (mR * L.pt - mL * R.pt + mL * mR * (sr.u - sl.u)) * dinv;  // MK05 Eq. 41
+  const T bn2 = bn * bn;
+  const T abn = vabs(bn);
   const bool left = ge0(SM);
-  const FaceState q = pick(left, sl, sr);
-  PhysFlux P;
+  const FaceStateT<T> q = pick(left, sl, sr);
+  PhysFluxT<T> P;
   pick(left, L, R, P);
-  const double S = left ? SL : SR;
-  Star a;
+  const T S = left ? SL : SR;
+  StarT<T> a;
   star_state(q, P, S, SM, ptS, bn, bn2, a);
-  const double isqa = rsqrt_(a.rs);
-  const double Ss = left ? SM - abn * isqa : SM + abn * isqa;  // MK05 Eq. 51
-  const double Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
-  double Fs[5];
+  const T isqa = rsqrt_(a.rs);
+  const T Ss = left ? SM - abn * isqa : SM + abn * isqa;  // MK05 Eq. 51
+  const T Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
+  T Fs[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) Fs[v] = fma(S, Usa[v] - P.U[v], P.F[v]);
   const bool dstar = left ? !ge0(Ss) : ge0(Ss);
@@ -370,31 +459,31 @@ __device__ __forceinline__ void hlld(const FaceState& sl, const FaceState& sr, d
     return;
   }
   // inside the rotational wave of this side: the other side's star state and the double star
-  const FaceState qo = pick(!left, sl, sr);
-  PhysFlux Po;
+  const FaceStateT<T> qo = pick(!left, sl, sr);
+  PhysFluxT<T> Po;
   pick(!left, L, R, Po);
-  Star b;
+  StarT<T> b;
   star_state(qo, Po, left ? SR : SL, SM, ptS, bn, bn2, b);
-  const double isqb = rsqrt_(b.rs);
-  const double rsL = left ? a.rs : b.rs, rsR = left ? b.rs : a.rs;
-  const double vsL = left ? a.vs : b.vs, vsR = left ? b.vs : a.vs;
-  const double wsL = left ? a.ws : b.ws, wsR = left ? b.ws : a.ws;
-  const double bysL = left ? a.bys : b.bys, bysR = left ? b.bys : a.bys;
-  const double bzsL = left ? a.bzs : b.bzs, bzsR = left ? b.bzs : a.bzs;
-  const double iL = left ? isqa : isqb, iR = left ? isqb : isqa;
-  const double sqL = rsL * iL, sqR = rsR * iR;
+  const T isqb = rsqrt_(b.rs);
+  const T rsL = left ? a.rs : b.rs, rsR = left ? b.rs : a.rs;
+  const T vsL = left ? a.vs : b.vs, vsR = left ? b.vs : a.vs;
+  const T wsL = left ? a.ws : b.ws, wsR = left ? b.ws : a.ws;
+  const T bysL = left ? a.bys : b.bys, bysR = left ? b.bys : a.bys;
+  const T bzsL = left ? a.bzs : b.bzs, bzsR = left ? b.bzs : a.bzs;
+  const T iL = left ? isqa : isqb, iR = left ? isqb : isqa;
+  const T sqL = rsL * iL, sqR = rsR * iR;
   const double sb = sgnd(bn);
-  const double inv = rcp(sqL + sqR);
-  const double vss = fma(sqL, vsL, fma(sqR, vsR, (bysR - bysL) * sb)) * inv;
-  const double wss = fma(sqL, wsL, fma(sqR, wsR, (bzsR - bzsL) * sb)) * inv;
-  const double sLR = sqL * sqR;
-  const double byss = fma(sqL, bysR, fma(sqR, bysL, sLR * (vsR - vsL) * sb)) * inv;
-  const double bzss = fma(sqL, bzsR, fma(sqR, bzsL, sLR * (wsR - wsL) * sb)) * inv;
-  const double vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
-  const double sq = left ? sqL : sqR;
+  const T inv = rcp(sqL + sqR);
+  const T vss = fma(sqL, vsL, fma(sqR, vsR, (bysR - bysL) * sb)) * inv;
+  const T wss = fma(sqL, wsL, fma(sqR, wsR, (bzsR - bzsL) * sb)) * inv;
+  const T sLR = sqL * sqR;
+  const T byss = fma(sqL, bysR, fma(sqR, bysL, sLR * (vsR - vsL) * sb)) * inv;
+  const T bzss = fma(sqL, bzsR, fma(sqR, bzsL, sLR * (wsR - wsL) * sb)) * inv;
+  const T vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
+  const T sq = left ? sqL : sqR;
   const double sgn_side = left ? -1.0 : 1.0;
-  const double vbs = fma(SM, bn, fma(a.vs, a.bys, a.ws * a.bzs));
-  double Uss[5];
+  const T vbs = fma(SM, bn, fma(a.vs, a.bys, a.ws * a.bzs));
+  T Uss[5];
   Uss[0] = a.rs;
   Uss[1] = a.rs * SM;
   Uss[2] = a.rs * vss;
@@ -405,30 +494,30 @@ __device__ __forceinline__ void hlld(const FaceState& sl, const FaceState& sr, d
 }
 
 // Full face solve: flux of {rho, m_n, m_t1, m_t2, e}, alpha+/-, and the Q26 face velocity.
-template <int RS>
-__device__ __forceinline__ void riemann(const FaceState& sl, const FaceState& sr, double bn,
-                                        double gam, double gm1inv, double* F, double& ap,
-                                        double& am, double& ustar) {
-  PhysFlux L, R;
+template <int RS, class T>
+__device__ __forceinline__ void riemann(const FaceStateT<T>& sl, const FaceStateT<T>& sr, T bn,
+                                        double gam, double gm1inv, T* F, T& ap,
+                                        T& am, T& ustar) {
+  PhysFluxT<T> L, R;
   phys(sl, bn, gam, gm1inv, L);
   phys(sr, bn, gam, gm1inv, R);
-  double SL = 0.0, SR = 0.0;
+  T SL = 0.0, SR = 0.0;
   if (RS == RS_LLF) {
-    const double a = pmax(vabs(sl.u) + L.cf, vabs(sr.u) + R.cf);
+    const T a = pmax(vabs(sl.u) + L.cf, vabs(sr.u) + R.cf);
     ap = a;
     am = a;
   } else {
     // Eq. (alpha-pm) = MK05 Eq. 67 speeds
-    const double cmax = pmax(L.cf, R.cf);
-    const double umax = vmax(sl.u, sr.u), umin = vmin(sl.u, sr.u);
+    const T cmax = pmax(L.cf, R.cf);
+    const T umax = vmax(sl.u, sr.u), umin = vmin(sl.u, sr.u);
     SR = umax + cmax;
     SL = umin - cmax;
     ap = vmax(0.0, SR);
     am = vmax(0.0, cmax - umin);
   }
-  const double sum = ap + am;
+  const T sum = ap + am;
   const bool zero = is_zero(sum);
-  const double inv = zero ? 0.0 : rcp(sum);
+  const T inv = zero ? 0.0 : rcp(sum);
   if (RS == RS_HLLD)
     hlld(sl, sr, bn, L, R, SL, SR, F);
   else

@@ -109,13 +109,24 @@ __device__ __forceinline__ void b25_seg(const Dev& D, int e, int to_a, const Lin
 }
 
 // Eq. (ld04) with the edge speeds of Eq. (alpha-edge), plus eta j (Eq. emf-update).
-__device__ __forceinline__ double ld04(double apa, double ama, double apc, double amc, double eLB,
-                                       double eRB, double eLT, double eRT, double baB, double baT,
-                                       double bcL, double bcR) {
-  const double ia = rcp(apa + ama), ic = rcp(apc + amc);
-  const double w = ia * ic;
-  const double up = fma(apc, fma(apa, eLB, ama * eRB), amc * fma(apa, eLT, ama * eRT)) * w;
+template <class T>
+__device__ __forceinline__ T ld04(T apa, T ama, T apc, T amc, T eLB, T eRB, T eLT, T eRT, T baB, T baT, T bcL,
+                                  T bcR) {
+  const T ia = rcp(apa + ama), ic = rcp(apc + amc);
+  const T w = ia * ic;
+  const T up = fma(apc, fma(apa, eLB, ama * eRB), amc * fma(apa, eLT, ama * eRT)) * w;
   return fma(apa * ama * ia, bcR - bcL, fma(-apc * amc * ic, baT - baB, up));
+}
+
+// Q26 corner EMFs (Eq. q26) and their LD04 average, as a function of its 12 inputs.
+template <class T>
+__device__ __forceinline__ T q26_edge_emf(T baB, T baT, T uaB, T uaT, T bcL, T bcR, T ucL, T ucR, T apa, T ama,
+                                          T apc, T amc) {
+  const T eLB = fma(-uaB, bcL, ucL * baB);
+  const T eRB = fma(-uaB, bcR, ucR * baB);
+  const T eLT = fma(-uaT, bcL, ucL * baT);
+  const T eRT = fma(-uaT, bcR, ucR * baT);
+  return ld04(apa, ama, apc, amc, eLB, eRB, eLT, eRT, baB, baT, bcL, bcR);
 }
 
 // Sources reconstructed along a on the c-faces of e-edges (their left/right values), per scheme:

@@ -16,6 +16,16 @@ __device__ __forceinline__ long long shift(const Dev& D, long long X, int d, int
   return X + (long long)(cn - cd) * (long long)st;
 }
 
+// X shifted by any s along d (true modulo, for lines shorter than |s|)
+__device__ __forceinline__ long long shift2(const Dev& D, long long X, int d, int s) {
+  const unsigned st = (unsigned)D.stride[d];
+  const int nd = D.n[d];
+  const int cd = (int)(((unsigned long long)X / st) % (unsigned)nd);
+  int cn = (cd + s) % nd;
+  if (cn < 0) cn += nd;
+  return X + (long long)(cn - cd) * (long long)st;
+}
+
 // Sweeps along `dir`: lines are indexed by the two other axes, the faster one first so that
 // neighbouring threads touch neighbouring addresses when dir != 0; each line is cut into
 // segments of `seg` points, one per thread.

@@ -53,6 +53,27 @@ struct Dev {
   int stage;      // 0 or 1 (which counter the flux correction reads)
 };
 
+// Adjoint of the flux function at a stage input state (mhd_adjoint.cu).
+struct AdjDev {
+  Dev D;                // forward parameters at the state (P, Ap, Am, Us recomputed for it)
+  const double* lF;     // [3][5][N] adjoint of the face fluxes
+  const double* lE;     // [3][N] adjoint of the edge EMFs
+  double* lAp;          // [3][N] adjoint of alpha+ on faces
+  double* lAm;          // [3][N] adjoint of alpha-
+  double* lUs;          // [3][N] adjoint of the Q26 face velocity
+  double* lEdge;        // [3][8][N] adjoint of baB, baT, uaB, uaT, bcL, bcR, ucL, ucR per e-edge
+  double* lLR;          // [3][14][N] adjoint of the left (7) and right (7) face states
+  double* lP;           // [8][N] adjoint of the primitives
+  double* lU;           // [5][N] output: adjoint of the conserved variables (accumulated)
+  double* lB;           // [3][N] output: adjoint of the face field (accumulated, atomics)
+  double* lEta;         // [1] output: d/d(eta) (accumulated, atomics)
+};
+
+void launch_adj_flux(const AdjDev& A, int recon, int rs, cudaStream_t st);
+void launch_adj_update(const Dev& D, const double* lU, const double* lB, double* lF, double* lE, double scale,
+                       double s_old, cudaStream_t st);
+void launch_axpy3(long long n, double* y, const double* a, const double* b, cudaStream_t st);
+
 // message reported by mhd_create_error() for calls that have no context
 void set_call_error(const char* msg);
 

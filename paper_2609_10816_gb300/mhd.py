@@ -83,6 +83,8 @@ def lib():
     L.mhd_last_error.restype = ctypes.c_char_p
     L.mhd_create_error.argtypes = []
     L.mhd_create_error.restype = ctypes.c_char_p
+    L.mhd_step_adjoint.argtypes = [vp, P(_State), P(_State), d, ctypes.c_int, d, P(d)]
+    L.mhd_step_adjoint.restype = ctypes.c_int
     L.mhd_math_check.argtypes = [vp, ctypes.c_longlong, P(d)]
     L.mhd_math_check.restype = ctypes.c_int
     L.mhd_profile.argtypes = [vp, ctypes.c_int]
@@ -179,6 +181,15 @@ class Context:
         a, b = ctypes.c_longlong(), ctypes.c_longlong()
         self._err(lib().mhd_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def step_adjoint(self, st: State, lam: State, dt: float, scheme_bits: int, eta: float = 0.0) -> float:
+        """lam <- (dS^{n+1}/dS^n)^T lam for the step from st; returns the step's d/d(eta) term."""
+        s = self._state(st)
+        l = self._state(lam)
+        out = ctypes.c_double(0.0)
+        self._err(lib().mhd_step_adjoint(self._h, ctypes.byref(s), ctypes.byref(l), float(dt), int(scheme_bits),
+                                         float(eta), ctypes.byref(out)))
+        return out.value
 
     def math_check(self, n: int = 1 << 22):
         """Largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE."""

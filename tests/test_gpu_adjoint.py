@@ -1,0 +1,99 @@
+"""Hand-written adjoint of the step (mhd_step_adjoint, MHDEvolve) against the oracle (GPU).
+
+Reference: the oracle run on forward-mode dual numbers gives the exact directional derivative
+J v of the same steps (same frozen dts, same branches); the adjoint must satisfy
+<lam, J v> = <J^T lam, v> to ~1e-10 relative. Central finite differences (h = 1e-6) of the GPU
+forward run check the assembled torch gradient, including d/d(eta).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_10816_gb300 import adjoint, inputs, mhd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("recon,rs", [("ppm", "hlld"), ("plm_mc", "hll"), ("plm_minmod", "llf"), ("pc", "hlld")])
+@pytest.mark.parametrize("eta", [0.0, 3e-3])
+def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta):
+    shape = (10, 8, 6)
+    cons, b, info = inputs.random_smooth(shape, seed=21, rough=0.02)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf="q26", eta=eta)
+    dt = oracle.max_dt(cfg, cons, b, 0.3)
+    rng = np.random.default_rng(1)
+    lc, lb = rng.normal(size=cons.shape), rng.normal(size=b.shape)
+    vc, vb, veta = rng.normal(size=cons.shape) * 1e-2, rng.normal(size=b.shape) * 1e-3, 0.7
+    _, _, tc, tb = oracle.steps_jvp(cfg, cons, b, vc, vb, veta, [dt])
+    lhs = (lc * tc).sum() + (lb * tb).sum()
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    lam = mhd.to_device(lc, lb)
+    deta = ctx.step_adjoint(st, lam, dt, mhd.scheme(recon, rs, "q26"), eta)
+    torch.cuda.synchronize()
+    rc, rb = lam.cons.cpu().numpy(), lam.b.cpu().numpy()
+    rhs = (rc * vc).sum() + (rb * vb).sum() + deta * veta
+    print(f"ADJ {recon} {rs} eta={eta}: lhs {lhs:.15e} rhs {rhs:.15e} rel {abs(lhs - rhs) / abs(lhs):.2e}")
+    assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs((rc * vc).sum()) + abs((rb * vb).sum()) + 1e-300), (lhs, rhs)
+    # the state is not modified by the adjoint
+    assert np.array_equal(st.cons.cpu().numpy(), cons) and np.array_equal(st.b.cpu().numpy(), b)
+
+
+def _initial(shape, u, rho, p, b):
+    """Conserved state from an initial velocity (torch, differentiable), density, pressure, field."""
+    bc = 0.5 * (b + torch.stack([torch.roll(b[d], -1, dims=2 - d) for d in range(3)]))
+    m = rho * u
+    e = p / (5.0 / 3.0 - 1.0) + 0.5 * rho * (u * u).sum(0) + 0.5 * (bc * bc).sum(0)
+    return torch.cat([rho[None], m, e[None]], 0)
+
+
+def test_multistep_gradient_wrt_velocity_and_eta(gpu_lib):
+    """L = sum of b^2 after 6 steps (checkpoints every 2): torch gradient vs the oracle's exact
+    directional derivative and vs central differences of the GPU forward run."""
+    shape = (12, 10, 8)
+    cons, b, info = inputs.turbulence(shape, seed=2, v_rms=2.0)
+    eta0 = 1e-3
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    cfg = oracle.Config(shape=shape, h=info["h"], recon="ppm", riemann="hlld", eta=eta0)
+    dts, c, bb = [], cons, b
+    for _ in range(6):
+        dts.append(oracle.max_dt(cfg, c, bb, 0.3))
+        c, bb, _ = oracle.step(cfg, c, bb, dts[-1])
+    dev = "cuda"
+    rho = torch.tensor(cons[0], device=dev)
+    u0 = torch.tensor(cons[1:4] / cons[0], device=dev, requires_grad=True)
+    p = torch.tensor(np.full(cons[0].shape, 1.0 / (5.0 / 3.0)), device=dev)
+    bt = torch.tensor(b, device=dev)
+    eta = torch.tensor(eta0, dtype=torch.float64, requires_grad=True)
+    ctx = mhd.Context(shape, info["h"])
+
+    def loss(u, e):
+        c0 = _initial(shape, u, rho, p, bt).contiguous()
+        cf, bf = adjoint.evolve(c0, bt, e, ctx, dts, sch, every=2)
+        return (bf * bf).sum()
+
+    L = loss(u0, eta)
+    L.backward()
+    gu, geta = u0.grad.cpu().numpy(), float(eta.grad)
+    rng = np.random.default_rng(5)
+    for trial in range(2):
+        vu = rng.normal(size=u0.shape)
+        veta = rng.normal()
+        # exact directional derivative from the oracle on dual numbers
+        u_np = cons[1:4] / cons[0]
+        dm = cons[0] * vu
+        de = cons[0] * (u_np * vu).sum(0)
+        dc = np.concatenate([np.zeros_like(cons[:1]), dm, de[None]], 0)
+        _, bfin, _, tbf = oracle.steps_jvp(cfg, cons, b, dc, np.zeros_like(b), veta, dts)
+        exact = 2.0 * (bfin * tbf).sum()
+        got = (gu * vu).sum() + geta * veta
+        assert abs(got - exact) <= 1e-9 * abs(exact), (got, exact)
+        # central differences of the GPU forward run
+        h = 1e-6
+        with torch.no_grad():
+            vt = torch.tensor(vu, device=dev)
+            lp = float(loss(u0 + h * vt, eta + h * veta))
+            lm = float(loss(u0 - h * vt, eta - h * veta))
+        fd = (lp - lm) / (2 * h)
+        assert abs(got - fd) <= 1e-5 * abs(fd), (got, fd)
