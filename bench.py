@@ -210,6 +210,78 @@ def run_batched(args, dev, stream, barrier, dist, world):
     return out
 
 
+def run_fwd_adjoint(args, dev, stream, barrier, dist, world):
+    """64^3 turbulence at Mach 2 (rho = 1, B0 = (0,0,0.5), p = rho/gamma), eta = 1e-3, PPM + HLLD
+    + Q26 + LD04, 20 steps with the dt sequence frozen from a first forward pass, checkpoints
+    every 5 steps; loss = sum of b^2 at the final time; gradients in the initial velocity field
+    (rho and p held) and eta. Throughput counts cell-updates of the forward pass per second of
+    forward + backward time. Central differences (h = 1e-6) on 16 random directions check it."""
+    import numpy as np
+    import torch
+
+    from paper_2609_10816_gb300 import adjoint, inputs, mhd
+
+    n, nsteps, eta0 = args.adj_n, 20, 1e-3
+    cons, b, info = inputs.turbulence((n, n, n), seed=2, v_rms=2.0)
+    ctx = mhd.Context((n, n, n), info["h"], stream=stream)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    st = mhd.to_device(cons, b, dev)
+    dts = []
+    for _ in range(nsteps):  # freeze the dt sequence
+        dts.append(ctx.max_dt(st, 0.3, eta0))
+        ctx.step(st, dts[-1], sch, eta0)
+    rho = torch.tensor(cons[0], device=dev)
+    p = rho / (5.0 / 3.0)
+    bt = torch.tensor(b, device=dev)
+    u_init = torch.tensor(cons[1:4] / cons[0], device=dev)
+
+    def init(u):
+        bc = 0.5 * (bt + torch.stack([torch.roll(bt[d], -1, dims=2 - d) for d in range(3)]))
+        e = p / (5.0 / 3.0 - 1.0) + 0.5 * rho * (u * u).sum(0) + 0.5 * (bc * bc).sum(0)
+        return torch.cat([rho[None], rho * u, e[None]], 0).contiguous()
+
+    def loss(u, e):
+        cf, bf = adjoint.evolve(init(u), bt, e, ctx, dts, sch, every=5)
+        return (bf * bf).sum()
+
+    def one():
+        u = u_init.clone().requires_grad_(True)
+        e = torch.tensor(eta0, dtype=torch.float64, requires_grad=True)
+        L = loss(u, e)
+        L.backward()
+        return u.grad, e.grad
+
+    one()  # warm-up (allocates the adjoint scratch)
+    barrier()
+    t0 = time.perf_counter()
+    reps = 2
+    for _ in range(reps):
+        gu, ge = one()
+    torch.cuda.synchronize(dev)
+    el = (time.perf_counter() - t0) / reps
+    if dist is not None:
+        t = torch.tensor([el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    # central differences on 16 random directions
+    rng = np.random.default_rng(16)
+    worst = 0.0
+    with torch.no_grad():
+        for _ in range(16):
+            vu = torch.tensor(rng.normal(size=u_init.shape), device=dev)
+            ve = float(rng.normal())
+            h = 1e-6
+            fd = (float(loss(u_init + h * vu, torch.tensor(eta0 + h * ve, dtype=torch.float64)))
+                  - float(loss(u_init - h * vu, torch.tensor(eta0 - h * ve, dtype=torch.float64)))) / (2 * h)
+            got = float((gu * vu).sum()) + float(ge) * ve
+            worst = max(worst, abs(got - fd) / max(abs(fd), 1e-300))
+    ctx.close()
+    return {"fwd_adjoint": world * n**3 * nsteps / el,
+            "fwd_adjoint_config": {"cells": n**3, "steps": nsteps, "checkpoint_every": 5, "eta": eta0,
+                                   "seconds_fwd_plus_bwd": el, "dL_deta": float(ge),
+                                   "fd_16_directions_max_rel_err": worst}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,6 +294,8 @@ def main():
     ap.add_argument("--q26-only", action="store_true", help="skip the FS18 / B25a comparison runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-patches form")
     ap.add_argument("--npatch", type=int, default=1024)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint form")
+    ap.add_argument("--adj-n", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -327,6 +401,9 @@ def main():
     # ---- batched form: 1024 uneven periodic patches, one persistent launch per stage ---------
     if not args.no_batch:
         forms.update(run_batched(args, dev, stream, barrier, dist, world))
+
+    if not args.no_adjoint:
+        forms.update(run_fwd_adjoint(args, dev, stream, barrier, dist, world))
 
     # ---- end to end through the C ABI with host buffers --------------------------------------
     cons_h = torch.from_numpy(cons).pin_memory()
