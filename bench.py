@@ -39,7 +39,7 @@ HBM_PEAK_GBS = 6759.6  # MEASURED_PEAKS.json copy bandwidth
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 686.3e6, "cells": 160**3, "src": "40dd8ea10159d6da"}}
+TRAFFIC = {"face": {"bytes_per_launch": 676.0e6, "cells": 160**3, "src": "6c321db76d18bb2f"}}
 
 
 def kernel_src_hash():
