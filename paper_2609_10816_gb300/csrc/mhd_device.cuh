@@ -33,8 +33,8 @@ __device__ __forceinline__ double vmin(double a, double b) { return okey(a) <= o
 __device__ __forceinline__ double pmax(double a, double b) { return dbits(a) >= dbits(b) ? a : b; }
 __device__ __forceinline__ double pmin(double a, double b) { return dbits(a) <= dbits(b) ? a : b; }
 __device__ __forceinline__ double vabs(double x) { return dfrom(dbits(x) & 0x7fffffffffffffffLL); }
-__device__ __forceinline__ bool gt0(double x) { return okey(x) > 0; }    // x > 0
-__device__ __forceinline__ bool lt0(double x) { return okey(x) < -1; }   // x < 0 (not -0)
+__device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }   // x > 0
+__device__ __forceinline__ bool lt0(double x) { return dbits(-x) > 0; }  // x < 0 (not -0)
 __device__ __forceinline__ bool ge0(double x) { return okey(x) >= -1; }  // x >= 0 (either zero)
 __device__ __forceinline__ bool le0(double x) { return !gt0(x); }
 __device__ __forceinline__ bool vgt(double a, double b) { return okey(a) > okey(b); }
@@ -209,13 +209,24 @@ template <> struct Rec<REC_PLM_MINMOD> : RecPLM<REC_PLM_MINMOD> {};
 // (Eq. 1.6) and monotonicity constraints (Eq. 1.10), arranged to reuse the one-sided
 // differences: the slope is carried doubled, dq2 = 2 dq = sgn min(|dl + dr|, 4|dl|, 4|dr|), the
 // interface value between points 0 and 1 is q0 + (q1 - q0)/2 - (dq2_1 - dq2_0)/12, and with
-// s1 = aR - a, s2 = a - aL the constraint quantities are aR - aL = s1 + s2 and
-// 6 (a - (aL + aR)/2) = 3 (s2 - s1), the corrections 3a - 2aR = a - 2 s1, 3a - 2aL = a + 2 s2.
+// s1 = aR - a, s2 = a - aL (same sign unless a is an extremum) the tests of Eq. 1.10 become sign
+// tests: with da = aR - aL = s1 + s2 (sign of s1) and a6 = 6 (a - (aL + aR)/2) = 3 (s2 - s1),
+// da a6 > da^2 <=> da (a6 - da) > 0 <=> s2 - 2 s1 has the sign of s1, and
+// -da^2 > da a6 <=> da (a6 + da) < 0 <=> 2 s2 - s1 has the opposite sign; the corrections are
+// 3a - 2aR = a - 2 s1 and 3a - 2aL = a + 2 s2.
+
+// 4 m for m >= 0 by adding 2 to the binary exponent (exact for normal m; zero stays zero)
+__device__ __forceinline__ double times4(double m) {
+  const long long b = dbits(m);
+  return b == 0 ? 0.0 : dfrom(b + (2LL << 52));
+}
+__device__ __forceinline__ Dual times4(Dual m) { return Dual(times4(m.v), 4.0 * m.t); }
+
 template <class T>
 __device__ __forceinline__ T vl_slope2(T dl, T dr) {
   if (!same_sign(dl, dr)) return T(0.0);
   const T s = dl + dr;
-  const T m = pmin(vabs(s), 4.0 * pmin(vabs(dl), vabs(dr)));
+  const T m = pmin(vabs(s), times4(pmin(vabs(dl), vabs(dr))));
   return with_sign(m, s);
 }
 template <class T>
@@ -230,12 +241,11 @@ __device__ __forceinline__ void ppm_mono(T a, T& aL, T& aR) {
     aR = a;
     return;
   }
-  const T da = s1 + s2;
-  const T a6 = 3.0 * (s2 - s1);
-  const T p1 = da * a6, p2 = da * da;
-  if (vgt(p1, p2)) {
+  const T u = fma(T(-2.0), s1, s2);  // (a6 - da) / 2
+  const T v = fma(T(2.0), s2, -s1);  // (a6 + da) / 2
+  if (same_sign(u, s1)) {
     aL = fma(T(-2.0), s1, a);
-  } else if (vgt(-p2, p1)) {
+  } else if (same_sign(v, -s1)) {
     aR = fma(T(2.0), s2, a);
   }
 }
@@ -313,20 +323,33 @@ using FaceState = FaceStateT<double>;
 
 template <class T> struct PhysFluxT {
   T U[5], F[5];
-  T pt, e, cf;
+  T pt, e, cf, b2;
 };
 using PhysFlux = PhysFluxT<double>;
 
-// Ideal-MHD flux of Eq. (mhd:conservation-laws) in the face frame, energy flux with e_tot,
-// and the fast magnetosonic speed of Eq. (waves:fast-speed) along the normal.
+// Total pressure and the fast magnetosonic speed of Eq. (waves:fast-speed) along the normal:
+// all the wave-speed estimates need from a state.
 template <class T>
-__device__ __forceinline__ void phys(const FaceStateT<T>& s, T bn, double gam, double gm1inv,
-                                     PhysFluxT<T>& o) {
+__device__ __forceinline__ void phys_speed(const FaceStateT<T>& s, T bn, double gam, PhysFluxT<T>& o) {
   const T bn2 = bn * bn;
   const T b2 = fma(s.by, s.by, fma(s.bz, s.bz, bn2));
+  o.b2 = b2;
+  o.pt = fma(0.5, b2, s.p);
+  const T rinv = rcp(s.rho);
+  const T a2 = gam * s.p * rinv;
+  const T sum = fma(b2, rinv, a2);
+  T disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
+  disc = pmax(disc, T(0.0));
+  o.cf = sqrt_(0.5 * (sum + sqrt_(disc)));
+}
+
+// Conserved vector and ideal-MHD flux of Eq. (mhd:conservation-laws) in the face frame, with e_tot
+// in the energy flux (needs b2 and pt from phys_speed).
+template <class T>
+__device__ __forceinline__ void phys_flux(const FaceStateT<T>& s, T bn, double gm1inv, PhysFluxT<T>& o) {
+  const T bn2 = bn * bn;
   const T u2 = fma(s.u, s.u, fma(s.v, s.v, s.w * s.w));
-  const T e = fma(s.p, gm1inv, 0.5 * fma(s.rho, u2, b2));
-  const T pt = fma(0.5, b2, s.p);
+  const T e = fma(s.p, gm1inv, 0.5 * fma(s.rho, u2, o.b2));
   const T ub = fma(s.u, bn, fma(s.v, s.by, s.w * s.bz));
   const T mu = s.rho * s.u;
   o.U[0] = s.rho;
@@ -335,18 +358,11 @@ __device__ __forceinline__ void phys(const FaceStateT<T>& s, T bn, double gam, d
   o.U[3] = s.rho * s.w;
   o.U[4] = e;
   o.F[0] = mu;
-  o.F[1] = fma(mu, s.u, pt - bn2);
+  o.F[1] = fma(mu, s.u, o.pt - bn2);
   o.F[2] = fma(mu, s.v, -bn * s.by);
   o.F[3] = fma(mu, s.w, -bn * s.bz);
-  o.F[4] = fma(e + pt, s.u, -ub * bn);
-  o.pt = pt;
+  o.F[4] = fma(e + o.pt, s.u, -ub * bn);
   o.e = e;
-  const T rinv = rcp(s.rho);
-  const T a2 = gam * s.p * rinv;
-  const T sum = fma(b2, rinv, a2);
-  T disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
-  disc = pmax(disc, 0.0);
-  o.cf = sqrt_(0.5 * (sum + sqrt_(disc)));
 }
 
 // HLL-type two-state flux; inv = 1 / (ap + am), or 0 when ap + am = 0 (then the left flux).
@@ -406,30 +422,22 @@ __device__ __forceinline__ FaceStateT<T> pick(bool left, const FaceStateT<T>& a,
   r.bz = left ? a.bz : b.bz;
   return r;
 }
-template <class T>
-__device__ __forceinline__ void pick(bool left, const PhysFluxT<T>& a, const PhysFluxT<T>& b, PhysFluxT<T>& r) {
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    r.U[v] = left ? a.U[v] : b.U[v];
-    r.F[v] = left ? a.F[v] : b.F[v];
-  }
-  r.pt = left ? a.pt : b.pt;
-  r.e = left ? a.e : b.e;
-}
 
 // Miyoshi & Kusano (2005) HLLD without the Minoshima fixes. The face x/t = 0 lies on the side of
 // the contact given by sgn(S_M); only that side's star state is formed, and the other side's star
 // state and the double-star state (MK05 Eqs. 49-63) only when the face lies inside that side's
 // rotational wave. Same values as forming all four states and selecting.
 template <class T>
-__device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T>& sr, T bn,
-                                     const PhysFluxT<T>& L, const PhysFluxT<T>& R, T SL, T SR,
-                                     T* F) {
+__device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T>& sr, T bn, double gm1inv,
+                                     PhysFluxT<T>& L, PhysFluxT<T>& R, T SL, T SR, T* F) {
+  // the flux vectors are formed only for the side(s) the face needs
   if (gt0(SL)) {
+    phys_flux(sl, bn, gm1inv, L);
     for (int v = 0; v < 5; ++v) F[v] = L.F[v];
     return;
   }
   if (lt0(SR)) {
+    phys_flux(sr, bn, gm1inv, R);
     for (int v = 0; v < 5; ++v) F[v] = R.F[v];
     return;
   }
@@ -443,7 +451,9 @@ __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T
   const bool left = ge0(SM);
   const FaceStateT<T> q = pick(left, sl, sr);
   PhysFluxT<T> P;
-  pick(left, L, R, P);
+  P.b2 = left ? L.b2 : R.b2;
+  P.pt = left ? L.pt : R.pt;
+  phys_flux(q, bn, gm1inv, P);
   const T S = left ? SL : SR;
   StarT<T> a;
   star_state(q, P, S, SM, ptS, bn, bn2, a);
@@ -461,7 +471,9 @@ __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T
   // inside the rotational wave of this side: the other side's star state and the double star
   const FaceStateT<T> qo = pick(!left, sl, sr);
   PhysFluxT<T> Po;
-  pick(!left, L, R, Po);
+  Po.b2 = left ? R.b2 : L.b2;
+  Po.pt = left ? R.pt : L.pt;
+  phys_flux(qo, bn, gm1inv, Po);
   StarT<T> b;
   star_state(qo, Po, left ? SR : SL, SM, ptS, bn, bn2, b);
   const T isqb = rsqrt_(b.rs);
@@ -499,8 +511,8 @@ __device__ __forceinline__ void riemann(const FaceStateT<T>& sl, const FaceState
                                         double gam, double gm1inv, T* F, T& ap,
                                         T& am, T& ustar) {
   PhysFluxT<T> L, R;
-  phys(sl, bn, gam, gm1inv, L);
-  phys(sr, bn, gam, gm1inv, R);
+  phys_speed(sl, bn, gam, L);
+  phys_speed(sr, bn, gam, R);
   T SL = 0.0, SR = 0.0;
   if (RS == RS_LLF) {
     const T a = pmax(vabs(sl.u) + L.cf, vabs(sr.u) + R.cf);
@@ -518,10 +530,13 @@ __device__ __forceinline__ void riemann(const FaceStateT<T>& sl, const FaceState
   const T sum = ap + am;
   const bool zero = is_zero(sum);
   const T inv = zero ? 0.0 : rcp(sum);
-  if (RS == RS_HLLD)
-    hlld(sl, sr, bn, L, R, SL, SR, F);
-  else
+  if (RS == RS_HLLD) {
+    hlld(sl, sr, bn, gm1inv, L, R, SL, SR, F);
+  } else {
+    phys_flux(sl, bn, gm1inv, L);
+    phys_flux(sr, bn, gm1inv, R);
     two_state(L, R, ap, am, inv, zero, F);
+  }
   // Eq. (q26-facevel)
   ustar = zero ? sl.u : fma(ap, sl.u, am * sr.u) * inv;
 }

@@ -3,8 +3,13 @@
 
 namespace mhd {
 
+// blocks of 128 threads the compiler must fit per SM (register budget of the face sweep)
+#ifndef MHD_FACE_MINB
+#define MHD_FACE_MINB 1
+#endif
+
 template <int RC, int RS>
-__global__ void __launch_bounds__(128) k_face(Dev D, int dir, int seg) {
+__global__ void __launch_bounds__(128, MHD_FACE_MINB) k_face(Dev D, int dir, int seg) {
   Line ln;
   int m0, m1;
   if (!sweep_line(D, dir, seg, ln, m0, m1)) return;
