@@ -42,13 +42,34 @@ ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B i
 TRAFFIC = {"face": {"bytes_per_launch": 676.0e6, "cells": 160**3, "src": "6c321db76d18bb2f"}}
 
 
-def kernel_src_hash():
+# sources the face sweep is compiled from (its kernel, the numerics, indexing and parameters)
+FACE_SOURCES = ("mhd_face.cu", "mhd_face.cuh", "mhd_device.cuh", "mhd_index.cuh", "mhd_internal.cuh")
+
+
+def kernel_src_hash(files=FACE_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2609_10816_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(files):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "mhd.h"), "rb").read())
     return h.hexdigest()[:16]
+
+
+def max_over_ranks(x, dist, dev):
+    """The largest of the ranks' values of x (the slowest rank's time); x itself at N = 1."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, timed by the slowest rank (replicas: every rank
+    advances its own box of the same size)."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 class ClockSampler:
@@ -198,15 +219,49 @@ def run_batched(args, dev, stream, barrier, dist, world):
     barrier()
     ms = e0.elapsed_time(e1)
     dt = bt.last_dt()  # also raises on a barrier timeout
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    out = {"batched": world * bt.ncell * args.steps / (ms / 1e3),
+    phases = {f"stage{st + 1}": {k: round(v, 3) for k, v in ph.items()} for st, ph in bt.phase_ms().items()}
+    ms = max_over_ranks(ms, dist, dev)
+    out = {"batched": whole_job_rate(bt.ncell * args.steps, world, ms),
            "batched_config": {"patches": len(dims), "cells_per_gpu": bt.ncell, "schedule": sched,
                               "ms_per_step": ms / args.steps, "last_dt": dt,
+                              "phase_ms_last_step": phases,
                               "launches_per_step": "1 graph: maxspeed, set_dt, 2 persistent stage kernels"}}
     bt.close()
+    return out
+
+
+def run_alfven(args, dev, stream, barrier, dist, world):
+    """The paper's throughput problem (Sec. 5.2): linearly polarised Alfven wave, k L / 2 pi =
+    (1, 2, 3), theta = pi/4, rho = b_bg = 1, p = 1/gamma, at its per-GPU size (128^3 by default)
+    for 100 CFL steps, PPM + HLLD with each EMF compute scheme and LD04 averaging. The paper uses
+    PPM-EP, which it does not define; plain PPM stands in."""
+    import torch
+
+    from paper_2609_10816_gb300 import inputs, mhd
+
+    n, steps = args.alfven_n, args.alfven_steps
+    cons, b, info = inputs.alfven_oblique((n, n, n))
+    ctx = mhd.Context((n, n, n), info["h"], stream=stream)
+    out = {}
+    for emf in ("q26", "fs18", "b25a"):
+        sch = mhd.scheme("ppm", "hlld", emf)
+        st = mhd.to_device(cons, b, dev)
+        for _ in range(3):
+            ctx.step(st, ctx.max_dt(st, 0.3), sch)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step(st, ctx.max_dt(st, 0.3), sch)
+        e1.record(stream)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        out[f"alfven{n}_{emf}"] = whole_job_rate(n**3 * steps, world, ms)
+        del st
+    ctx.close()
+    out[f"alfven{n}_config"] = {"cells": n**3, "steps": steps, "scheme": "PPM + HLLD + {Q26, FS18, B25a} + LD04",
+                                "q26_speedup_vs_fs18": out[f"alfven{n}_q26"] / out[f"alfven{n}_fs18"] - 1,
+                                "q26_speedup_vs_b25a": out[f"alfven{n}_q26"] / out[f"alfven{n}_b25a"] - 1}
     return out
 
 
@@ -259,10 +314,7 @@ def run_fwd_adjoint(args, dev, stream, barrier, dist, world):
         gu, ge = one()
     torch.cuda.synchronize(dev)
     el = (time.perf_counter() - t0) / reps
-    if dist is not None:
-        t = torch.tensor([el], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(el, dist, dev)
     # central differences on 16 random directions
     rng = np.random.default_rng(16)
     worst = 0.0
@@ -276,7 +328,7 @@ def run_fwd_adjoint(args, dev, stream, barrier, dist, world):
             got = float((gu * vu).sum()) + float(ge) * ve
             worst = max(worst, abs(got - fd) / max(abs(fd), 1e-300))
     ctx.close()
-    return {"fwd_adjoint": world * n**3 * nsteps / el,
+    return {"fwd_adjoint": whole_job_rate(n**3 * nsteps, world, 1e3 * el),
             "fwd_adjoint_config": {"cells": n**3, "steps": nsteps, "checkpoint_every": 5, "eta": eta0,
                                    "seconds_fwd_plus_bwd": el, "dL_deta": float(ge),
                                    "fd_16_directions_max_rel_err": worst}}
@@ -296,6 +348,9 @@ def main():
     ap.add_argument("--npatch", type=int, default=1024)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint form")
     ap.add_argument("--adj-n", type=int, default=64)
+    ap.add_argument("--no-alfven", action="store_true", help="skip the oblique Alfven-wave throughput runs")
+    ap.add_argument("--alfven-n", type=int, default=128)
+    ap.add_argument("--alfven-steps", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -354,12 +409,8 @@ def main():
     ctx.profile(False)
     s1, s2 = ctx.stats()
     md, mb = ctx.divb(st)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * N * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(N * args.steps, world, t_max)
 
     # dominant kernel and its live roofline
     dom = max(prof, key=lambda k: prof[k][0])
@@ -390,17 +441,16 @@ def main():
                 ctx.step(st_e, ctx.max_dt(st_e, 0.3), sch_e)
             g1.record(stream)
             barrier()
-            ms_e = g0.elapsed_time(g1)
-            if dist is not None:
-                t = torch.tensor([ms_e], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms_e = float(t.item())
-            forms[f"plain_{emf}"] = world * N * args.steps / (ms_e / 1e3)
+            ms_e = max_over_ranks(g0.elapsed_time(g1), dist, dev)
+            forms[f"plain_{emf}"] = whole_job_rate(N * args.steps, world, ms_e)
             del st_e
 
     # ---- batched form: 1024 uneven periodic patches, one persistent launch per stage ---------
     if not args.no_batch:
         forms.update(run_batched(args, dev, stream, barrier, dist, world))
+
+    if not args.no_alfven:
+        forms.update(run_alfven(args, dev, stream, barrier, dist, world))
 
     if not args.no_adjoint:
         forms.update(run_fwd_adjoint(args, dev, stream, barrier, dist, world))
@@ -421,12 +471,8 @@ def main():
         out_b.copy_(st.b, non_blocking=True)
     f1.record(stream)
     barrier()
-    e2e_ms = f0.elapsed_time(f1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * N * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+    e2e_value = whole_job_rate(N * args.e2e_steps, world, e2e_ms)
 
     if rank != 0:
         if dist is not None:

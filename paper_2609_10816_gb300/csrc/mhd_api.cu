@@ -2,7 +2,10 @@
 // management, argument checks, and the launch sequence of one RK2 + FOFC step (Sec. 2.5).
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mhd.h"
@@ -110,6 +113,23 @@ void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc) {
 
 void mhd::set_call_error(const char* msg) { g_create_err = msg; }
 
+int mhd::resident_blocks(const void* fn, int threads) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(fn, threads, dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+  cache[key] = per_sm * nsm;
+  return per_sm * nsm;
+}
+
 extern "C" {
 
 const char* mhd_create_error(void) { return g_create_err.c_str(); }
@@ -151,7 +171,7 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   // scratch, in doubles per cell: U1 5, B1 3, P 8, F 15, Ap/Am/Us 9, Epart 12, E 3,
   // VL/VR 18, Xpart 24, Ec 3, EfL 6, EfB 6  -> 112; + flags (1 byte) + counters
   const size_t nd = 112;
-  const size_t bytes = nd * sizeof(double) * (size_t)N + (size_t)N + 256 + 64;
+  const size_t bytes = nd * sizeof(double) * (size_t)N + (size_t)N + 256 + 64 + 128;
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
@@ -178,8 +198,9 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   D.Ec = take(3);
   D.EfL = take(6);
   D.EfB = take(6);
-  D.counters = (unsigned long long*)q;  // 8 counters, 64 bytes
-  D.flag = (unsigned char*)(q + 8);
+  D.counters = (unsigned long long*)q;  // 8 counters, then the sweeps' work cursors
+  D.work = D.counters + 8;
+  D.flag = (unsigned char*)(q + 8 + 16);
   e = cudaMemsetAsync(p, 0, bytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {

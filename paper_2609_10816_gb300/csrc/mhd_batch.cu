@@ -33,6 +33,8 @@ struct BatchDev {
   unsigned long long* counters;   // [0] stage-1 flags, [1] stage-2 flags, [2] max speed, [7] error
   long long spin_limit;           // bounded wait per barrier (iterations of ~100 ns)
   int barrier_extra;              // test hook: wait for this many blocks more than launched
+  unsigned long long* ptime;      // [2][8] global-timer stamps at the phase boundaries of each stage
+  unsigned long long* cursor;     // [3] work-list cursors of the face, edge_bt and edge_lr phases
 };
 
 // position k with pref[k] <= i < pref[k + 1]
@@ -43,6 +45,21 @@ __device__ __forceinline__ int find_pos(const long long* pref, int n, long long 
     if (pref[mid] <= i) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// schedule position of item i at or after k (a thread's items only grow, by less than a patch)
+__device__ __forceinline__ int advance_pos(const long long* pref, int k, long long i) {
+  while (pref[k + 1] <= i) ++k;
+  return k;
+}
+
+// block 0 stamps the global timer (ns) when it passes phase boundary j of this stage
+__device__ __forceinline__ void stamp(const BatchDev& B, int j) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    B.ptime[8 * B.stage + j] = t;
+  }
 }
 
 // Grid-wide barrier with a bounded wait: false (and the error flag set) if the other blocks did
@@ -79,113 +96,140 @@ __device__ bool grid_sync(const BatchDev& B) {
   return s_ok != 0;
 }
 
+// One sweep phase: the sweeps along dirs[0..2] of every patch form one work list (sweep j's
+// segments after those of sweeps 0 .. j-1, patches in schedule order), taken 32 segments at a
+// time per warp from `cursor`; fn(D, j, line, m0, m1) runs each segment.
+template <class Fn>
+__device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long long* cursor, const int* dirs, Fn fn) {
+  const long long* pref[3];
+  long long tot[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    pref[j] = B.sweep_pref + dirs[j] * (B.npatch + 1);
+    tot[j] = pref[j][B.npatch];
+  }
+  for_each_segment(cursor, tot[0] + tot[1] + tot[2], [&](long long t) {
+    int j = 0;
+    if (t >= tot[0]) {
+      t -= tot[0];
+      j = 1;
+      if (t >= tot[1]) {
+        t -= tot[1];
+        j = 2;
+      }
+    }
+    const int k = find_pos(pref[j], B.npatch, t);
+    const Dev& D = B.patches[B.order[k]];
+    Line ln;
+    int m0, m1;
+    if (sweep_line_at(D, dirs[j], B.seg, t - pref[j][k], ln, m0, m1)) fn(D, j, ln, m0, m1);
+  });
+}
+
 template <int RC, int RS>
 __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long ncell = B.cell_pref[B.npatch];
+  const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
+  stamp(B, 0);
+  // the sweep phases' cursors start at zero; no block takes work from them before the first
+  // grid barrier, which block 0 passes only after this
+  if (blockIdx.x == 0 && threadIdx.x < 3) atomicExch(B.cursor + threadIdx.x, 0ull);
   // cons -> prim
-  for (long long i = t0; i < ncell; i += nth) {
-    const int k = find_pos(B.cell_pref, B.npatch, i);
+  for (long long i = t0, k = k0; i < ncell; i += nth) {
+    k = advance_pos(B.cell_pref, (int)k, i);
     const Dev& D = B.patches[B.order[k]];
     prim_cell(D, i - B.cell_pref[k]);
   }
   if (!grid_sync(B)) return;
+  stamp(B, 1);
   // face sweeps along each direction
-  for (int dir = 0; dir < 3; ++dir) {
-    const long long* pref = B.sweep_pref + dir * (B.npatch + 1);
-    for (long long i = t0; i < pref[B.npatch]; i += nth) {
-      const int k = find_pos(pref, B.npatch, i);
-      const Dev& D = B.patches[B.order[k]];
-      Line ln;
-      int m0, m1;
-      if (sweep_line_at(D, dir, B.seg, i - pref[k], ln, m0, m1)) face_seg<RC, RS>(D, dir, ln, m0, m1);
-    }
+  {
+    const int dirs[3] = {0, 1, 2};
+    sweep_phase(B, B.cursor + 0, dirs, [&](const Dev& D, int j, const Line& ln, int m0, int m1) {
+      face_seg<RC, RS>(D, j, ln, m0, m1);
+    });
   }
   if (!grid_sync(B)) return;
+  stamp(B, 2);
   // a-face quantities to e-edges (lines along c = e + 2)
-  for (int e = 0; e < 3; ++e) {
-    const int dir = (e + 2) % 3;
-    const long long* pref = B.sweep_pref + dir * (B.npatch + 1);
-    for (long long i = t0; i < pref[B.npatch]; i += nth) {
-      const int k = find_pos(pref, B.npatch, i);
-      const Dev& D = B.patches[B.order[k]];
-      Line ln;
-      int m0, m1;
-      if (sweep_line_at(D, dir, B.seg, i - pref[k], ln, m0, m1)) edge_bt_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
-    }
+  {
+    const int dirs[3] = {2, 0, 1};
+    sweep_phase(B, B.cursor + 1, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
+      edge_bt_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
+    });
   }
   if (!grid_sync(B)) return;
+  stamp(B, 3);
   // c-face quantities to e-edges (lines along a = e + 1) and the edge EMFs
-  for (int e = 0; e < 3; ++e) {
-    const int dir = (e + 1) % 3;
-    const long long* pref = B.sweep_pref + dir * (B.npatch + 1);
-    for (long long i = t0; i < pref[B.npatch]; i += nth) {
-      const int k = find_pos(pref, B.npatch, i);
-      const Dev& D = B.patches[B.order[k]];
-      Line ln;
-      int m0, m1;
-      if (sweep_line_at(D, dir, B.seg, i - pref[k], ln, m0, m1)) edge_lr_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
-    }
+  {
+    const int dirs[3] = {1, 2, 0};
+    sweep_phase(B, B.cursor + 2, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
+      edge_lr_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
+    });
   }
   if (!grid_sync(B)) return;
+  stamp(B, 4);
   // update
-  for (long long i = t0; i < ncell; i += nth) {
-    const int k = find_pos(B.cell_pref, B.npatch, i);
+  for (long long i = t0, k = k0; i < ncell; i += nth) {
+    k = advance_pos(B.cell_pref, (int)k, i);
     update_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
   }
   if (!grid_sync(B)) return;
+  stamp(B, 5);
   // validity flags (every lane of a warp runs the same number of iterations for the ballot)
+  int kf = k0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += nth) {
     const long long i = base + threadIdx.x;
     bool f = false;
-    int k = 0;
     if (i < ncell) {
-      k = find_pos(B.cell_pref, B.npatch, i);
-      f = flag_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
+      kf = advance_pos(B.cell_pref, kf, i);
+      f = flag_cell(B.patches[B.order[kf]], i - B.cell_pref[kf]);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&B.counters[B.stage], (unsigned long long)__popc(bal));
   }
   if (!B.fofc) return;
   if (!grid_sync(B)) return;
+  stamp(B, 6);
   if (*(volatile unsigned long long*)(B.counters + B.stage) == 0) return;  // uniform over the grid
-  for (long long i = t0; i < ncell; i += nth) {
-    const int k = find_pos(B.cell_pref, B.npatch, i);
+  for (long long i = t0, k = k0; i < ncell; i += nth) {
+    k = advance_pos(B.cell_pref, (int)k, i);
     const Dev& D = B.patches[B.order[k]];
     fo_faces_cell(D, i - B.cell_pref[k]);
     fo_edges_cell(D, i - B.cell_pref[k]);
   }
   if (!grid_sync(B)) return;
-  for (long long i = t0; i < ncell; i += nth) {
-    const int k = find_pos(B.cell_pref, B.npatch, i);
+  stamp(B, 7);
+  for (long long i = t0, k = k0; i < ncell; i += nth) {
+    k = advance_pos(B.cell_pref, (int)k, i);
     fo_recompute_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
   }
 }
 
-// max over all cells of all patches of the CFL signal speed (Sec. 2.4)
+// max over all cells of all patches of the CFL signal speed (Sec. 2.4, cfl_speed_max), with the
+// running maximum shared across each warp after every pass
 __global__ void __launch_bounds__(256) k_batch_maxspeed(BatchDev B) {
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long ncell = B.cell_pref[B.npatch];
+  const int lane = threadIdx.x & 31;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int k = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
   double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += nth) {
-    const int k = find_pos(B.cell_pref, B.npatch, i);
-    const Dev& D = B.patches[B.order[k]];
-    const long long X = i - B.cell_pref[k];
-    double w[8];
-    prim_of(D, D.U0, D.B0, X, w);
-    const double hmin = fmin(D.h[0], fmin(D.h[1], D.h[2]));
-    const double rinv = 1.0 / w[0];
-    const double a2 = D.gam * w[4] * rinv;
-    const double b2 = fma(w[5], w[5], fma(w[6], w[6], w[7] * w[7]));
-    const double sum = fma(b2, rinv, a2);
-    for (int d = 0; d < 3; ++d) {
-      const double bn2 = w[5 + d] * w[5 + d];
-      const double disc = pmax(fma(sum, sum, -4.0 * (a2 * bn2 * rinv)), 0.0);
-      const double cf = sqrt(0.5 * (sum + sqrt(disc)));
-      const double v = (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]);
-      s = finite_d(v) ? pmax(s, v) : __longlong_as_double(0x7ff0000000000000LL);
+  for (long long base = t0 - lane; base < ncell; base += nth) {  // uniform over the warp
+    const long long i = base + lane;
+    if (i < ncell) {
+      k = advance_pos(B.cell_pref, k, i);
+      const Dev& D = B.patches[B.order[k]];
+      s = cfl_speed_max(D, D.U0, D.B0, i - B.cell_pref[k], s);
     }
+    unsigned long long b = (unsigned long long)dbits(s);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+      b = t > b ? t : b;
+    }
+    s = __longlong_as_double((long long)b);
   }
   // block max then one atomic
   unsigned long long bits = (unsigned long long)dbits(s);
@@ -265,6 +309,8 @@ struct mhd_batch {
   unsigned char* flag;
   unsigned long long* counters;   // 8
   unsigned* barrier;              // 2
+  unsigned long long* ptime;      // [2][8] phase stamps of the last step
+  unsigned long long* cursor;     // [3] sweep-phase work cursors
   double* dt_dev;
   mhd::Dev* pdev[2];              // per-patch parameters per stage
   int* order_dev;
@@ -406,6 +452,8 @@ mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc) {
   B.counters = b->counters;
   B.spin_limit = b->spin_limit;
   B.barrier_extra = b->barrier_extra;
+  B.ptime = b->ptime;
+  B.cursor = b->cursor;
   return B;
 }
 
@@ -423,6 +471,7 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
   const unsigned grid = (unsigned)(b->nsm * bps);
   e = cudaMemsetAsync(b->counters, 0, 8 * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 2 * sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ptime, 0, 16 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
   mhd::BatchDev B0 = batch_dev(b, 0, fofc);
   mhd::k_batch_maxspeed<<<b->nsm * 8, 256, 0, st>>>(B0);
@@ -504,7 +553,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->graph_ok = false;
   b->params_ok = false;
   const long long C = b->ncell;
-  size_t bytes = (size_t)C * (5 + 3 + 47) * sizeof(double) + (size_t)C + 16 * 256 +
+  size_t bytes = (size_t)C * (5 + 3 + 47) * sizeof(double) + (size_t)C + 24 * 256 +
                  2 * npatch * sizeof(mhd::Dev) + npatch * sizeof(int) + 4 * (npatch + 1) * sizeof(long long);
   cudaError_t e = cudaMalloc(&b->mem, bytes);
   if (e != cudaSuccess) {
@@ -520,6 +569,8 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->scratch = (double*)take(C * 47 * sizeof(double));
   b->counters = (unsigned long long*)take(8 * sizeof(unsigned long long));
   b->barrier = (unsigned*)take(2 * sizeof(unsigned));
+  b->ptime = (unsigned long long*)take(16 * sizeof(unsigned long long));
+  b->cursor = (unsigned long long*)take(4 * sizeof(unsigned long long));
   b->dt_dev = (double*)take(sizeof(double));
   b->pdev[0] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
   b->pdev[1] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
@@ -656,6 +707,21 @@ mhd_status mhd_batch_stats(mhd_batch* b, long long* s1, long long* s2) {
   if (s1) *s1 = (long long)h[0];
   if (s2) *s2 = (long long)h[1];
   if (h[7]) return bfail(b, MHD_ERR_TIMEOUT, "a grid barrier of the batched stage gave up waiting");
+  return MHD_OK;
+}
+
+mhd_status mhd_batch_phase_ms(mhd_batch* b, double* ms) {
+  if (!b || !ms) return MHD_ERR_ARG;
+  unsigned long long t[16];
+  cudaError_t e = cudaMemcpyAsync(t, b->ptime, sizeof(t), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  mhd_status s = bcuda(b, e, "read phase stamps");
+  if (s != MHD_OK) return s;
+  for (int st = 0; st < 2; ++st)
+    for (int j = 0; j < 7; ++j) {
+      const unsigned long long a = t[8 * st + j], z = t[8 * st + j + 1];
+      ms[7 * st + j] = (a && z && z >= a) ? (double)(z - a) * 1e-6 : 0.0;
+    }
   return MHD_OK;
 }
 

@@ -1,6 +1,8 @@
 // mhd_cell.cu -- per-cell kernels: conserved -> primitive (Sec. 2.2), the update increments
 // (Eqs. rk:increment-state, rk:increment-bfield), the validity flags and first-order flux
 // correction (Sec. 2.5), and the CFL and divergence reductions (Sec. 2.4, Sec. 2.1).
+#include <algorithm>
+
 #include "mhd_cell.cuh"
 
 namespace mhd {
@@ -58,26 +60,21 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* o
   __syncthreads();  // sm[] may be reused by a following call
 }
 
-// max over cells of max_d (|u_d| + c_fm,d) * hmin / h_d (Sec. 2.4, Eq. waves:fast-speed)
+// max over cells of the CFL signal speed (cfl_speed_max): a grid-stride loop whose warps share
+// their running maximum after every pass, so that most cells are settled by the bound check
 __global__ void __launch_bounds__(256) k_maxspeed(Dev D, const double* U, Ptr3 Bp,
                                                   unsigned long long* out) {
-  const long long X = cell_id();
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  if (X < D.N) {
-    double w[8];
-    prim_of(D, U, Bp.p, X, w);
-    const double hmin = fmin(D.h[0], fmin(D.h[1], D.h[2]));
-    const double rinv = rcp(w[0]);
-    const double a2 = D.gam * w[4] * rinv;
-    const double b2 = fma(w[5], w[5], fma(w[6], w[6], w[7] * w[7]));
-    const double sum = fma(b2, rinv, a2);
-    for (int d = 0; d < 3; ++d) {
-      const double bn2 = w[5 + d] * w[5 + d];
-      const double disc = pmax(fma(sum, sum, -4.0 * (a2 * bn2 * rinv)), 0.0);
-      const double cf = sqrt(0.5 * (sum + sqrt(disc)));
-      s = pmax(s, (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]));
+  for (long long base = cell_id() - lane; base < D.N; base += nth) {  // uniform over the warp
+    if (base + lane < D.N) s = cfl_speed_max(D, U, Bp.p, base + lane, s);
+    unsigned long long b = (unsigned long long)dbits(s);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+      b = t > b ? t : b;
     }
-    if (!finite_d(s)) s = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    s = __longlong_as_double((long long)b);
   }
   block_max_atomic(s, out);
 }
@@ -136,7 +133,8 @@ void launch_fofc(const Dev& d, cudaStream_t st) {
   k_fo_recompute<<<blocks_for(d.N, 128), 128, 0, st>>>(d);
 }
 void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st) {
-  k_maxspeed<<<blocks_for(d.N, 256), 256, 0, st>>>(d, U, B, out);
+  const long long cap = 2LL * resident_blocks((const void*)k_maxspeed, 256);  // two waves of blocks
+  k_maxspeed<<<(unsigned)std::min((long long)blocks_for(d.N, 256), cap), 256, 0, st>>>(d, U, B, out);
 }
 void launch_divb(const Dev& d, Ptr3 B, unsigned long long* out, cudaStream_t st) {
   k_divb<<<blocks_for(d.N, 256), 256, 0, st>>>(d, B, out);

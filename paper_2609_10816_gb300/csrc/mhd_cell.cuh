@@ -28,6 +28,39 @@ __device__ __forceinline__ void prim_of(const Dev& D, const double* U, const dou
   w[5] = b0; w[6] = b1; w[7] = b2;
 }
 
+// ---- CFL signal speed (Sec. 2.4, Eq. waves:fast-speed) ----------------------------------------
+// max(m, s) for the cell's speed s = max_d (|u_d| + c_f,d) hmin / h_d, given a running maximum m.
+// With S = a^2 + b^2/rho, every fast speed lies between sqrt(max(a^2, b^2/rho)) and sqrt(S) (the
+// discriminant (a^2 + b^2/rho)^2 - 4 a^2 b_d^2/rho is (a^2 - b^2/rho)^2 + 4 a^2 (b^2 - b_d^2)/rho),
+// so the three fast speeds are evaluated only when the upper bound, widened by 1e-12 against
+// rounding, reaches m: the running maximum is the same value, with two square roots for most
+// cells instead of six. A non-finite speed gives +inf.
+__device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, const double* const* B, long long X,
+                                                double m) {
+  double w[8];
+  prim_of(D, U, B, X, w);
+  const double hmin = fmin(D.h[0], fmin(D.h[1], D.h[2]));
+  const double rinv = rcp(w[0]);
+  const double a2 = D.gam * w[4] * rinv;
+  const double b2 = fma(w[5], w[5], fma(w[6], w[6], w[7] * w[7]));
+  const double sum = fma(b2, rinv, a2);
+  const double cu = sqrt_(sum);
+  double hi = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) hi = pmax(hi, (vabs(w[1 + d]) + cu) * (hmin * D.hinv[d]));
+  hi *= 1.0 + 1e-12;
+  if (finite_d(hi) && dbits(hi) < dbits(m)) return m;
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double bn2 = w[5 + d] * w[5 + d];
+    const double disc = pmax(fma(sum, sum, -4.0 * (a2 * bn2 * rinv)), 0.0);
+    const double cf = sqrt_(0.5 * (sum + sqrt_(disc)));
+    s = pmax(s, (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]));
+  }
+  if (!finite_d(s)) s = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+  return pmax(m, s);
+}
+
 __device__ __forceinline__ void prim_cell(const Dev& D, long long X) {
   double w[8];
   prim_of(D, D.Uin, D.Bin, X, w);

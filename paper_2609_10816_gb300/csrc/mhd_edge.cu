@@ -1,13 +1,24 @@
 // mhd_edge.cu -- edge-sweep kernels of the single-box step (bodies in mhd_edge.cuh).
+#include <algorithm>
+
 #include "mhd_edge.cuh"
 
 namespace mhd {
 
 template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_edge_bt(Dev D, int e, int seg) {
+  const int dir = (e + 2) % 3;
+  if (D.work) {
+    for_each_segment(D.work + 3 + e, sweep_threads(D, dir, seg), [&](long long t) {
+      Line ln;
+      int m0, m1;
+      if (sweep_line_at(D, dir, seg, t, ln, m0, m1, dir == 0)) edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
+    });
+    return;
+  }
   Line ln;
   int m0, m1;
-  if (!sweep_line(D, (e + 2) % 3, seg, ln, m0, m1)) return;
+  if (!sweep_line(D, dir, seg, ln, m0, m1, dir == 0)) return;
   edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
 }
 
@@ -15,15 +26,25 @@ template <int RC>
 __global__ void __launch_bounds__(128) k_b25_cell_to_face(Dev D, int e, int to_a, int seg) {
   Line ln;
   int m0, m1;
-  if (!sweep_line(D, to_a ? (e + 1) % 3 : (e + 2) % 3, seg, ln, m0, m1)) return;
+  const int dir = to_a ? (e + 1) % 3 : (e + 2) % 3;
+  if (!sweep_line(D, dir, seg, ln, m0, m1, dir == 0)) return;
   b25_seg<RC>(D, e, to_a, ln, m0, m1);
 }
 
 template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_edge_lr(Dev D, int e, int seg) {
+  const int dir = (e + 1) % 3;
+  if (D.work) {
+    for_each_segment(D.work + 6 + e, sweep_threads(D, dir, seg), [&](long long t) {
+      Line ln;
+      int m0, m1;
+      if (sweep_line_at(D, dir, seg, t, ln, m0, m1, dir == 0)) edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
+    });
+    return;
+  }
   Line ln;
   int m0, m1;
-  if (!sweep_line(D, (e + 1) % 3, seg, ln, m0, m1)) return;
+  if (!sweep_line(D, dir, seg, ln, m0, m1, dir == 0)) return;
   edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
 }
 
@@ -32,8 +53,14 @@ static void launch_bt_t(const Dev& d, int seg, cudaStream_t st) {
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int c = (e + 2) % 3;
-    const long long th = sweep_threads(d, c, seg);
-    k_edge_bt<RC, EMF><<<(unsigned)((th + bs - 1) / bs), bs, 0, st>>>(d, e, seg);
+    const int sg = edge_sweep_seg(d, c, seg);
+    const long long th = sweep_threads(d, c, sg);
+    long long blocks = (th + bs - 1) / bs;
+    if (d.work) {
+      blocks = std::min(blocks, (long long)resident_blocks((const void*)k_edge_bt<RC, EMF>, bs));
+      cudaMemsetAsync(d.work + 3 + e, 0, sizeof(unsigned long long), st);
+    }
+    k_edge_bt<RC, EMF><<<(unsigned)blocks, bs, 0, st>>>(d, e, sg);
   }
 }
 template <int RC, int EMF>
@@ -41,8 +68,14 @@ static void launch_lr_t(const Dev& d, int seg, cudaStream_t st) {
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3;
-    const long long th = sweep_threads(d, a, seg);
-    k_edge_lr<RC, EMF><<<(unsigned)((th + bs - 1) / bs), bs, 0, st>>>(d, e, seg);
+    const int sg = edge_sweep_seg(d, a, seg);
+    const long long th = sweep_threads(d, a, sg);
+    long long blocks = (th + bs - 1) / bs;
+    if (d.work) {
+      blocks = std::min(blocks, (long long)resident_blocks((const void*)k_edge_lr<RC, EMF>, bs));
+      cudaMemsetAsync(d.work + 6 + e, 0, sizeof(unsigned long long), st);
+    }
+    k_edge_lr<RC, EMF><<<(unsigned)blocks, bs, 0, st>>>(d, e, sg);
   }
 }
 template <int RC>
@@ -51,8 +84,9 @@ static void launch_b25_t(const Dev& d, int seg, cudaStream_t st) {
   for (int e = 0; e < 3; ++e)
     for (int to_a = 0; to_a < 2; ++to_a) {
       const int dir = to_a ? (e + 1) % 3 : (e + 2) % 3;
-      const long long th = sweep_threads(d, dir, seg);
-      k_b25_cell_to_face<RC><<<(unsigned)((th + bs - 1) / bs), bs, 0, st>>>(d, e, to_a, seg);
+      const int sg = edge_sweep_seg(d, dir, seg);
+      const long long th = sweep_threads(d, dir, sg);
+      k_b25_cell_to_face<RC><<<(unsigned)((th + bs - 1) / bs), bs, 0, st>>>(d, e, to_a, sg);
     }
 }
 

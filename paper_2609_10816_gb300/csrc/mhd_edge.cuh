@@ -112,8 +112,9 @@ __device__ __forceinline__ void b25_seg(const Dev& D, int e, int to_a, const Lin
 template <class T>
 __device__ __forceinline__ T ld04(T apa, T ama, T apc, T amc, T eLB, T eRB, T eLT, T eRT, T baB, T baT, T bcL,
                                   T bcR) {
-  const T ia = rcp(apa + ama), ic = rcp(apc + amc);
-  const T w = ia * ic;
+  const T sa = apa + ama, sc = apc + amc;
+  const T w = rcp(sa * sc);  // one reciprocal gives 1/sa, 1/sc and their product
+  const T ia = sc * w, ic = sa * w;
   const T up = fma(apc, fma(apa, eLB, ama * eRB), amc * fma(apa, eLT, ama * eRT)) * w;
   return fma(apa * ama * ia, bcR - bcL, fma(-apc * amc * ic, baT - baB, up));
 }

@@ -1,4 +1,6 @@
 // mhd_face.cu -- face-sweep kernels of the single-box step (body in mhd_face.cuh).
+#include <algorithm>
+
 #include "mhd_face.cuh"
 
 namespace mhd {
@@ -10,6 +12,14 @@ namespace mhd {
 
 template <int RC, int RS>
 __global__ void __launch_bounds__(128, MHD_FACE_MINB) k_face(Dev D, int dir, int seg) {
+  if (D.work) {
+    for_each_segment(D.work + dir, sweep_threads(D, dir, seg), [&](long long t) {
+      Line ln;
+      int m0, m1;
+      if (sweep_line_at(D, dir, seg, t, ln, m0, m1)) face_seg<RC, RS>(D, dir, ln, m0, m1);
+    });
+    return;
+  }
   Line ln;
   int m0, m1;
   if (!sweep_line(D, dir, seg, ln, m0, m1)) return;
@@ -20,7 +30,12 @@ template <int RC, int RS>
 static void launch_face_t(const Dev& d, int dir, int seg, cudaStream_t st) {
   const long long threads = sweep_threads(d, dir, seg);
   const int bs = 128;
-  k_face<RC, RS><<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(d, dir, seg);
+  long long blocks = (threads + bs - 1) / bs;
+  if (d.work) {
+    blocks = std::min(blocks, (long long)resident_blocks((const void*)k_face<RC, RS>, bs));
+    cudaMemsetAsync(d.work + dir, 0, sizeof(unsigned long long), st);
+  }
+  k_face<RC, RS><<<(unsigned)blocks, bs, 0, st>>>(d, dir, seg);
 }
 
 template <int RC>

@@ -54,6 +54,11 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
   for (int m = m0; m < m1; ++m) {
     const long long X = ln.at(m);
     const long long Xn = ln.at(m + LA);
+    double Fold[5];  // stage 2: the stage-1 flux, loaded before the solve so its latency is hidden
+    if (D.combine) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fold[v] = F[v * N + X];
+    }
     double Lv[7], Rv[7];
 #pragma unroll
     for (int v = 0; v < 7; ++v) r[v].step(q[v][Xn], Lv[v], Rv[v]);
@@ -71,7 +76,7 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
     g[4] = f[4];
     if (D.combine) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) F[v * N + X] = 0.5 * (F[v * N + X] + g[v]);
+      for (int v = 0; v < 5; ++v) F[v * N + X] = 0.5 * (Fold[v] + g[v]);
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) F[v * N + X] = g[v];

@@ -41,18 +41,31 @@ __host__ __device__ inline long long sweep_threads(const Dev& D, int dir, int se
   return (long long)D.n[t1] * D.n[t2] * nseg;
 }
 
-// segment number `tid` of the sweeps along dir (false past the last one)
+// segment number `tid` of the sweeps along dir (false past the last one). Segments are numbered
+// line by line, the faster line axis first, so that neighbouring threads walk neighbouring lines;
+// with seg_fastest the segments of one line take consecutive numbers instead, so that
+// neighbouring threads walk neighbouring stretches of the same line (for sweeps along x, whose
+// neighbouring lines lie nx apart: one thread per line would stream a separate cache line per
+// thread and array).
 __device__ __forceinline__ bool sweep_line_at(const Dev& D, int dir, int seg, long long tid, Line& ln, int& m0,
-                                              int& m1) {
+                                              int& m1, bool seg_fastest = false) {
   int t1, t2;
   sweep_axes(dir, t1, t2);
   const int n1 = D.n[t1], n2 = D.n[t2], nd = D.n[dir];
   const int nseg = (nd + seg - 1) / seg;
   if (tid >= (long long)n1 * n2 * nseg) return false;
-  const int i1 = (int)(tid % n1);
-  const long long r = tid / n1;
-  const int i2 = (int)(r % n2);
-  const int s = (int)(r / n2);
+  int i1, i2, s;
+  if (seg_fastest) {
+    s = (int)(tid % nseg);
+    const long long r = tid / nseg;
+    i1 = (int)(r % n1);
+    i2 = (int)(r / n1);
+  } else {
+    i1 = (int)(tid % n1);
+    const long long r = tid / n1;
+    i2 = (int)(r % n2);
+    s = (int)(r / n2);
+  }
   ln.base = (long long)i1 * D.stride[t1] + (long long)i2 * D.stride[t2];
   ln.stride = D.stride[dir];
   ln.n = nd;
@@ -61,8 +74,34 @@ __device__ __forceinline__ bool sweep_line_at(const Dev& D, int dir, int seg, lo
   return true;
 }
 
-__device__ __forceinline__ bool sweep_line(const Dev& D, int dir, int seg, Line& ln, int& m0, int& m1) {
-  return sweep_line_at(D, dir, seg, (long long)blockIdx.x * blockDim.x + threadIdx.x, ln, m0, m1);
+__device__ __forceinline__ bool sweep_line(const Dev& D, int dir, int seg, Line& ln, int& m0, int& m1,
+                                           bool seg_fastest = false) {
+  return sweep_line_at(D, dir, seg, (long long)blockIdx.x * blockDim.x + threadIdx.x, ln, m0, m1, seg_fastest);
+}
+
+// Dynamic schedule of a sweep: a persistent grid whose warps each take the next 32 segments of the
+// work list from a cursor in device memory until the list is exhausted, so that no SM idles while
+// others finish a long tail (segments differ in cost through the Riemann-fan and limiter branches).
+// Calls body(segment index) for every segment exactly once; lanes past the end skip the call.
+template <class Body>
+__device__ __forceinline__ void for_each_segment(unsigned long long* cursor, long long total, Body body) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    long long base = 0;
+    if (lane == 0) base = (long long)atomicAdd(cursor, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= total) return;
+    if (base + lane < total) body(base + lane);
+  }
+}
+
+// Segment length and numbering of the edge sweeps along dir: along x, a warp takes whole lines
+// (segments of about nx/32 points, 4 to 16, numbered along the line); along y and z the given
+// segment length with one line per thread.
+__host__ __device__ inline int edge_sweep_seg(const Dev& D, int dir, int seg) {
+  if (dir != 0) return seg;
+  const int s = (D.n[0] + 31) / 32;
+  return s < 4 ? 4 : (s > 16 ? 16 : s);
 }
 
 }  // namespace mhd

@@ -50,8 +50,14 @@ struct Dev {
   double* EfB;    // [3][2][N] B25a e-EMF on c-faces (B/T) for order (c then a)
   unsigned char* flag;         // [N]
   unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
+  // work-list cursors of the dynamically scheduled sweeps ([dir] face, [3 + e] edge_bt,
+  // [6 + e] edge_lr), zeroed before every stage; NULL: one segment per thread, no cursor
+  unsigned long long* work;
   int stage;      // 0 or 1 (which counter the flux correction reads)
 };
+
+// Work slots of the dynamically scheduled sweeps of one stage.
+constexpr int kWorkSlots = 9;
 
 // Adjoint of the flux function at a stage input state (mhd_adjoint.cu).
 struct AdjDev {
@@ -73,6 +79,10 @@ void launch_adj_flux(const AdjDev& A, int recon, int rs, cudaStream_t st);
 void launch_adj_update(const Dev& D, const double* lU, const double* lB, double* lF, double* lE, double scale,
                        double s_old, cudaStream_t st);
 void launch_axpy3(long long n, double* y, const double* a, const double* b, cudaStream_t st);
+
+// blocks of `threads` threads of kernel `fn` that fit on the device at once (all SMs), for the
+// persistent launches of the dynamically scheduled sweeps; cached per kernel
+int resident_blocks(const void* fn, int threads);
 
 // message reported by mhd_create_error() for calls that have no context
 void set_call_error(const char* msg);

@@ -157,6 +157,26 @@ def alfven_wave(shape, kvec=(1, 0, 0), bdir=(1.0, 0.0, 0.0), pol=(0.0, 0.0, 1.0)
     return assemble(rho, u, p, b, gamma), b, {"omega": ca * kk * cos_t, "k": kk, "h": box.h}
 
 
+def alfven_oblique(shape, kvec=(1, 2, 3), theta=np.pi / 4, amp=1e-6, gamma=GAMMA):
+    """The linearly polarised Alfven wave of the paper's throughput runs (Sec. 5.2 with the setup
+    of Sec. 4.1.1 and the oblique geometry of Sec. 5.1): rho = b_bg = 1, p = 1/gamma, L = 1,
+    k L / 2 pi = kvec, theta = angle(b_bg, k) = pi/4. The polarisation n_perp is orthogonal to
+    n_k and to the x2 axis ((-2, 1, 0)/sqrt5 for k ~ (1, 2, 3)); b_bg lies in the plane of n_k
+    and the x2 axis, turned from n_k by theta towards +x2, so that n_perp is also orthogonal to
+    it (an Alfven mode)."""
+    k = np.asarray(kvec, float)
+    nk = k / np.linalg.norm(k)
+    npol = np.cross((0.0, 0.0, 1.0), nk)
+    npol /= np.linalg.norm(npol)
+    e = np.cross(nk, npol)  # unit, orthogonal to n_k and n_perp, positive x2 component
+    if e[2] < 0:
+        e = -e
+    nb = np.cos(theta) * nk + np.sin(theta) * e
+    cons, b, info = alfven_wave(shape, kvec=kvec, bdir=nb, pol=npol, amp=amp, gamma=gamma)
+    info.update(n_bg=nb, n_perp=npol)
+    return cons, b, info
+
+
 def circular_alfven(shape, rho0=1.0, p0=1.0 / GAMMA, b0=1.0, amp=0.1, t=0.0, gamma=GAMMA, L=1.0):
     """Circularly polarised Alfven wave along x0 (Sec. 3.1.2): exact at any amplitude."""
     box = Box(shape, (L, L, L))

@@ -105,6 +105,8 @@ def lib():
     L.mhd_batch_last_dt.restype = i
     L.mhd_batch_stats.argtypes = [vp, P(ll), P(ll)]
     L.mhd_batch_stats.restype = i
+    L.mhd_batch_phase_ms.argtypes = [vp, P(d)]
+    L.mhd_batch_phase_ms.restype = i
     L.mhd_batch_set_schedule.argtypes = [vp, i, i, i, i]
     L.mhd_batch_set_schedule.restype = i
     L.mhd_batch_tune.argtypes = [vp, P(_BatchState), d, i, d, P(i), P(i), P(i)]
@@ -288,6 +290,14 @@ class Batch:
         a, c = ctypes.c_longlong(), ctypes.c_longlong()
         self._err(lib().mhd_batch_stats(self._h, ctypes.byref(a), ctypes.byref(c)))
         return a.value, c.value
+
+    PHASES = ("prim", "face", "edge_bt", "edge_lr", "update", "flag", "fo_fluxes")
+
+    def phase_ms(self):
+        """Device time of each phase of the last step's two stages, {stage: {phase: ms}}."""
+        out = (ctypes.c_double * 14)()
+        self._err(lib().mhd_batch_phase_ms(self._h, out))
+        return {s: {ph: out[7 * s + j] for j, ph in enumerate(self.PHASES)} for s in (0, 1)}
 
     def set_schedule(self, seg=64, order=1, blocks_per_sm=0, use_graph=True):
         self._err(lib().mhd_batch_set_schedule(self._h, int(seg), int(order), int(blocks_per_sm), 1 if use_graph else 0))

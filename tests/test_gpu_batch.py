@@ -119,3 +119,20 @@ def test_batch_barrier_wait_is_bounded(gpu_lib):
     cp, bp, _ = _plain_step(dims[0], *pats[0], bt.last_dt(), sch, 0.0)
     c1, b1 = bt.unpack(c2, b2, 0)
     assert np.array_equal(c1, cp) and np.array_equal(b1, bp)
+
+
+def test_batch_phase_times(gpu_lib):
+    """Phase stamps of the persistent stage kernel: every phase that ran has a non-negative
+    duration, the sweeps take time, and the flux-correction phase is zero without flagged cells."""
+    dims, pats = _patches(12, seed=5)
+    bt = mhd.Batch(dims, H)
+    cons, b = bt.pack(pats)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    bt.step(cons, b, 0.3, sch)
+    ph = bt.phase_ms()
+    assert bt.stats() == (0, 0)
+    for s in (0, 1):
+        assert all(v >= 0.0 for v in ph[s].values())
+        assert ph[s]["face"] > 0.0
+        assert ph[s]["fo_fluxes"] == 0.0
+    bt.close()

@@ -108,6 +108,46 @@ def test_turbulence_256cubed_sampled(gpu_lib, emf):
     assert worst <= 1e-12, worst
 
 
+@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
+def test_alfven_oblique_24cubed_full(gpu_lib, emf):
+    """The throughput workload's oblique Alfven wave (k ~ (1, 2, 3), theta = pi/4) at 24^3,
+    PPM + HLLD, each EMF compute scheme: 5 CFL steps against the oracle on the whole box."""
+    shape = (24, 24, 24)
+    cons, b, info = inputs.alfven_oblique(shape)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon="ppm", riemann="hlld", emf=emf)
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    sch = mhd.scheme("ppm", "hlld", emf)
+    scales = field_scales(cons, b)
+    co, bo = cons, b
+    for _ in range(5):
+        dt = ctx.max_dt(st, 0.3)
+        ctx.step(st, dt, sch)
+        co, bo, _ = oracle.step(cfg, co, bo, dt)
+    torch.cuda.synchronize()
+    cg, bg = st.cons.cpu().numpy(), st.b.cpu().numpy()
+    errs = [rel_l1(cg[v], co[v], scales[0][v]) for v in range(5)] + [rel_l1(bg[d], bo[d], scales[1][d]) for d in range(3)]
+    assert max(errs) <= 1e-12, errs
+    md, mb = ctx.divb(st)
+    ctx.close()
+    assert md * info["h"][0] / mb <= 1e-13
+
+
+@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
+def test_alfven_oblique_128cubed_sampled(gpu_lib, emf):
+    """The same wave at the throughput run's 128^3: one full-size GPU step against the oracle
+    on three sampled sub-boxes."""
+    n = 128
+    cons, b, info = inputs.alfven_oblique((n, n, n))
+    sch = mhd.scheme("ppm", "hlld", emf)
+    cg, bg, dt, div, _ = _gpu_step((n, n, n), info["h"], cons, b, sch, 0.0)
+    assert div <= 1e-13
+    centres = [(0, 0, 0), (64, 32, 100), (17, 90, 45)]
+    worst = _sampled_parity(cons, b, cg, bg, info["h"], dt, dict(recon="ppm", riemann="hlld", emf=emf), 0.0,
+                            centres)
+    assert worst <= 1e-12, worst
+
+
 def test_reconnection_512x512x4_sampled(gpu_lib):
     """512 x 512 x 4 double Harris sheet, eta = 1e-4, PLM-MC + HLLD + Q26 + LD04: one full-size
     step against the oracle on sub-boxes across both current sheets (all 4 cells in z)."""

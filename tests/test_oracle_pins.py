@@ -326,6 +326,23 @@ def test_fast_wave_second_order_3d_diagonal():
     assert errs[0] / errs[1] > 3.0, errs
 
 
+def test_oblique_alfven_wave_second_order_ppm_hlld():
+    """The throughput workload's oblique linear Alfven wave (k ~ (1, 2, 3), theta = pi/4),
+    PPM + HLLD + Q26: after one period the exact state is the initial one; the error shrinks
+    towards second order from 16^3 to 32^3 (5 and 11 cells per wavelength along x2)."""
+    errs = []
+    for n in (16, 32):
+        shape = (n, n, n)
+        cons, b, info = inputs.alfven_oblique(shape)
+        cbg, bbg, _ = inputs.alfven_oblique(shape, amp=0.0)
+        assert np.allclose(info["n_perp"] @ np.array([1, 2, 3]), 0) and abs(info["n_perp"][2]) == 0.0
+        assert info["n_bg"] @ info["n_perp"] == pytest.approx(0.0, abs=1e-15)
+        cfg = cfg_for(shape, info, recon="ppm", riemann="hlld")
+        c, bb = _one_period(cfg, cons, b, 2 * np.pi / info["omega"])
+        errs.append(_relerr_pert(cons, b, c, bb, cbg, bbg))
+    assert errs[0] / errs[1] > 3.0, errs
+
+
 def test_circular_alfven_exact_nonlinear():
     """Finite-amplitude circularly polarised Alfven wave: exact solution, second-order error."""
     errs = []
