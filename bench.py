@@ -39,11 +39,12 @@ HBM_PEAK_GBS = 6759.6  # MEASURED_PEAKS.json copy bandwidth
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 676.0e6, "cells": 160**3, "src": "6c321db76d18bb2f"}}
+TRAFFIC = {"face": {"bytes_per_launch": 688.0e6, "cells": 160**3, "src": "a42215e424c47769"}}
 
 
-# sources the face sweep is compiled from (its kernel, the numerics, indexing and parameters)
-FACE_SOURCES = ("mhd_face.cu", "mhd_face.cuh", "mhd_device.cuh", "mhd_index.cuh", "mhd_internal.cuh")
+# what the face sweep's machine code is compiled from: its kernel, the numerics and indexing
+# headers, and the layout of the parameter struct it receives
+FACE_SOURCES = ("mhd_face.cu", "mhd_face.cuh", "mhd_device.cuh", "mhd_index.cuh")
 
 
 def kernel_src_hash(files=FACE_SOURCES):
@@ -51,25 +52,10 @@ def kernel_src_hash(files=FACE_SOURCES):
     csrc = os.path.join(ROOT, "paper_2609_10816_gb300", "csrc")
     for f in sorted(files):
         h.update(open(os.path.join(csrc, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "mhd.h"), "rb").read())
+    internal = open(os.path.join(csrc, "mhd_internal.cuh")).read()
+    i0 = internal.index("struct Dev {")
+    h.update(internal[i0:internal.index("};", i0)].encode())
     return h.hexdigest()[:16]
-
-
-def max_over_ranks(x, dist, dev):
-    """The largest of the ranks' values of x (the slowest rank's time); x itself at N = 1."""
-    if dist is None:
-        return x
-    import torch
-
-    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def whole_job_rate(units_per_rank, world, ms):
-    """Units processed by all ranks per second, timed by the slowest rank (replicas: every rank
-    advances its own box of the same size)."""
-    return world * units_per_rank / (ms / 1e3)
 
 
 class ClockSampler:

@@ -143,6 +143,17 @@ mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_stat
  * The paper has no counterpart. */
 mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
 
+/* Self-check of the adjoint's reverse sweep through the face solve (the Riemann solver of
+ * `scheme`'s bits 4-7; mhd_step_adjoint uses it): on n hashed face problems (seed), from equal
+ * states to extreme ones, with zero normal field and field along the normal among them, and
+ * random output weights, it compares the reverse-mode gradient of the weighted fluxes, speeds
+ * and face velocity in the 15 inputs with the same gradient from 15 forward-mode dual-number
+ * passes. max_rel_err (7 doubles) receives the largest |difference| / |dual gradient|_inf over
+ * all problems, then per kind of problem: equal states, nearby states, no normal field, field
+ * along the normal, near-vacuum pressure, large velocities and fields. Synchronous. The paper
+ * has no counterpart. */
+mhd_status mhd_adjoint_check(mhd_ctx *ctx, long long n, int scheme, unsigned long long seed, double *max_rel_err);
+
 /* Message of the last failure on ctx ("" if none). Valid until the next call on ctx. */
 const char *mhd_last_error(const mhd_ctx *ctx);
 

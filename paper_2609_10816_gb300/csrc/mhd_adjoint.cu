@@ -21,6 +21,7 @@
 #include "mhd_cell.cuh"
 #include "mhd_edge.cuh"
 #include "mhd_face.cuh"
+#include "mhd_riemann_vjp.cuh"
 
 namespace mhd {
 
@@ -157,6 +158,49 @@ __global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
 }
 
 // ---- faces: adjoint of the Riemann solve -------------------------------------------------
+// gradient of the weighted face outputs in the 15 inputs by the dual numbers: one forward pass
+// per input (the reference that the reverse sweep of mhd_riemann_vjp.cuh is checked against)
+template <int RS>
+__device__ void riemann_grad_dual(const double* WL, const double* WR, double bn, double gam, double gm1inv,
+                                  const double* lf, double lap, double lam_, double lus, double* g) {
+#pragma unroll 1
+  for (int i = 0; i < 15; ++i) {
+    FaceStateT<Dual> sl, sr;
+    Dual* pl = &sl.rho;
+    Dual* pr = &sr.rho;
+    for (int v = 0; v < 7; ++v) {
+      pl[v] = Dual(WL[v], i == v ? 1.0 : 0.0);
+      pr[v] = Dual(WR[v], i == 7 + v ? 1.0 : 0.0);
+    }
+    const Dual b = Dual(bn, i == 14 ? 1.0 : 0.0);
+    Dual F[5], ap, am, us;
+    riemann<RS>(sl, sr, b, gam, gm1inv, F, ap, am, us);
+    double acc = lap * ap.t + lam_ * am.t + lus * us.t;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc = fma(lf[v], F[v].t, acc);
+    g[i] = acc;
+  }
+}
+
+// the same gradient by the reverse sweep
+template <int RS>
+__device__ __forceinline__ void riemann_grad_rev(const double* WL, const double* WR, double bn, double gam,
+                                                 double gm1inv, const double* lf, double lap, double lam_,
+                                                 double lus, double* g) {
+  const FaceState sl = {WL[0], WL[1], WL[2], WL[3], WL[4], WL[5], WL[6]};
+  const FaceState sr = {WR[0], WR[1], WR[2], WR[3], WR[4], WR[5], WR[6]};
+  FaceState dl, dr;
+  double dbn;
+  riemann_vjp<RS>(sl, sr, bn, gam, gm1inv, lf, lap, lam_, lus, dl, dr, dbn);
+  const double* pl = &dl.rho;
+  const double* pr = &dr.rho;
+  for (int v = 0; v < 7; ++v) {
+    g[v] = pl[v];
+    g[7 + v] = pr[v];
+  }
+  g[14] = dbn;
+}
+
 template <int RC, int RS>
 __global__ void __launch_bounds__(128) k_adj_faces(AdjDev A, int dir) {
   const Dev& D = A.D;
@@ -177,27 +221,81 @@ __global__ void __launch_bounds__(128) k_adj_faces(AdjDev A, int dir) {
   const double* lF = A.lF + 5LL * dir * N;
   const double lf[5] = {lF[0 * N + f], lF[(1 + dir) * N + f], lF[(1 + a) * N + f], lF[(1 + c) * N + f],
                         lF[4 * N + f]};
-  const double lap = A.lAp[dir * N + f], lam_ = A.lAm[dir * N + f], lus = A.lUs[dir * N + f];
-#pragma unroll 1
-  for (int i = 0; i < 15; ++i) {
-    FaceStateT<Dual> sl, sr;
-    Dual* pl = &sl.rho;
-    Dual* pr = &sr.rho;
-    for (int v = 0; v < 7; ++v) {
-      pl[v] = Dual(WL[v], i == v ? 1.0 : 0.0);
-      pr[v] = Dual(WR[v], i == 7 + v ? 1.0 : 0.0);
-    }
-    const Dual b = Dual(bn, i == 14 ? 1.0 : 0.0);
-    Dual F[5], ap, am, us;
-    riemann<RS>(sl, sr, b, D.gam, D.gm1inv, F, ap, am, us);
-    double g = lap * ap.t + lam_ * am.t + lus * us.t;
+  double g[15];
+  riemann_grad_rev<RS>(WL, WR, bn, D.gam, D.gm1inv, lf, A.lAp[dir * N + f], A.lAm[dir * N + f],
+                       A.lUs[dir * N + f], g);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) g = fma(lf[v], F[v].t, g);
-    if (i < 14)
-      A.lLR[(14LL * dir + i) * N + f] = g;
-    else
-      atomicAdd(&A.lB[dir * N + f], g);
+  for (int i = 0; i < 14; ++i) A.lLR[(14LL * dir + i) * N + f] = g[i];
+  atomicAdd(&A.lB[dir * N + f], g[14]);
+}
+
+// Self-check of the reverse sweep: n hashed face problems (states from smooth to extreme, with
+// repeated, zero and sign-flipped values to reach the degenerate branches) and weights; the
+// largest |reverse - dual| / (|dual|_inf + 1e-300) over all problems goes to out[0] and, per
+// kind of problem, to out[1 + kind] (as bits).
+__device__ __forceinline__ double hash_unit(unsigned long long k) {  // splitmix64 -> [0, 1)
+  k += 0x9e3779b97f4a7c15ull;
+  k = (k ^ (k >> 30)) * 0xbf58476d1ce4e5b9ull;
+  k = (k ^ (k >> 27)) * 0x94d049bb133111ebull;
+  k ^= k >> 31;
+  return (double)(k >> 11) * (1.0 / 9007199254740992.0);
+}
+// the kind of face problem number i of the check (0 equal states, 1 nearby states, 2 no normal
+// field, 3 field along the normal, 4 near-vacuum pressure, 5 large velocities and fields)
+__device__ __forceinline__ int mode_of(unsigned long long seed, long long i) {
+  return (int)(hash_unit(seed * 0x100000001b3ull + (unsigned long long)i * 64) * 6.0);
+}
+template <int RS>
+__global__ void __launch_bounds__(128) k_vjp_check(long long n, unsigned long long seed, double gam,
+                                                   unsigned long long* out) {
+  const long long i = aid();
+  double err = 0.0;
+  if (i < n) {
+    unsigned long long k = seed * 0x100000001b3ull + (unsigned long long)i * 64;
+    auto u = [&]() { return hash_unit(k++); };
+    const int mode = (int)(u() * 6.0);
+    double WL[7], WR[7];
+    const double scale = mode == 5 ? 20.0 : 2.0;
+    WL[0] = 0.05 + 2.0 * u();
+    WL[4] = (mode == 4 ? 1e-4 : 0.02) + 2.0 * u();
+    for (int v : {1, 2, 3, 5, 6}) WL[v] = scale * (2.0 * u() - 1.0);
+    for (int v = 0; v < 7; ++v) WR[v] = WL[v];
+    if (mode != 0) {  // mode 0: equal states
+      WR[0] = 0.05 + 2.0 * u();
+      WR[4] = (mode == 4 ? 1e-4 : 0.02) + 2.0 * u();
+      for (int v : {1, 2, 3, 5, 6}) WR[v] = mode == 1 ? WL[v] + 0.01 * (2.0 * u() - 1.0) : scale * (2.0 * u() - 1.0);
+    }
+    double bn = 2.0 * (2.0 * u() - 1.0);
+    if (mode == 2) bn = 0.0;               // no normal field
+    if (mode == 3) { WL[1] = 0.0; WR[1] = 0.0; WL[5] = WR[5] = 0.0; WL[6] = WR[6] = 0.0; }  // field along n
+    const double lf[5] = {2 * u() - 1, 2 * u() - 1, 2 * u() - 1, 2 * u() - 1, 2 * u() - 1};
+    const double lap = 2 * u() - 1, lam_ = 2 * u() - 1, lus = 2 * u() - 1;
+    const double gm1inv = 1.0 / (gam - 1.0);
+    double gd[15], gr[15];
+    riemann_grad_dual<RS>(WL, WR, bn, gam, gm1inv, lf, lap, lam_, lus, gd);
+    riemann_grad_rev<RS>(WL, WR, bn, gam, gm1inv, lf, lap, lam_, lus, gr);
+    double nrm = 0.0, dif = 0.0;
+    for (int v = 0; v < 15; ++v) {
+      nrm = pmax(nrm, vabs(gd[v]));
+      dif = pmax(dif, vabs(gr[v] - gd[v]));
+    }
+    err = (finite_d(nrm) && finite_d(dif)) ? dif / (nrm + 1e-300) : 1e300;
   }
+  if (i < n) atomicMax(out + 1 + mode_of(seed, i), (unsigned long long)dbits(err));
+  unsigned long long b = (unsigned long long)dbits(err);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+    b = t > b ? t : b;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, b);
+}
+
+void launch_vjp_check(long long n, unsigned long long seed, double gam, int rs, unsigned long long* out,
+                      cudaStream_t st) {
+  const unsigned nb = (unsigned)((n + 127) / 128);
+  if (rs == RS_HLL) k_vjp_check<RS_HLL><<<nb, 128, 0, st>>>(n, seed, gam, out);
+  else if (rs == RS_HLLD) k_vjp_check<RS_HLLD><<<nb, 128, 0, st>>>(n, seed, gam, out);
+  else k_vjp_check<RS_LLF><<<nb, 128, 0, st>>>(n, seed, gam, out);
 }
 
 // ---- Joule flux eta (j x b)_d (bilinear; by hand) ----------------------------------------

@@ -498,6 +498,29 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   return MHD_OK;
 }
 
+mhd_status mhd_adjoint_check(mhd_ctx* ctx, long long n, int scheme, unsigned long long seed, double* max_rel_err) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!max_rel_err || n < 1 || n > (1LL << 34)) return fail(ctx, MHD_ERR_ARG, "need 1 <= n <= 2^34 and an output");
+  Decoded sc;
+  mhd_status s = decode(ctx, scheme, sc);
+  if (s != MHD_OK) return s;
+  const mhd::Dev& D = ctx->base;
+  // 7 results: the scratch's work cursors serve (they are rezeroed before every sweep)
+  unsigned long long* out = D.work;
+  s = cuda_check(ctx, cudaMemsetAsync(out, 0, 7 * sizeof(unsigned long long), ctx->stream), "cudaMemsetAsync");
+  if (s != MHD_OK) return s;
+  mhd::launch_vjp_check(n, seed, D.gam, sc.rs, out, ctx->stream);
+  s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
+  if (s != MHD_OK) return s;
+  unsigned long long h[7];
+  s = cuda_check(ctx, cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+  if (s == MHD_OK) s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  std::memcpy(max_rel_err, h, sizeof(h));
+  return MHD_OK;
+}
+
 mhd_status mhd_math_check(mhd_ctx* ctx, long long n, double* max_rel_err) {
   if (!ctx) return MHD_ERR_ARG;
   ctx->err.clear();

@@ -95,9 +95,21 @@ __device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.
 __device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.t - b.t); }
 __device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.t); }
 __device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, fma(a.t, b.v, a.v * b.t)); }
+// mixed forms with a constant operand (no tangent arithmetic for the constant's zero tangent)
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.t); }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return Dual(a.v * b, a.t * b); }
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return Dual(a.v + b, a.t); }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return Dual(a + b.v, b.t); }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return Dual(a.v - b, a.t); }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return Dual(a - b.v, -b.t); }
 __device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 __device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) {
   return Dual(fma(a.v, b.v, c.v), fma(a.t, b.v, fma(a.v, b.t, c.t)));
+}
+__device__ __forceinline__ Dual fma(double a, Dual b, Dual c) { return Dual(fma(a, b.v, c.v), fma(a, b.t, c.t)); }
+__device__ __forceinline__ Dual fma(Dual a, double b, Dual c) { return Dual(fma(a.v, b, c.v), fma(a.t, b, c.t)); }
+__device__ __forceinline__ Dual fma(Dual a, Dual b, double c) {
+  return Dual(fma(a.v, b.v, c), fma(a.t, b.v, a.v * b.t));
 }
 __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ double val(const Dual& x) { return x.v; }
@@ -126,9 +138,11 @@ __device__ __forceinline__ Dual rsqrt_(Dual x) {
   const double r = rsqrt_(x.v);
   return Dual(r, -0.5 * x.t * r * r * r);
 }
+// sqrt(x) = x rsqrt(x) (the value of sqrt_), derivative rsqrt(x) / 2; both 0 at x = 0
 __device__ __forceinline__ Dual sqrt_(Dual x) {
-  const double r = sqrt_(x.v);
-  return Dual(r, is_zero(r) ? 0.0 : 0.5 * x.t / r);
+  const double q = rsqrt_(x.v);
+  const bool z = is_zero(x.v);
+  return Dual(z ? 0.0 : x.v * q, z ? 0.0 : 0.5 * q * x.t);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -53,12 +53,15 @@ static void launch_bt_t(const Dev& d, int seg, cudaStream_t st) {
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int c = (e + 2) % 3;
-    const int sg = edge_sweep_seg(d, c, seg);
-    const long long th = sweep_threads(d, c, sg);
-    long long blocks = (th + bs - 1) / bs;
+    int sg = edge_sweep_seg(d, c, seg);
+    long long blocks;
     if (d.work) {
-      blocks = std::min(blocks, (long long)resident_blocks((const void*)k_edge_bt<RC, EMF>, bs));
+      const long long res = resident_blocks((const void*)k_edge_bt<RC, EMF>, bs);
+      if (c != 0) sg = fill_seg(d, c, sg, res * bs);
+      blocks = std::min((sweep_threads(d, c, sg) + bs - 1) / bs, res);
       cudaMemsetAsync(d.work + 3 + e, 0, sizeof(unsigned long long), st);
+    } else {
+      blocks = (sweep_threads(d, c, sg) + bs - 1) / bs;
     }
     k_edge_bt<RC, EMF><<<(unsigned)blocks, bs, 0, st>>>(d, e, sg);
   }
@@ -68,12 +71,15 @@ static void launch_lr_t(const Dev& d, int seg, cudaStream_t st) {
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3;
-    const int sg = edge_sweep_seg(d, a, seg);
-    const long long th = sweep_threads(d, a, sg);
-    long long blocks = (th + bs - 1) / bs;
+    int sg = edge_sweep_seg(d, a, seg);
+    long long blocks;
     if (d.work) {
-      blocks = std::min(blocks, (long long)resident_blocks((const void*)k_edge_lr<RC, EMF>, bs));
+      const long long res = resident_blocks((const void*)k_edge_lr<RC, EMF>, bs);
+      if (a != 0) sg = fill_seg(d, a, sg, res * bs);
+      blocks = std::min((sweep_threads(d, a, sg) + bs - 1) / bs, res);
       cudaMemsetAsync(d.work + 6 + e, 0, sizeof(unsigned long long), st);
+    } else {
+      blocks = (sweep_threads(d, a, sg) + bs - 1) / bs;
     }
     k_edge_lr<RC, EMF><<<(unsigned)blocks, bs, 0, st>>>(d, e, sg);
   }

@@ -28,14 +28,17 @@ __global__ void __launch_bounds__(128, MHD_FACE_MINB) k_face(Dev D, int dir, int
 
 template <int RC, int RS>
 static void launch_face_t(const Dev& d, int dir, int seg, cudaStream_t st) {
-  const long long threads = sweep_threads(d, dir, seg);
   const int bs = 128;
-  long long blocks = (threads + bs - 1) / bs;
   if (d.work) {
-    blocks = std::min(blocks, (long long)resident_blocks((const void*)k_face<RC, RS>, bs));
+    const long long res = resident_blocks((const void*)k_face<RC, RS>, bs);
+    seg = fill_seg(d, dir, seg, res * bs);
+    const long long blocks = std::min((sweep_threads(d, dir, seg) + bs - 1) / bs, res);
     cudaMemsetAsync(d.work + dir, 0, sizeof(unsigned long long), st);
+    k_face<RC, RS><<<(unsigned)blocks, bs, 0, st>>>(d, dir, seg);
+    return;
   }
-  k_face<RC, RS><<<(unsigned)blocks, bs, 0, st>>>(d, dir, seg);
+  const long long threads = sweep_threads(d, dir, seg);
+  k_face<RC, RS><<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(d, dir, seg);
 }
 
 template <int RC>

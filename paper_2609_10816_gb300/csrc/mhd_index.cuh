@@ -95,6 +95,14 @@ __device__ __forceinline__ void for_each_segment(unsigned long long* cursor, lon
   }
 }
 
+// Segment length of a dynamically scheduled sweep: the requested length, halved (down to 8) until
+// the sweep has at least two segments per resident thread, so that small boxes still fill the GPU
+// (a shorter segment costs one more window start-up, about two points of reconstruction).
+__host__ __device__ inline int fill_seg(const Dev& D, int dir, int seg, long long resident_threads) {
+  while (seg > 8 && sweep_threads(D, dir, seg) < 2 * resident_threads) seg = (seg + 1) / 2;
+  return seg;
+}
+
 // Segment length and numbering of the edge sweeps along dir: along x, a warp takes whole lines
 // (segments of about nx/32 points, 4 to 16, numbered along the line); along y and z the given
 // segment length with one line per thread.

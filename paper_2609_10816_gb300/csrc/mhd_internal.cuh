@@ -79,6 +79,8 @@ void launch_adj_flux(const AdjDev& A, int recon, int rs, cudaStream_t st);
 void launch_adj_update(const Dev& D, const double* lU, const double* lB, double* lF, double* lE, double scale,
                        double s_old, cudaStream_t st);
 void launch_axpy3(long long n, double* y, const double* a, const double* b, cudaStream_t st);
+void launch_vjp_check(long long n, unsigned long long seed, double gam, int rs, unsigned long long* out,
+                      cudaStream_t st);
 
 // blocks of `threads` threads of kernel `fn` that fit on the device at once (all SMs), for the
 // persistent launches of the dynamically scheduled sweeps; cached per kernel

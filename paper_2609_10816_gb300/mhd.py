@@ -87,6 +87,8 @@ def lib():
     L.mhd_step_adjoint.restype = ctypes.c_int
     L.mhd_math_check.argtypes = [vp, ctypes.c_longlong, P(d)]
     L.mhd_math_check.restype = ctypes.c_int
+    L.mhd_adjoint_check.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_ulonglong, P(d)]
+    L.mhd_adjoint_check.restype = ctypes.c_int
     L.mhd_profile.argtypes = [vp, ctypes.c_int]
     L.mhd_profile.restype = ctypes.c_int
     L.mhd_profile_read.argtypes = [vp, P(d), P(ctypes.c_longlong), ctypes.c_int]
@@ -192,6 +194,15 @@ class Context:
         self._err(lib().mhd_step_adjoint(self._h, ctypes.byref(s), ctypes.byref(l), float(dt), int(scheme_bits),
                                          float(eta), ctypes.byref(out)))
         return out.value
+
+    ADJ_CHECK_KINDS = ("equal", "nearby", "bn_zero", "field_along_n", "low_pressure", "large")
+
+    def adjoint_check(self, scheme_bits: int, n: int = 1 << 20, seed: int = 1):
+        """Largest relative gap between the reverse-mode and dual-number gradients of the face solve:
+        (overall, {kind of face problem: largest gap})."""
+        out = (ctypes.c_double * 7)()
+        self._err(lib().mhd_adjoint_check(self._h, int(n), int(scheme_bits), int(seed), out))
+        return out[0], dict(zip(self.ADJ_CHECK_KINDS, out[1:]))
 
     def math_check(self, n: int = 1 << 22):
         """Largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE."""
