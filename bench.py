@@ -58,6 +58,23 @@ def kernel_src_hash(files=FACE_SOURCES):
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(x, dist, dev):
+    """The largest of the ranks' values of x (the slowest rank's time); x itself at N = 1."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, timed by the slowest rank (replicas: every rank
+    advances its own box of the same size)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples every 200 ms while running."""
 

@@ -79,3 +79,27 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_bench_module_names_resolve():
+    """Every global name a function of bench.py loads is defined in the module or a builtin (the
+    GPU legs cannot run here, so a missing helper would surface only on the GPU machine)."""
+    import builtins
+    import dis
+    import types
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def globals_used(code):
+        for ins in dis.get_instructions(code):
+            if ins.opname in ("LOAD_GLOBAL", "LOAD_NAME"):
+                yield ins.argval
+        for c in code.co_consts:
+            if isinstance(c, types.CodeType):
+                yield from globals_used(c)
+
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    missing = sorted({n for n in globals_used(compile(src, "bench.py", "exec"))
+                      if not hasattr(bench, n) and not hasattr(builtins, n)})
+    assert not missing, missing
