@@ -27,18 +27,109 @@ namespace mhd {
 
 __device__ __forceinline__ long long aid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 
-// lower/upper values of point m of `arr` along dir, from the window m-2 .. m+2, with a unit
-// tangent on every window slot that holds point Y (several on lines shorter than the window)
+// adds v, summed over the warp, to *out with one atomic (every lane of the warp must call it)
+__device__ __forceinline__ void warp_add(double v, double* out) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
+}
+
+// Jacobian of a point's reconstructed lower / upper values (aL, aR) in its window q[0..4]
+// (q[2] the point): every reconstruction is piecewise linear, so the rows follow from the branch
+// decisions, taken on the same values and with the same tie rules as the forward sweep.
+// d(slope) / d(dl, dr) of the limited slopes, on the branch taken
+__device__ __forceinline__ void vl_slope2_jac(double dl, double dr, double& gl, double& gr) {
+  gl = gr = 0.0;
+  if (!same_sign(dl, dr)) return;
+  const double a = vabs(dl + dr);
+  const bool left_min = dbits(vabs(dl)) <= dbits(vabs(dr));
+  const double m4 = times4(left_min ? vabs(dl) : vabs(dr));
+  if (dbits(a) <= dbits(m4)) { gl = 1.0; gr = 1.0; }   // |dl + dr|
+  else if (left_min) gl = 4.0;                         // 4 |dl|
+  else gr = 4.0;                                       // 4 |dr|
+}
+template <int R>
+__device__ __forceinline__ void half_slope_jac(double dl, double dr, double& gl, double& gr) {
+  gl = gr = 0.0;
+  if (!same_sign(dl, dr)) return;
+  const bool left_min = dbits(vabs(dl)) <= dbits(vabs(dr));
+  if (R == REC_PLM_MINMOD) {
+    (left_min ? gl : gr) = 0.5;
+    return;
+  }
+  const double m = left_min ? vabs(dl) : vabs(dr);
+  if (dbits(m) <= dbits(0.25 * vabs(dl + dr))) (left_min ? gl : gr) = 1.0;
+  else { gl = 0.25; gr = 0.25; }
+}
+template <int R>
+__device__ __forceinline__ void recon_jac(const double* q, double* JL, double* JR) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) JL[k] = JR[k] = 0.0;
+  if (R == REC_PC) {
+    JL[2] = JR[2] = 1.0;
+  } else if (R == REC_PLM_MC || R == REC_PLM_MINMOD) {
+    double gl, gr;  // h = gl (q2 - q1) + gr (q3 - q2); aL = q2 - h, aR = q2 + h
+    half_slope_jac<R>(q[2] - q[1], q[3] - q[2], gl, gr);
+    const double h1 = -gl, h2 = gl - gr, h3 = gr;
+    JL[1] = -h1; JL[2] = 1.0 - h2; JL[3] = -h3;
+    JR[1] = h1;  JR[2] = 1.0 + h2; JR[3] = h3;
+  } else {
+    const double e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3];
+    double a0, b0, a1, b1, a2, b2;  // d_k = a_k e_k + b_k e_(k+1)
+    vl_slope2_jac(e0, e1, a0, b0);
+    vl_slope2_jac(e1, e2, a1, b1);
+    vl_slope2_jac(e2, e3, a2, b2);
+    // coefficient rows of d0, d1, d2 in q (e_k = q_(k+1) - q_k)
+    double D0[5] = {-a0, a0 - b0, b0, 0.0, 0.0};
+    double D1[5] = {0.0, -a1, a1 - b1, b1, 0.0};
+    double D2[5] = {0.0, 0.0, -a2, a2 - b2, b2};
+    // aL = q1 + e1/2 - (d1 - d0)/12, aR = q2 + e2/2 - (d2 - d1)/12
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      JL[k] = -(D1[k] - D0[k]) * (1.0 / 12.0);
+      JR[k] = -(D2[k] - D1[k]) * (1.0 / 12.0);
+    }
+    JL[1] += 0.5; JL[2] += 0.5;
+    JR[2] += 0.5; JR[3] += 0.5;
+    // monotonicity (ppm_mono on the values)
+    const double d0 = vl_slope2(e0, e1), d1 = vl_slope2(e1, e2), d2 = vl_slope2(e2, e3);
+    const double aL = ppm_iface(q[1], e1, d0, d1), aR = ppm_iface(q[2], e2, d1, d2);
+    const double s1 = aR - q[2], s2 = q[2] - aL;
+    if (!same_sign(s1, s2)) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) JL[k] = JR[k] = 0.0;
+      JL[2] = JR[2] = 1.0;
+    } else if (same_sign(fma(-2.0, s1, s2), s1)) {  // aL = 3 a - 2 aR
+#pragma unroll
+      for (int k = 0; k < 5; ++k) JL[k] = -2.0 * JR[k];
+      JL[2] += 3.0;
+    } else if (same_sign(fma(2.0, s2, -s1), -s1)) {  // aR = 3 a - 2 aL
+#pragma unroll
+      for (int k = 0; k < 5; ++k) JR[k] = -2.0 * JL[k];
+      JR[2] += 3.0;
+    }
+  }
+}
+
+// adjoint of the reconstruction of `arr` along dir at point X: lam_lo / lam_hi are the adjoints of
+// its lower / upper values; the contributions go to the window's points (atomics: every point
+// gets them from the five windows it lies in, and more than once on lines shorter than five)
 template <int RC>
-__device__ __forceinline__ void rec_pt(const Dev& D, const double* arr, long long m, int dir, long long Y,
-                                       Dual& aL, Dual& aR) {
-  Dual q[5];
+__device__ __forceinline__ void rec_scatter(const Dev& D, const double* arr, long long X, int dir, double lam_lo,
+                                            double lam_hi, double* out) {
+  if (lam_lo == 0.0 && lam_hi == 0.0) return;
+  long long Z[5];
+  double q[5], JL[5], JR[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    const long long Z = shift2(D, m, dir, k - 2);
-    q[k] = Dual(arr[Z], Z == Y ? 1.0 : 0.0);
+    Z[k] = shift2(D, X, dir, k - 2);
+    q[k] = arr[Z[k]];
   }
-  recon_point<RC>(q, aL, aR);
+  recon_jac<RC>(q, JL, JR);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const double c = fma(JL[k], lam_lo, JR[k] * lam_hi);
+    if (c != 0.0) atomicAdd(&out[Z[k]], c);
+  }
 }
 template <int RC>
 __device__ __forceinline__ void rec_val(const Dev& D, const double* arr, long long m, int dir, double& aL,
@@ -49,15 +140,66 @@ __device__ __forceinline__ void rec_val(const Dev& D, const double* arr, long lo
   recon_point<RC>(q, aL, aR);
 }
 
+// Reverse sweep of q26_edge_emf (the Q26 corner EMFs of Eq. q26 and the LD04 average of Eq. ld04):
+// g[k] = lam dE/d in[k] for in = (baB, baT, uaB, uaT, bcL, bcR, ucL, ucR, apa, ama, apc, amc).
+__device__ __forceinline__ void q26_edge_vjp(const double* in, double lam, double* g) {
+  const double baB = in[0], baT = in[1], uaB = in[2], uaT = in[3], bcL = in[4], bcR = in[5], ucL = in[6],
+               ucR = in[7], apa = in[8], ama = in[9], apc = in[10], amc = in[11];
+  const double eLB = fma(-uaB, bcL, ucL * baB), eRB = fma(-uaB, bcR, ucR * baB);
+  const double eLT = fma(-uaT, bcL, ucL * baT), eRT = fma(-uaT, bcR, ucR * baT);
+  const double sa = apa + ama, sc = apc + amc;
+  const double w = rcp(sa * sc);
+  const double ia = sc * w, ic = sa * w;
+  const double hB = fma(apa, eLB, ama * eRB), hT = fma(apa, eLT, ama * eRT);
+  const double P = fma(apc, hB, amc * hT);
+  const double D1 = bcR - bcL, D2 = baT - baB;
+  // E = apa ama ia D1 - apc amc ic D2 + P w
+  const double dP = lam * w;
+  double dw = lam * P;
+  double dapc = dP * hB, damc = dP * hT;
+  const double dhB = dP * apc, dhT = dP * amc;
+  double dapa = dhB * eLB + dhT * eLT, dama = dhB * eRB + dhT * eRT;
+  const double deLB = dhB * apa, deRB = dhB * ama, deLT = dhT * apa, deRT = dhT * ama;
+  const double g1 = apa * ama * ia, g2 = apc * amc * ic;
+  dapa += lam * ama * ia * D1;
+  dama += lam * apa * ia * D1;
+  const double dia = lam * apa * ama * D1;
+  dapc -= lam * amc * ic * D2;
+  damc -= lam * apc * ic * D2;
+  const double dic = -lam * apc * amc * D2;
+  // ia = sc w, ic = sa w, w = 1 / (sa sc)
+  double dsc = dia * w, dsa = dic * w;
+  dw += dia * sc + dic * sa;
+  const double dprod = -dw * w * w;
+  dsa += dprod * sc;
+  dsc += dprod * sa;
+  dapa += dsa;
+  dama += dsa;
+  dapc += dsc;
+  damc += dsc;
+  // corners e = -u_a b_c + u_c b_a
+  g[0] = lam * g2 + deLB * ucL + deRB * ucR;          // baB
+  g[1] = -lam * g2 + deLT * ucL + deRT * ucR;         // baT
+  g[2] = -(deLB * bcL + deRB * bcR);                  // uaB
+  g[3] = -(deLT * bcL + deRT * bcR);                  // uaT
+  g[4] = -lam * g1 - deLB * uaB - deLT * uaT;         // bcL
+  g[5] = lam * g1 - deRB * uaB - deRT * uaT;          // bcR
+  g[6] = deLB * baB + deLT * baT;                     // ucL
+  g[7] = deRB * baB + deRT * baT;                     // ucR
+  g[8] = dapa;
+  g[9] = dama;
+  g[10] = dapc;
+  g[11] = damc;
+}
+
 // ---- edges: adjoint of E_e from the 8 reconstructed edge values, the edge speeds, eta j ----
 template <int RC>
 __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
   const Dev& D = A.D;
   const long long X = aid();
-  if (X >= D.N) return;
   const long long N = D.N;
   double etaacc = 0.0;
-  for (int e = 0; e < 3; ++e) {
+  for (int e = 0; e < 3 && X < N; ++e) {  // no early return: the whole warp sums d/d(eta) below
     const int a = (e + 1) % 3, c = (e + 2) % 3;
     const double lam = A.lE[e * N + X];
     if (lam == 0.0) {
@@ -86,14 +228,7 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
     in[10] = wc_p ? Apc[Xa] : Apc[X];
     in[11] = wc_m ? Amc[Xa] : Amc[X];
     double g[12];
-#pragma unroll 1
-    for (int i = 0; i < 12; ++i) {
-      Dual v[12];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = Dual(in[k], k == i ? 1.0 : 0.0);
-      const Dual E = q26_edge_emf(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11]);
-      g[i] = lam * E.t;
-    }
+    q26_edge_vjp(in, lam, g);
     for (int k = 0; k < 8; ++k) A.lEdge[(8LL * e + k) * N + X] = g[k];
     atomicAdd(&A.lAp[a * N + (wa_p ? Xc : X)], g[8]);
     atomicAdd(&A.lAm[a * N + (wa_m ? Xc : X)], g[9]);
@@ -111,7 +246,7 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
       atomicAdd(&A.lB[a * N + Xc], lc);
     }
   }
-  if (etaacc != 0.0) atomicAdd(A.lEta, etaacc);
+  warp_add(etaacc, A.lEta);
 }
 
 // ---- edge reconstructions: adjoint of the face arrays b_d and u_d* ------------------------
@@ -119,41 +254,24 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
 // e = d + 2 (bottom/top slots 0/1 for b, 2/3 for u*), and along t2 = d + 2 as the "c" array of
 // e-edges with e = d + 1 (left/right slots 4/5 for b, 6/7 for u*). Point m's lower value is the
 // top/right value at edge m; its upper value is the bottom/left value at edge m + t.
-// sum over the points m whose window holds Y of d(lower_m)/dY lam_lo[m] + d(upper_m)/dY lam_hi[m+1]
-template <int RC>
-__device__ __forceinline__ double gather_rec(const Dev& D, const double* arr, long long Y, int t,
-                                             const double* lam_lo, const double* lam_hi) {
-  double acc = 0.0;
-  const int nt = D.n[t];
-  const int k0 = nt >= 5 ? -2 : 0, k1 = nt >= 5 ? 2 : nt - 1;  // each distinct point once
-#pragma unroll 1
-  for (int k = k0; k <= k1; ++k) {
-    const long long m = shift2(D, Y, t, k);
-    Dual aL, aR;
-    rec_pt<RC>(D, arr, m, t, Y, aL, aR);
-    acc = fma(aL.t, lam_lo[m], acc);
-    acc = fma(aR.t, lam_hi[shift(D, m, t, 1)], acc);
-  }
-  return acc;
-}
-
 template <int RC>
 __global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
   const Dev& D = A.D;
-  const long long Y = aid();
-  if (Y >= D.N) return;
+  const long long X = aid();
+  if (X >= D.N) return;
   const long long N = D.N;
   for (int d = 0; d < 3; ++d) {
     const int t1 = (d + 1) % 3, e1 = (d + 2) % 3;  // d is "a" of e1, reconstructed along c(e1) = t1
     const int t2 = (d + 2) % 3, e2 = (d + 1) % 3;  // d is "c" of e2, reconstructed along a(e2) = t2
     const double* L1 = A.lEdge + 8LL * e1 * N;
     const double* L2 = A.lEdge + 8LL * e2 * N;
-    double lb = gather_rec<RC>(D, D.Bin[d], Y, t1, L1 + 1 * N, L1 + 0 * N);
-    lb += gather_rec<RC>(D, D.Bin[d], Y, t2, L2 + 5 * N, L2 + 4 * N);
-    double lu = gather_rec<RC>(D, D.Us + d * N, Y, t1, L1 + 3 * N, L1 + 2 * N);
-    lu += gather_rec<RC>(D, D.Us + d * N, Y, t2, L2 + 7 * N, L2 + 6 * N);
-    atomicAdd(&A.lB[d * N + Y], lb);
-    A.lUs[d * N + Y] = lu;
+    const long long X1 = shift(D, X, t1, 1), X2 = shift(D, X, t2, 1);
+    // point X's lower value is the top (right) value at edge X, its upper value the bottom (left)
+    // value at edge X + t
+    rec_scatter<RC>(D, D.Bin[d], X, t1, L1[1 * N + X], L1[0 * N + X1], A.lB + d * N);
+    rec_scatter<RC>(D, D.Bin[d], X, t2, L2[5 * N + X], L2[4 * N + X2], A.lB + d * N);
+    rec_scatter<RC>(D, D.Us + d * N, X, t1, L1[3 * N + X], L1[2 * N + X1], A.lUs + d * N);
+    rec_scatter<RC>(D, D.Us + d * N, X, t2, L2[7 * N + X], L2[6 * N + X2], A.lUs + d * N);
   }
 }
 
@@ -299,13 +417,10 @@ void launch_vjp_check(long long n, unsigned long long seed, double gam, int rs, 
 }
 
 // ---- Joule flux eta (j x b)_d (bilinear; by hand) ----------------------------------------
-__global__ void __launch_bounds__(128) k_adj_joule(AdjDev A, int d) {
+// the Joule flux's adjoint on the d-face of X (weight lam): scatters into lB, returns d/d(eta)
+__device__ __forceinline__ double joule_adj(const AdjDev& A, int d, long long X, double lam) {
   const Dev& D = A.D;
-  const long long X = aid();
-  if (X >= D.N || !D.resistive) return;
   const long long N = D.N;
-  const double lam = A.lF[(5LL * d + 4) * N + X];
-  if (lam == 0.0) return;
   const int a = (d + 1) % 3, c = (d + 2) % 3;
   const double* Ba = D.Bin[a];
   const double* Bc = D.Bin[c];
@@ -328,7 +443,7 @@ __global__ void __launch_bounds__(128) k_adj_joule(AdjDev A, int d) {
   const double bcbar = 0.25 * (Bc[Xmd] + Bc[X] + Bc[Xmdc] + Bc[Xc]);
   const double babar = 0.25 * (Ba[Xmd] + Ba[X] + Ba[Xmda] + Ba[Xa]);
   // flux = eta (ja bcbar - jc babar)
-  atomicAdd(A.lEta, lam * (ja * bcbar - jc * babar));
+  const double deta = lam * (ja * bcbar - jc * babar);
   const double wja = 0.5 * D.eta * lam * bcbar, wjc = -0.5 * D.eta * lam * babar;
   jadj(a, X, wja);
   jadj(a, Xc, wja);
@@ -343,24 +458,36 @@ __global__ void __launch_bounds__(128) k_adj_joule(AdjDev A, int d) {
   atomicAdd(&A.lB[a * N + X], wba);
   atomicAdd(&A.lB[a * N + Xmda], wba);
   atomicAdd(&A.lB[a * N + Xa], wba);
+  return deta;
 }
 
+
+__global__ void __launch_bounds__(128) k_adj_joule(AdjDev A, int d) {
+  const Dev& D = A.D;
+  if (!D.resistive) return;
+  const long long X = aid();
+  const long long N = D.N;
+  const double lam = X < N ? A.lF[(5LL * d + 4) * N + X] : 0.0;
+  double deta = 0.0;
+  if (lam != 0.0) deta = joule_adj(A, d, X, lam);
+  warp_add(deta, A.lEta);
+}
 // ---- face reconstructions: adjoint of the primitives --------------------------------------
 template <int RC>
 __global__ void __launch_bounds__(128) k_adj_face_rec(AdjDev A) {
   const Dev& D = A.D;
-  const long long q = aid();
-  if (q >= D.N) return;
+  const long long X = aid();
+  if (X >= D.N) return;
   const long long N = D.N;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int dir = 0; dir < 3; ++dir) {
     const int a = (dir + 1) % 3, c = (dir + 2) % 3;
     const int slot[7] = {0, 1 + dir, 1 + a, 1 + c, 4, 5 + a, 5 + c};
     const double* lLR = A.lLR + 14LL * dir * N;
-    for (int v = 0; v < 7; ++v)  // point m's lower value = right state of face m, upper = left of face m+1
-      acc[slot[v]] += gather_rec<RC>(D, D.P + slot[v] * N, q, dir, lLR + (7 + v) * N, lLR + v * N);
+    const long long Xn = shift(D, X, dir, 1);
+    // point X's lower value = right state of face X, upper value = left state of face X + dir
+    for (int v = 0; v < 7; ++v)
+      rec_scatter<RC>(D, D.P + slot[v] * N, X, dir, lLR[(7 + v) * N + X], lLR[v * N + Xn], A.lP + slot[v] * N);
   }
-  for (int v = 0; v < 8; ++v) A.lP[v * N + q] = acc[v];
 }
 
 // ---- primitives: adjoint of cons -> prim ------------------------------------------------

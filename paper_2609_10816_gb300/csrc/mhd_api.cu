@@ -392,8 +392,8 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   const long long N = ctx->base.N;
   cudaStream_t st = ctx->stream;
   // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
-  // lB0 3, lam2 8 (doubles per cell) + eta accumulator
-  const size_t nd = 125;
+  // lB0 3, lam2 8, and the stage-1 input's P 8 and alpha+- / u* 9 (doubles per cell) + eta
+  const size_t nd = 142;
   if (!ctx->adj) {
     s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + 8) * sizeof(double)), "cudaMalloc of adjoint scratch");
     if (s != MHD_OK) { ctx->adj = nullptr; return s; }
@@ -414,6 +414,8 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* lB0 = take(3);
   double* lamU = take(5);
   double* lamB = take(3);
+  double* P0 = take(8);
+  double* Apm0 = take(9);
   double* lEta = q;
 
   mhd::Dev D = ctx->base;
@@ -438,10 +440,16 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   if (e == cudaSuccess) e = cudaMemsetAsync(lEta, 0, sizeof(double), st);
   if ((s = cuda_check(ctx, e, "adjoint set-up")) != MHD_OK) return s;
 
-  // forward stage 1 again: S^{n+1/2} into the context's stage scratch
+  // forward stage 1 again: S^{n+1/2} into the context's stage scratch; its input's primitives,
+  // alpha+- and u* go to buffers of their own, where the stage-1 adjoint reads them
   D.Uin = D.U0;
   for (int d = 0; d < 3; ++d) D.Bin[d] = D.B0[d];
-  run_stage(ctx, D, sc);
+  mhd::Dev D0 = D;
+  D0.P = P0;
+  D0.Ap = Apm0;
+  D0.Am = Apm0 + 3 * N;
+  D0.Us = Apm0 + 6 * N;
+  run_stage(ctx, D0, sc);
 
   auto adj_dev = [&](const mhd::Dev& Ds, double* lU, double* lB) {
     mhd::AdjDev A;
@@ -464,18 +472,18 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
   e = zero(lU1, 5);
   if (e == cudaSuccess) e = zero(lB1, 3);
-  if (e == cudaSuccess) e = zero(lAp, 6);
+  if (e == cudaSuccess) e = zero(lAp, 9);  // alpha+-, u* (accumulated)
+  if (e == cudaSuccess) e = zero(lP, 8);   // primitives (accumulated)
   if ((s = cuda_check(ctx, e, "cudaMemsetAsync")) != MHD_OK) return s;
   mhd::launch_adj_flux(adj_dev(D1, lU1, lB1), sc.recon, sc.rs, st);
 
   // stage 1 flux function at S^n: (D^T lam) / 2 + D^T lam_{n+1/2}
   mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
   mhd::launch_adj_update(D, lU1, lB1, lF, lE, 1.0, 1.0, st);
-  mhd::Dev D0 = D;
-  recompute(D0);
   e = zero(lU0, 5);
   if (e == cudaSuccess) e = zero(lB0, 3);
-  if (e == cudaSuccess) e = zero(lAp, 6);
+  if (e == cudaSuccess) e = zero(lAp, 9);  // alpha+-, u* (accumulated)
+  if (e == cudaSuccess) e = zero(lP, 8);   // primitives (accumulated)
   if ((s = cuda_check(ctx, e, "cudaMemsetAsync")) != MHD_OK) return s;
   mhd::launch_adj_flux(adj_dev(D0, lU0, lB0), sc.recon, sc.rs, st);
 

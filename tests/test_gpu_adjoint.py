@@ -17,8 +17,8 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("recon,rs", [("ppm", "hlld"), ("plm_mc", "hll"), ("plm_minmod", "llf"), ("pc", "hlld")])
 @pytest.mark.parametrize("eta", [0.0, 3e-3])
-def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta):
-    shape = (10, 8, 6)
+@pytest.mark.parametrize("shape", [(10, 8, 6), (7, 4, 2)])  # the second: windows wrap onto themselves
+def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta, shape):
     cons, b, info = inputs.random_smooth(shape, seed=21, rough=0.02)
     cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf="q26", eta=eta)
     dt = oracle.max_dt(cfg, cons, b, 0.3)
