@@ -223,10 +223,10 @@ mhd_status mhd_batch_stats(mhd_batch *batch, long long *fofc_cells_stage1, long 
 
 /* Device time of the phases of the last step's two stage launches (synchronous), as measured by
  * block 0 of the persistent kernel with the GPU global timer at each grid barrier it passes:
- * ms[7 * stage + j] for j = 0 cons->prim, 1 face sweeps (reconstruction + Riemann), 2 a-face
- * quantities to edges, 3 c-face quantities to edges + LD04 EMFs, 4 increments and update,
- * 5 validity flags, 6 first-order fluxes of flagged cells (0 when the phase did not run: no
- * flagged cell, or flux correction off). `ms` holds 14 doubles, written by this call. */
+ * ms[6 * stage + j] for j = 0 cons->prim, 1 face sweeps (reconstruction + Riemann), 2 a-face
+ * quantities to edges, 3 c-face quantities to edges + LD04 EMFs, 4 increments, update and
+ * validity flags, 5 first-order fluxes of flagged cells (0 when the phase did not run: no
+ * flagged cell, or flux correction off). `ms` holds 12 doubles, written by this call. */
 mhd_status mhd_batch_phase_ms(mhd_batch *batch, double *ms);
 
 /* Schedule of the persistent stage kernel: sweep segment length seg (points per thread), patch

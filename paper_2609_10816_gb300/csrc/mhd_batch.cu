@@ -126,6 +126,9 @@ __device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long lon
   });
 }
 
+// cells per thread per pass of the per-cell phases
+constexpr int kCellIlp = 4;
+
 template <int RC, int RS>
 __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -136,11 +139,27 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   // the sweep phases' cursors start at zero; no block takes work from them before the first
   // grid barrier, which block 0 passes only after this
   if (blockIdx.x == 0 && threadIdx.x < 3) atomicExch(B.cursor + threadIdx.x, 0ull);
-  // cons -> prim
-  for (long long i = t0, k = k0; i < ncell; i += nth) {
-    k = advance_pos(B.cell_pref, (int)k, i);
-    const Dev& D = B.patches[B.order[k]];
-    prim_cell(D, i - B.cell_pref[k]);
+  // cons -> prim; the per-cell phases take kCellIlp cells per thread at a time, loads of all of
+  // them before any store (the persistent grid has few warps per SM to hide memory latency)
+  for (long long i0 = t0, k = k0; i0 < ncell; i0 += kCellIlp * nth) {
+    double w[kCellIlp][8];
+    const Dev* Dp[kCellIlp];
+    long long X[kCellIlp];
+#pragma unroll
+    for (int g = 0; g < kCellIlp; ++g) {
+      const long long i = i0 + g * nth;
+      Dp[g] = nullptr;
+      if (i < ncell) {
+        k = advance_pos(B.cell_pref, (int)k, i);
+        Dp[g] = &B.patches[B.order[k]];
+        X[g] = i - B.cell_pref[k];
+        prim_of(*Dp[g], Dp[g]->Uin, Dp[g]->Bin, X[g], w[g]);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kCellIlp; ++g)
+      if (Dp[g])
+        for (int v = 0; v < 8; ++v) Dp[g]->P[v * Dp[g]->N + X[g]] = w[g][v];
   }
   if (!grid_sync(B)) return;
   stamp(B, 1);
@@ -171,28 +190,39 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   }
   if (!grid_sync(B)) return;
   stamp(B, 4);
-  // update
-  for (long long i = t0, k = k0; i < ncell; i += nth) {
-    k = advance_pos(B.cell_pref, (int)k, i);
-    update_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
-  }
-  if (!grid_sync(B)) return;
-  stamp(B, 5);
-  // validity flags (every lane of a warp runs the same number of iterations for the ballot)
+  // update and validity flags (every lane of a warp runs the same number of passes for the ballot)
   int kf = k0;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += nth) {
-    const long long i = base + threadIdx.x;
-    bool f = false;
-    if (i < ncell) {
-      kf = advance_pos(B.cell_pref, kf, i);
-      f = flag_cell(B.patches[B.order[kf]], i - B.cell_pref[kf]);
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kCellIlp * nth) {
+    double w[kCellIlp][8];
+    bool f[kCellIlp];
+    const Dev* Dp[kCellIlp];
+    long long X[kCellIlp];
+#pragma unroll
+    for (int g = 0; g < kCellIlp; ++g) {
+      const long long i = base + g * nth + threadIdx.x;
+      f[g] = false;
+      Dp[g] = nullptr;
+      if (i < ncell) {
+        kf = advance_pos(B.cell_pref, kf, i);
+        Dp[g] = &B.patches[B.order[kf]];
+        X[g] = i - B.cell_pref[kf];
+        f[g] = update_flag_vals(*Dp[g], X[g], w[g]);
+      }
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&B.counters[B.stage], (unsigned long long)__popc(bal));
+    unsigned cnt = 0;
+#pragma unroll
+    for (int g = 0; g < kCellIlp; ++g) {
+      if (Dp[g]) {
+        store_update(*Dp[g], X[g], w[g]);
+        Dp[g]->flag[X[g]] = f[g] ? 1 : 0;
+      }
+      cnt += __popc(__ballot_sync(0xffffffffu, f[g]));
+    }
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&B.counters[B.stage], (unsigned long long)cnt);
   }
   if (!B.fofc) return;
   if (!grid_sync(B)) return;
-  stamp(B, 6);
+  stamp(B, 5);
   if (*(volatile unsigned long long*)(B.counters + B.stage) == 0) return;  // uniform over the grid
   for (long long i = t0, k = k0; i < ncell; i += nth) {
     k = advance_pos(B.cell_pref, (int)k, i);
@@ -201,7 +231,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
     fo_edges_cell(D, i - B.cell_pref[k]);
   }
   if (!grid_sync(B)) return;
-  stamp(B, 7);
+  stamp(B, 6);
   for (long long i = t0, k = k0; i < ncell; i += nth) {
     k = advance_pos(B.cell_pref, (int)k, i);
     fo_recompute_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
@@ -520,8 +550,8 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->off.assign(npatch + 1, 0);
   for (int p = 0; p < npatch; ++p) {
     const int* n = &dims[3 * p];
-    if (n[0] < 1 || n[1] < 1 || n[2] < 1) {
-      g_batch_create_err = "every patch needs n >= 1 cells per direction";
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1 || (long long)n[0] * n[1] * n[2] > (1LL << 31) - 1) {
+      g_batch_create_err = "every patch needs n >= 1 cells per direction and fewer than 2^31 cells";
       delete b;
       return MHD_ERR_ARG;
     }
@@ -718,9 +748,9 @@ mhd_status mhd_batch_phase_ms(mhd_batch* b, double* ms) {
   mhd_status s = bcuda(b, e, "read phase stamps");
   if (s != MHD_OK) return s;
   for (int st = 0; st < 2; ++st)
-    for (int j = 0; j < 7; ++j) {
+    for (int j = 0; j < 6; ++j) {
       const unsigned long long a = t[8 * st + j], z = t[8 * st + j + 1];
-      ms[7 * st + j] = (a && z && z >= a) ? (double)(z - a) * 1e-6 : 0.0;
+      ms[6 * st + j] = (a && z && z >= a) ? (double)(z - a) * 1e-6 : 0.0;
     }
   return MHD_OK;
 }

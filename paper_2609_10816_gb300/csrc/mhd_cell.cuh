@@ -86,40 +86,93 @@ __device__ __forceinline__ double incr_face(const Dev& D, int d, long long X, co
   return D.dt * fma(Ec[X] - Ec[Xp[a]], D.hinv[a], (Ea[Xp[c]] - Ea[X]) * D.hinv[c]);
 }
 
-__device__ __forceinline__ void update_cell(const Dev& D, long long X) {
+// the updated field on the d-face of cell X (its lower face); Xp[a], Xp[c] = X + 1 along a, c
+__device__ __forceinline__ double face_new(const Dev& D, int d, long long X, const long long* Xp) {
+  return D.B0[d][X] + incr_face(D, d, X, Xp);
+}
+// the updated state of cell X (5 conserved values, then its 3 lower faces), not yet stored
+__device__ __forceinline__ void update_vals(const Dev& D, long long X, const long long* Xp, double* out) {
   const long long N = D.N;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v] = D.U0[v * N + X] + incr_cell(D, v, X, Xp);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) out[5 + d] = face_new(D, d, X, Xp);
+}
+__device__ __forceinline__ void update_vals(const Dev& D, long long X, double* out) {
   const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
+  update_vals(D, X, Xp, out);
+}
+// the updated field on the upper d-face of cell X (the lower d-face of X + 1 along d), computed as
+// the neighbour computes it, so that a cell's validity can be tested where it is updated
+__device__ __forceinline__ double upper_face_new(const Dev& D, int d, long long Xd) {
+  long long Yp[3];
+  Yp[d] = Xd;  // not used by face_new
+  Yp[(d + 1) % 3] = shift(D, Xd, (d + 1) % 3, 1);
+  Yp[(d + 2) % 3] = shift(D, Xd, (d + 2) % 3, 1);
+  return face_new(D, d, Xd, Yp);
+}
+__device__ __forceinline__ void store_update(const Dev& D, long long X, const double* out) {
+  const long long N = D.N;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) D.Uout[v * N + X] = D.U0[v * N + X] + incr_cell(D, v, X, Xp);
+  for (int v = 0; v < 5; ++v) D.Uout[v * N + X] = out[v];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) D.Bout[d][X] = D.B0[d][X] + incr_face(D, d, X, Xp);
+  for (int d = 0; d < 3; ++d) D.Bout[d][X] = out[5 + d];
+}
+__device__ __forceinline__ void update_cell(const Dev& D, long long X) {
+  double out[8];
+  update_vals(D, X, out);
+  store_update(D, X, out);
 }
 
 // ---- validity flags (Sec. 2.5) --------------------------------------------------------------
-__device__ __forceinline__ bool invalid_cell(const Dev& D, const double* U, double* const* B, long long X) {
-  const long long N = D.N;
+// u: the cell's 5 conserved values; lo / hi: its lower / upper face fields
+__device__ __forceinline__ bool invalid_vals(const Dev& D, const double* u, const double* lo, const double* hi) {
   bool fin = true;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) fin = fin && finite_d(U[v * N + X]);
+  for (int v = 0; v < 5; ++v) fin = fin && finite_d(u[v]);
   double bc[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double lo = B[d][X], hi = B[d][shift(D, X, d, 1)];
-    fin = fin && finite_d(lo) && finite_d(hi);
-    bc[d] = 0.5 * (lo + hi);
+    fin = fin && finite_d(lo[d]) && finite_d(hi[d]);
+    bc[d] = 0.5 * (lo[d] + hi[d]);
   }
   if (!fin) return true;
-  const double rho = U[X];
+  const double rho = u[0];
   if ((D.fofc_criteria & 1) && le0(rho)) return true;
   if (D.fofc_criteria & 2) {
     const double rinv = rcp(rho);
-    const double u0 = U[N + X] * rinv, u1 = U[2 * N + X] * rinv, u2 = U[3 * N + X] * rinv;
+    const double u0 = u[1] * rinv, u1 = u[2] * rinv, u2 = u[3] * rinv;
     const double u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double b2s = fma(bc[0], bc[0], fma(bc[1], bc[1], bc[2] * bc[2]));
-    const double p = (D.gam - 1.0) * (U[4 * N + X] - 0.5 * fma(rho, u2s, b2s));
+    const double p = (D.gam - 1.0) * (u[4] - 0.5 * fma(rho, u2s, b2s));
     if (!gt0(p)) return true;  // p <= 0 or NaN
   }
   return false;
+}
+__device__ __forceinline__ bool invalid_cell(const Dev& D, const double* U, double* const* B, long long X) {
+  const long long N = D.N;
+  double u[5], lo[3], hi[3];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = U[v * N + X];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = B[d][X];
+    hi[d] = B[d][shift(D, X, d, 1)];
+  }
+  return invalid_vals(D, u, lo, hi);
+}
+
+// update of cell X with its validity flag: the upper faces are recomputed here (as the
+// neighbours compute them) instead of read back, so no separate pass over the new state is needed
+// (the batched stage's fused phase; on a single box two passes are faster: the recomputed faces'
+// EMFs of the next plane come from L2, while the flag pass streams the new state)
+__device__ __forceinline__ bool update_flag_vals(const Dev& D, long long X, double* out) {
+  const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
+  update_vals(D, X, Xp, out);
+  double hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) hi[d] = upper_face_new(D, d, Xp[d]);
+  return invalid_vals(D, out, out + 5, hi);
 }
 
 // flag of cell X (written) and whether it is set

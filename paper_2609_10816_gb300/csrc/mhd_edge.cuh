@@ -67,13 +67,25 @@ __device__ __forceinline__ void edge_bt_seg(const Dev& D, int e, const Line& ln,
     for (int t = 0; t < LB + LA; ++t) w[t] = q[v][ln.at(m0 - LB + t)];
     r[v].init(w);
   }
+  // the next point's values are loaded one iteration ahead (this sweep does little arithmetic per
+  // point, so the loads' latency would otherwise stall it)
+  double nxt[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) nxt[v] = q[v][ln.at(m0 + LA)];
   for (int m = m0; m < m1; ++m) {
     const long long X = ln.at(m);
-    const long long Xn = ln.at(m + LA);
+    double cur[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cur[v] = nxt[v];
+    if (m + 1 < m1) {
+      const long long Xn = ln.at(m + 1 + LA);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) nxt[v] = q[v][Xn];
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       double B, T;
-      r[v].step(q[v][Xn], B, T);
+      r[v].step(cur[v], B, T);
       out[2 * v][X] = B;
       out[2 * v + 1][X] = T;
     }

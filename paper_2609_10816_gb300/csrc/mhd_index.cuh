@@ -5,11 +5,12 @@
 
 namespace mhd {
 
-// linear index of X shifted by s (|s| < n[d]) cells along d, periodic
+// linear index of X shifted by s (|s| < n[d]) cells along d, periodic. A box holds fewer than
+// 2^31 cells (checked when it is created), so the index arithmetic is 32-bit.
 __device__ __forceinline__ long long shift(const Dev& D, long long X, int d, int s) {
   const unsigned st = (unsigned)D.stride[d];
   const int nd = D.n[d];
-  const int cd = (int)(((unsigned long long)X / st) % (unsigned)nd);
+  const int cd = (int)(((unsigned)X / st) % (unsigned)nd);
   int cn = cd + s;
   if (cn >= nd) cn -= nd;
   if (cn < 0) cn += nd;
@@ -20,7 +21,7 @@ __device__ __forceinline__ long long shift(const Dev& D, long long X, int d, int
 __device__ __forceinline__ long long shift2(const Dev& D, long long X, int d, int s) {
   const unsigned st = (unsigned)D.stride[d];
   const int nd = D.n[d];
-  const int cd = (int)(((unsigned long long)X / st) % (unsigned)nd);
+  const int cd = (int)(((unsigned)X / st) % (unsigned)nd);
   int cn = (cd + s) % nd;
   if (cn < 0) cn += nd;
   return X + (long long)(cn - cd) * (long long)st;

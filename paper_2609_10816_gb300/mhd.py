@@ -302,13 +302,13 @@ class Batch:
         self._err(lib().mhd_batch_stats(self._h, ctypes.byref(a), ctypes.byref(c)))
         return a.value, c.value
 
-    PHASES = ("prim", "face", "edge_bt", "edge_lr", "update", "flag", "fo_fluxes")
+    PHASES = ("prim", "face", "edge_bt", "edge_lr", "update_flag", "fo_fluxes")
 
     def phase_ms(self):
         """Device time of each phase of the last step's two stages, {stage: {phase: ms}}."""
-        out = (ctypes.c_double * 14)()
+        out = (ctypes.c_double * 12)()
         self._err(lib().mhd_batch_phase_ms(self._h, out))
-        return {s: {ph: out[7 * s + j] for j, ph in enumerate(self.PHASES)} for s in (0, 1)}
+        return {s: {ph: out[6 * s + j] for j, ph in enumerate(self.PHASES)} for s in (0, 1)}
 
     def set_schedule(self, seg=64, order=1, blocks_per_sm=0, use_graph=True):
         self._err(lib().mhd_batch_set_schedule(self._h, int(seg), int(order), int(blocks_per_sm), 1 if use_graph else 0))
