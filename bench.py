@@ -39,7 +39,7 @@ HBM_PEAK_GBS = 6759.6  # MEASURED_PEAKS.json copy bandwidth
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 688.0e6, "cells": 160**3, "src": "a42215e424c47769"}}
+TRAFFIC = {"face": {"bytes_per_launch": 687.9e6, "cells": 160**3, "src": "30bb96995d7b5da1"}}
 
 
 # what the face sweep's machine code is compiled from: its kernel, the numerics and indexing

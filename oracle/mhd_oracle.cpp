@@ -22,7 +22,7 @@
 //      the total energy e_tot is used (the system is not conservative otherwise).
 //   R2 PLM limiters (Sec. 2.2): MC slope = sgn * min(2|dl|, 2|dr|, |dl+dr|/2) and minmod,
 //      both zero unless dl and dr are strictly of the same sign.
-//   R3 PPM (Sec. 2.2, "similar to Colella & Woodward 1984"): CW84 Eqs. 1.6-1.8 interface
+//   R3 PPM (Sec. 2.2, close to Colella & Woodward 1984 in the paper's description): CW84 Eqs. 1.6-1.8 interface
 //      interpolation with van Leer limited slopes, then the CW84 Eq. 1.10 monotonicity
 //      constraints; no flattening, steepening or characteristic tracing (method of lines).
 //   R4 fast speed along d (Eq. waves:fast-speed) with cos^2(theta) = b_d^2 / b^2; the square
