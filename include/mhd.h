@@ -75,7 +75,9 @@ typedef struct mhd_ctx mhd_ctx; /* opaque: owns the scratch of one patch size an
 
 /* Create a context for one patch size. `cuda_stream` is a cudaStream_t (NULL = legacy default
  * stream); all work of the context is enqueued on it. Allocates the step's scratch
- * (about 60 doubles per cell) with cudaMalloc on the current device. *out is NULL on error. */
+ * (112 doubles and one byte per cell, the FS18 / B25a intermediates included) with cudaMalloc on
+ * the current device; the first mhd_step_adjoint adds 142 doubles per cell. *out is NULL on
+ * error. */
 mhd_status mhd_create(const mhd_config *cfg, void *cuda_stream, mhd_ctx **out);
 
 /* Free the context and its scratch (synchronises the stream first). NULL is ignored. */
@@ -132,7 +134,7 @@ mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches,
  * stage 1 is recomputed inside). The paper has no counterpart; it makes the step usable inside
  * gradient-based workflows. Covers the Q26 EMF compute and steps in which flux correction
  * flagged no cell (the caller checks mhd_stats of the forward step); the first call allocates
- * about 125 doubles per cell of adjoint scratch. Synchronous when dL_deta is not NULL. */
+ * 142 doubles per cell of adjoint scratch. Synchronous when dL_deta is not NULL. */
 mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_state *lam, double dt, int scheme,
                             double eta, double *dL_deta);
 
@@ -201,8 +203,9 @@ typedef struct {
   double *b;
 } mhd_batch_state;
 
-/* Create a batch of npatch patches (dims: 3 ints per patch, each >= 1) with cell width h > 0.
- * Allocates about 55 doubles of scratch per cell. Errors: message from mhd_batch_last_error(NULL). */
+/* Create a batch of npatch patches (dims: 3 ints per patch, each >= 1, fewer than 2^31 cells per
+ * patch) with cell width h > 0. Allocates 55 doubles and one byte of scratch per cell. Errors:
+ * message from mhd_batch_last_error(NULL). */
 mhd_status mhd_batch_create(const int *dims, int npatch, double h, double gamma, void *cuda_stream,
                             mhd_batch **out);
 void mhd_batch_destroy(mhd_batch *batch);

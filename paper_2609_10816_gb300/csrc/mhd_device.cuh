@@ -394,8 +394,11 @@ __device__ __forceinline__ void two_state(const PhysFluxT<T>& L, const PhysFluxT
 // Star state on one side of the contact (MK05 Eqs. 43-48).
 template <class T> struct StarT {
   T rs, vs, ws, bys, bzs, es;
+  T vbs;  // u* . b* of the star state (formed with es)
 };
-template <class T>
+// (ES = false: the energy es is not formed, and ph is not read -- the other side's star state in
+// the double-star region needs only rs, vs, ws, bys, bzs)
+template <class T, bool ES = true>
 __device__ __forceinline__ void star_state(const FaceStateT<T>& q, const PhysFluxT<T>& ph, T S, T SM,
                                            T ptS, T bn, T bn2, StarT<T>& o) {
   const T su = S - q.u;
@@ -419,9 +422,10 @@ __device__ __forceinline__ void star_state(const FaceStateT<T>& q, const PhysFlu
     o.bys = q.by * cb;
     o.bzs = q.bz * cb;
   }
+  if (!ES) return;
   const T vb = fma(q.u, bn, fma(q.v, q.by, q.w * q.bz));
-  const T vbs = fma(SM, bn, fma(o.vs, o.bys, o.ws * o.bzs));
-  o.es = (fma(su, ph.e, -ph.pt * q.u) + fma(ptS, SM, bn * (vb - vbs))) * ssminv;
+  o.vbs = fma(SM, bn, fma(o.vs, o.bys, o.ws * o.bzs));
+  o.es = (fma(su, ph.e, -ph.pt * q.u) + fma(ptS, SM, bn * (vb - o.vbs))) * ssminv;
 }
 
 template <class T>
@@ -482,14 +486,11 @@ __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T
     for (int v = 0; v < 5; ++v) F[v] = Fs[v];
     return;
   }
-  // inside the rotational wave of this side: the other side's star state and the double star
+  // inside the rotational wave of this side: the other side's star state (its density, velocity
+  // and field only) and the double star
   const FaceStateT<T> qo = pick(!left, sl, sr);
-  PhysFluxT<T> Po;
-  Po.b2 = left ? R.b2 : L.b2;
-  Po.pt = left ? R.pt : L.pt;
-  phys_flux(qo, bn, gm1inv, Po);
   StarT<T> b;
-  star_state(qo, Po, left ? SR : SL, SM, ptS, bn, bn2, b);
+  star_state<T, false>(qo, P, left ? SR : SL, SM, ptS, bn, bn2, b);
   const T isqb = rsqrt_(b.rs);
   const T rsL = left ? a.rs : b.rs, rsR = left ? b.rs : a.rs;
   const T vsL = left ? a.vs : b.vs, vsR = left ? b.vs : a.vs;
@@ -508,7 +509,7 @@ __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T
   const T vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
   const T sq = left ? sqL : sqR;
   const double sgn_side = left ? -1.0 : 1.0;
-  const T vbs = fma(SM, bn, fma(a.vs, a.bys, a.ws * a.bzs));
+  const T vbs = a.vbs;
   T Uss[5];
   Uss[0] = a.rs;
   Uss[1] = a.rs * SM;

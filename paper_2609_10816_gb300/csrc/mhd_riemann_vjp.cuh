@@ -247,13 +247,9 @@ __device__ __forceinline__ void hlld_rev(const FaceState& sl, const FaceState& s
   double dPe = 0.0, dPpt = 0.0;
   if (dstar) {
     const FaceState qo = pick(!left, sl, sr);
-    PhysFlux Po;
-    Po.b2 = left ? Rsp.b2 : Lsp.b2;
-    Po.pt = left ? Rsp.pt : Lsp.pt;
-    phys_flux(qo, bn, gm1inv, Po);
     const double So = left ? SR : SL;
     StarT<double> b;
-    star_state(qo, Po, So, SM, ptS, bn, bn2, b);
+    star_state<double, false>(qo, P, So, SM, ptS, bn, bn2, b);
     const double isqb = rsqrt_(b.rs);
     const StarT<double>& sL = left ? a : b;
     const StarT<double>& sR = left ? b : a;
@@ -364,14 +360,13 @@ __device__ __forceinline__ void hlld_rev(const FaceState& sl, const FaceState& s
     StarAdj db = dB_;
     db.es = 0.0;
     db.rs += diB * (-0.5 * isqb * isqb * isqb);
-    // b = star_state(qo, Po, So, SM, ptS, bn, bn2)
+    // b = star_state(qo, ., So, SM, ptS, bn, bn2) without its energy (db.es = 0, so neither the
+    // side's flux vectors nor its pt enter)
     FaceState dqo = {0, 0, 0, 0, 0, 0, 0};
     double dPoe = 0.0, dPopt = 0.0, dSo = 0.0;
-    star_state_rev(qo, Po, So, SM, ptS, bn, bn2, b, db, dqo, dPoe, dPopt, dSo, dSM, dptS, dbn, dbn2);
-    double dob2 = 0.0, dopt = dPopt;
-    phys_flux_rev(qo, bn, gm1inv, Po, zero5, zero5, dPoe, dqo, dbn, dob2, dopt);
+    star_state_rev(qo, P, So, SM, ptS, bn, bn2, b, db, dqo, dPoe, dPopt, dSo, dSM, dptS, dbn, dbn2);
     add_side(!left, dsl, dsr, dqo);
-    if (left) { dRb2 += dob2; dRpt += dopt; dSR += dSo; } else { dLb2 += dob2; dLpt += dopt; dSL += dSo; }
+    if (left) dSR += dSo; else dSL += dSo;
   }
   // Ss = SM -/+ |bn| isqa
   dSM += dSs;
