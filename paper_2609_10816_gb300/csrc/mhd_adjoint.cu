@@ -93,16 +93,16 @@ __device__ __forceinline__ void recon_jac(const double* q, double* JL, double* J
     // monotonicity (ppm_mono on the values)
     const double d0 = vl_slope2(e0, e1), d1 = vl_slope2(e1, e2), d2 = vl_slope2(e2, e3);
     const double aL = ppm_iface(q[1], e1, d0, d1), aR = ppm_iface(q[2], e2, d1, d2);
-    const double s1 = aR - q[2], s2 = q[2] - aL;
-    if (!same_sign(s1, s2)) {
+    const int mc = ppm_mono_case(aR - q[2], q[2] - aL);
+    if (mc == PPM_FLAT) {
 #pragma unroll
       for (int k = 0; k < 5; ++k) JL[k] = JR[k] = 0.0;
       JL[2] = JR[2] = 1.0;
-    } else if (same_sign(fma(-2.0, s1, s2), s1)) {  // aL = 3 a - 2 aR
+    } else if (mc == PPM_FIX_L) {  // aL = 3 a - 2 aR
 #pragma unroll
       for (int k = 0; k < 5; ++k) JL[k] = -2.0 * JR[k];
       JL[2] += 3.0;
-    } else if (same_sign(fma(2.0, s2, -s1), -s1)) {  // aR = 3 a - 2 aL
+    } else if (mc == PPM_FIX_R) {  // aR = 3 a - 2 aL
 #pragma unroll
       for (int k = 0; k < 5; ++k) JR[k] = -2.0 * JL[k];
       JR[2] += 3.0;

@@ -229,11 +229,17 @@ template <> struct Rec<REC_PLM_MINMOD> : RecPLM<REC_PLM_MINMOD> {};
 // -da^2 > da a6 <=> da (a6 + da) < 0 <=> 2 s2 - s1 has the opposite sign; the corrections are
 // 3a - 2aR = a - 2 s1 and 3a - 2aL = a + 2 s2.
 
-// 4 m for m >= 0 by adding 2 to the binary exponent (exact for normal m; zero stays zero)
-__device__ __forceinline__ double times4(double m) {
-  const long long b = dbits(m);
-  return b == 0 ? 0.0 : dfrom(b + (2LL << 52));
+// Bit pattern of 2|x| from the bit pattern b >= 0 of |x|, exactly and on the integer pipe: zero
+// and subnormals double by a shift of the mantissa (which carries into the exponent where the
+// result becomes normal), normals by one more in the exponent, and 2|x| >= 2^1024 (or a NaN)
+// gives infinity.
+__device__ __forceinline__ long long twice_bits(long long b) {
+  if (b < (1LL << 52)) return b << 1;
+  if (b >= (2046LL << 52)) return 0x7ff0000000000000LL;
+  return b + (1LL << 52);
 }
+// 4 m for m >= 0, exact (two doublings)
+__device__ __forceinline__ double times4(double m) { return dfrom(twice_bits(twice_bits(dbits(m)))); }
 __device__ __forceinline__ Dual times4(Dual m) { return Dual(times4(m.v), 4.0 * m.t); }
 
 template <class T>
@@ -247,20 +253,30 @@ template <class T>
 __device__ __forceinline__ T ppm_iface(T q0, T dq, T d20, T d21) {
   return fma(-(d21 - d20), T(1.0 / 12.0), fma(T(0.5), dq, q0));
 }
+// With s1, s2 of one sign, u = s2 - 2 s1 = (a6 - da)/2 has the sign of s1 exactly when
+// |s2| > 2|s1|, and v = 2 s2 - s1 = (a6 + da)/2 the sign of -s1 exactly when 2|s2| < |s1| (u and v
+// are single roundings of exact differences of doubles, so their signs are exact): the two tests
+// compare bit patterns, and the one correction that applies is a single FMA.
+enum { PPM_FLAT = 0, PPM_FIX_L = 1, PPM_FIX_R = 2, PPM_KEEP = 3 };
+// which constraint applies for s1 = aR - a, s2 = a - aL
+__device__ __forceinline__ int ppm_mono_case(double s1, double s2) {
+  if (!same_sign(s1, s2)) return PPM_FLAT;                        // a is an extremum
+  const long long m1 = dbits(s1) & 0x7fffffffffffffffLL, m2 = dbits(s2) & 0x7fffffffffffffffLL;
+  if (m2 > twice_bits(m1)) return PPM_FIX_L;                        // aL = 3a - 2aR = a - 2 s1
+  if (twice_bits(m2) < m1) return PPM_FIX_R;                        // aR = 3a - 2aL = a + 2 s2
+  return PPM_KEEP;
+}
 template <class T>
 __device__ __forceinline__ void ppm_mono(T a, T& aL, T& aR) {
   const T s1 = aR - a, s2 = a - aL;
-  if (!same_sign(s1, s2)) {
+  const int c = ppm_mono_case(val(s1), val(s2));
+  if (c == PPM_FLAT) {
     aL = a;
     aR = a;
-    return;
-  }
-  const T u = fma(T(-2.0), s1, s2);  // (a6 - da) / 2
-  const T v = fma(T(2.0), s2, -s1);  // (a6 + da) / 2
-  if (same_sign(u, s1)) {
-    aL = fma(T(-2.0), s1, a);
-  } else if (same_sign(v, -s1)) {
-    aR = fma(T(2.0), s2, a);
+  } else if (c != PPM_KEEP) {
+    const bool l = c == PPM_FIX_L;
+    const T r = fma(l ? -2.0 : 2.0, l ? s1 : s2, a);
+    if (l) aL = r; else aR = r;
   }
 }
 
@@ -337,7 +353,7 @@ using FaceState = FaceStateT<double>;
 
 template <class T> struct PhysFluxT {
   T U[5], F[5];
-  T pt, e, cf, b2;
+  T pt, e, cf2, b2;  // cf2: the square of the fast magnetosonic speed along the normal
 };
 using PhysFlux = PhysFluxT<double>;
 
@@ -354,7 +370,7 @@ __device__ __forceinline__ void phys_speed(const FaceStateT<T>& s, T bn, double 
   const T sum = fma(b2, rinv, a2);
   T disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
   disc = pmax(disc, T(0.0));
-  o.cf = sqrt_(0.5 * (sum + sqrt_(disc)));
+  o.cf2 = 0.5 * (sum + sqrt_(disc));
 }
 
 // Conserved vector and ideal-MHD flux of Eq. (mhd:conservation-laws) in the face frame, with e_tot
@@ -530,12 +546,12 @@ __device__ __forceinline__ void riemann(const FaceStateT<T>& sl, const FaceState
   phys_speed(sr, bn, gam, R);
   T SL = 0.0, SR = 0.0;
   if (RS == RS_LLF) {
-    const T a = pmax(vabs(sl.u) + L.cf, vabs(sr.u) + R.cf);
+    const T a = pmax(vabs(sl.u) + sqrt_(L.cf2), vabs(sr.u) + sqrt_(R.cf2));
     ap = a;
     am = a;
   } else {
     // Eq. (alpha-pm) = MK05 Eq. 67 speeds
-    const T cmax = pmax(L.cf, R.cf);
+    const T cmax = sqrt_(pmax(L.cf2, R.cf2));  // = max of the two speeds, one square root
     const T umax = vmax(sl.u, sr.u), umin = vmin(sl.u, sr.u);
     SR = umax + cmax;
     SL = umin - cmax;

@@ -14,9 +14,9 @@
 
 namespace mhd {
 
-// adjoint of phys_speed (b2, pt, cf of a state): accumulates into ds and dbn
+// adjoint of phys_speed (b2, pt, cf2 of a state): accumulates into ds and dbn
 __device__ __forceinline__ void phys_speed_rev(const FaceState& s, double bn, double gam, double db2, double dpt,
-                                               double dcf, FaceState& ds, double& dbn) {
+                                               double dcf2, FaceState& ds, double& dbn) {
   const double bn2 = bn * bn;
   const double b2 = fma(s.by, s.by, fma(s.bz, s.bz, bn2));
   const double rinv = rcp(s.rho);
@@ -27,10 +27,7 @@ __device__ __forceinline__ void phys_speed_rev(const FaceState& s, double bn, do
   const double disc = keep ? disc0 : 0.0;
   const double q1 = rsqrt_(disc);
   const double sd = is_zero(disc) ? 0.0 : disc * q1;
-  const double cf2 = 0.5 * (sum + sd);
-  const double q2 = rsqrt_(cf2);
-  // cf = sqrt(cf2), sd = sqrt(disc): derivative rsqrt / 2, taken as 0 at 0
-  const double dcf2 = is_zero(cf2) ? 0.0 : 0.5 * q2 * dcf;
+  // cf2 = (sum + sd) / 2, sd = sqrt(disc): derivative rsqrt / 2, taken as 0 at 0
   double dsum = 0.5 * dcf2;
   const double dsd = 0.5 * dcf2;
   const double ddisc = (keep && !is_zero(disc)) ? 0.5 * q1 * dsd : 0.0;
@@ -431,12 +428,12 @@ __device__ __forceinline__ void riemann_vjp(const FaceState& sl, const FaceState
   double SL = 0.0, SR = 0.0, ap, am;
   bool llf_left = true, cmax_left = true, umax_left = true, umin_left = true, ap_pos = true, am_pos = true;
   if (RS == RS_LLF) {
-    const double aL = vabs(sl.u) + L.cf, aR = vabs(sr.u) + R.cf;
+    const double aL = vabs(sl.u) + sqrt_(L.cf2), aR = vabs(sr.u) + sqrt_(R.cf2);
     llf_left = dbits(aL) >= dbits(aR);
     ap = am = llf_left ? aL : aR;
   } else {
-    cmax_left = dbits(L.cf) >= dbits(R.cf);
-    const double cmax = cmax_left ? L.cf : R.cf;
+    cmax_left = dbits(L.cf2) >= dbits(R.cf2);
+    const double cmax = sqrt_(cmax_left ? L.cf2 : R.cf2);
     umax_left = okey(sl.u) >= okey(sr.u);
     umin_left = okey(sl.u) <= okey(sr.u);
     const double umax = umax_left ? sl.u : sr.u, umin = umin_left ? sl.u : sr.u;
@@ -524,8 +521,12 @@ __device__ __forceinline__ void riemann_vjp(const FaceState& sl, const FaceState
     if (umax_left) dsl.u += dumax; else dsr.u += dumax;
     if (umin_left) dsl.u += dumin; else dsr.u += dumin;
   }
-  phys_speed_rev(sl, bn, gam, dLb2, dLpt, dLcf, dsl, dbn);
-  phys_speed_rev(sr, bn, gam, dRb2, dRpt, dRcf, dsr, dbn);
+  // cf = sqrt(cf2) (the larger speed is the square root of the larger square): derivative
+  // rsqrt / 2, taken as 0 at 0
+  const double dLcf2 = is_zero(L.cf2) ? 0.0 : 0.5 * rsqrt_(L.cf2) * dLcf;
+  const double dRcf2 = is_zero(R.cf2) ? 0.0 : 0.5 * rsqrt_(R.cf2) * dRcf;
+  phys_speed_rev(sl, bn, gam, dLb2, dLpt, dLcf2, dsl, dbn);
+  phys_speed_rev(sr, bn, gam, dRb2, dRpt, dRcf2, dsr, dbn);
 }
 
 }  // namespace mhd
