@@ -131,15 +131,20 @@ __device__ __forceinline__ T ld04(T apa, T ama, T apc, T amc, T eLB, T eRB, T eL
   return fma(apa * ama * ia, bcR - bcL, fma(-apc * amc * ic, baT - baB, up));
 }
 
-// Q26 corner EMFs (Eq. q26) and their LD04 average, as a function of its 12 inputs.
+// Q26 corner EMFs (Eq. q26) and their LD04 average, as a function of its 12 inputs. The corner
+// EMF -u_a^{S_II} b_c^{S_I} + u_c^{S_I} b_a^{S_II} is bilinear, so the alpha-weighted sums of
+// Eq. (ld04) factor through the two weighted sums BC, UC of the c-face values:
+//   apa e_LB + ama e_RB = -u_a^B BC + b_a^B UC, and likewise on the top side
+// (same value as forming the four corners, four fewer operations).
 template <class T>
 __device__ __forceinline__ T q26_edge_emf(T baB, T baT, T uaB, T uaT, T bcL, T bcR, T ucL, T ucR, T apa, T ama,
                                           T apc, T amc) {
-  const T eLB = fma(-uaB, bcL, ucL * baB);
-  const T eRB = fma(-uaB, bcR, ucR * baB);
-  const T eLT = fma(-uaT, bcL, ucL * baT);
-  const T eRT = fma(-uaT, bcR, ucR * baT);
-  return ld04(apa, ama, apc, amc, eLB, eRB, eLT, eRT, baB, baT, bcL, bcR);
+  const T sa = apa + ama, sc = apc + amc;
+  const T w = rcp(sa * sc);
+  const T BC = fma(apa, bcL, ama * bcR), UC = fma(apa, ucL, ama * ucR);
+  const T hB = fma(-uaB, BC, baB * UC), hT = fma(-uaT, BC, baT * UC);
+  const T up = fma(apc, hB, amc * hT);
+  return fma(apa * ama * sc, bcR - bcL, fma(-(apc * amc * sa), baT - baB, up)) * w;
 }
 
 // Sources reconstructed along a on the c-faces of e-edges (their left/right values), per scheme:
@@ -200,15 +205,14 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
     for (int v = 0; v < NV; ++v) r[v].step(q[v][Xn], lo[v], hi[v]);
     const double bcL = lo[0], bcR = hi[0];
     const double baB = part[0 * N + X], baT = part[1 * N + X];
+    // Eq. (alpha-edge): alpha_a from the two a-faces (c-neighbours), alpha_c from the c-faces
+    const double apa = pmax(Apa[Xc], Apa[X]), ama = pmax(Ama[Xc], Ama[X]);
+    const double apc = pmax(Apc[Xa], Apc[X]), amc = pmax(Amc[Xa], Amc[X]);
+    double emf;
     double eLB, eRB, eLT, eRT;
     if (EMF == EMF_Q26) {
-      // Eq. (q26): corner EMFs -u_a^{S_II} b_c^{S_I} + u_c^{S_I} b_a^{S_II}
-      const double uaB = part[2 * N + X], uaT = part[3 * N + X];
-      const double ucL = lo[1], ucR = hi[1];
-      eLB = fma(-uaB, bcL, ucL * baB);
-      eRB = fma(-uaB, bcR, ucR * baB);
-      eLT = fma(-uaT, bcL, ucL * baT);
-      eRT = fma(-uaT, bcR, ucR * baT);
+      // Eq. (q26) corners and Eq. (ld04), factored
+      emf = q26_edge_emf(baB, baT, part[2 * N + X], part[3 * N + X], bcL, bcR, lo[1], hi[1], apa, ama, apc, amc);
     } else if (EMF == EMF_FS18) {
       // Eq. (fs18-average): mean of the two reconstruction orders per corner, then Eq. (fs18).
       // order a-then-c partials: slot 2k' + ... = (u_a L:B,T, u_a R:B,T, u_c L:B,T, u_c R:B,T)
@@ -244,10 +248,7 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
       eLT = ec[2];
       eRT = ec[3];
     }
-    // Eq. (alpha-edge): alpha_a from the two a-faces (c-neighbours), alpha_c from the c-faces
-    const double apa = pmax(Apa[Xc], Apa[X]), ama = pmax(Ama[Xc], Ama[X]);
-    const double apc = pmax(Apc[Xa], Apc[X]), amc = pmax(Amc[Xa], Amc[X]);
-    double emf = ld04(apa, ama, apc, amc, eLB, eRB, eLT, eRT, baB, baT, bcL, bcR);
+    if (EMF != EMF_Q26) emf = ld04(apa, ama, apc, amc, eLB, eRB, eLT, eRT, baB, baT, bcL, bcR);
     if (D.resistive) {
       const double j = (Bc[X] - Bc[Xa]) * D.hinv[a] - (Ba[X] - Ba[Xc]) * D.hinv[c];
       emf = fma(D.eta, j, emf);
