@@ -365,12 +365,13 @@ __device__ __forceinline__ void phys_speed(const FaceStateT<T>& s, T bn, double 
   const T b2 = fma(s.by, s.by, fma(s.bz, s.bz, bn2));
   o.b2 = b2;
   o.pt = fma(0.5, b2, s.p);
-  const T rinv = rcp(s.rho);
-  const T a2 = gam * s.p * rinv;
-  const T sum = fma(b2, rinv, a2);
-  T disc = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
+  // rho c_f^2 = (P + b^2 + sqrt((P + b^2)^2 - 4 P b_n^2)) / 2 with P = gamma p: the discriminant
+  // needs no 1/rho, which enters once at the end
+  const T P = gam * s.p;
+  const T Sp = P + b2;
+  T disc = fma(Sp, Sp, (-4.0 * bn2) * P);
   disc = pmax(disc, T(0.0));
-  o.cf2 = 0.5 * (sum + sqrt_(disc));
+  o.cf2 = (0.5 * rcp(s.rho)) * (Sp + sqrt_(disc));
 }
 
 // Conserved vector and ideal-MHD flux of Eq. (mhd:conservation-laws) in the face frame, with e_tot

@@ -19,27 +19,27 @@ __device__ __forceinline__ void phys_speed_rev(const FaceState& s, double bn, do
                                                double dcf2, FaceState& ds, double& dbn) {
   const double bn2 = bn * bn;
   const double b2 = fma(s.by, s.by, fma(s.bz, s.bz, bn2));
-  const double rinv = rcp(s.rho);
-  const double a2 = gam * s.p * rinv;
-  const double sum = fma(b2, rinv, a2);
-  const double disc0 = fma(sum, sum, -4.0 * (a2 * bn2 * rinv));
+  const double P = gam * s.p;
+  const double Sp = P + b2;
+  const double disc0 = fma(Sp, Sp, (-4.0 * bn2) * P);
   const bool keep = dbits(disc0) >= dbits(0.0);  // pmax(disc, 0) keeps disc
   const double disc = keep ? disc0 : 0.0;
   const double q1 = rsqrt_(disc);
   const double sd = is_zero(disc) ? 0.0 : disc * q1;
-  // cf2 = (sum + sd) / 2, sd = sqrt(disc): derivative rsqrt / 2, taken as 0 at 0
-  double dsum = 0.5 * dcf2;
-  const double dsd = 0.5 * dcf2;
+  const double r = rcp(s.rho);
+  // cf2 = (r / 2) (Sp + sd)
+  const double dh = dcf2 * (Sp + sd);
+  double dSp = dcf2 * 0.5 * r;
+  const double dsd = dSp;
+  ds.rho -= 0.5 * dh * r * r;
+  // sd = sqrt(disc): derivative rsqrt / 2, taken as 0 at 0
   const double ddisc = (keep && !is_zero(disc)) ? 0.5 * q1 * dsd : 0.0;
-  dsum += 2.0 * sum * ddisc;
-  const double dt = -4.0 * ddisc;  // t = a2 bn2 rinv
-  double da2 = dt * bn2 * rinv, dbn2 = dt * a2 * rinv, drinv = dt * a2 * bn2;
-  double db2t = db2 + dsum * rinv;
-  drinv += dsum * b2;
-  da2 += dsum;
-  ds.p += da2 * gam * rinv;
-  drinv += da2 * gam * s.p;
-  ds.rho -= drinv * rinv * rinv;
+  // disc = Sp^2 - 4 bn2 P
+  dSp += 2.0 * Sp * ddisc;
+  double dbn2 = -4.0 * P * ddisc;
+  const double dP = -4.0 * bn2 * ddisc + dSp;  // Sp = P + b2
+  double db2t = db2 + dSp;
+  ds.p += gam * dP;
   ds.p += dpt;
   db2t += 0.5 * dpt;
   ds.by += 2.0 * s.by * db2t;
