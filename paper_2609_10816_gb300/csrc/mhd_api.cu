@@ -94,10 +94,17 @@ struct Timed {
   }
 };
 
-// one RK stage: prim -> faces -> edges -> update -> flags -> flux correction
-void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc) {
+// one RK stage: prim -> faces -> edges -> update -> flags -> flux correction. prim_given: the
+// previous stage's flag pass wrote this stage's primitives (redo them only if it flagged cells).
+void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc, bool prim_given = false) {
   cudaStream_t st = c->stream;
-  { Timed t(c, MHD_K_PRIM, 1); mhd::launch_prim(D, st); }
+  if (prim_given) {
+    Timed t(c, MHD_K_PRIM, 1);
+    mhd::launch_prim_if_flagged(D, D.stage - 1, st);
+  } else {
+    Timed t(c, MHD_K_PRIM, 1);
+    mhd::launch_prim(D, st);
+  }
   for (int dir = 0; dir < 3; ++dir) {
     Timed t(c, MHD_K_FACE, 1);
     mhd::launch_face(D, dir, sc.recon, sc.rs, c->seg, st);
@@ -282,6 +289,7 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
   for (int d = 0; d < 3; ++d) D.Bout[d] = ctx->B1[d];
   D.combine = 0;
   D.stage = 0;
+  D.Pnext = D.P;  // stage 1's flag pass leaves the primitives of S^{n+1/2} for stage 2
   run_stage(ctx, D, sc);
 
   // stage 2: S^{n+1} = S^n + D(F_rk), F_rk = (F^n + F^{n+1/2}) / 2  (Eq. rk2:update); the
@@ -290,7 +298,8 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
   for (int d = 0; d < 3; ++d) D.Bin[d] = ctx->B1[d];
   D.combine = 1;
   D.stage = 1;
-  run_stage(ctx, D, sc);
+  D.Pnext = nullptr;
+  run_stage(ctx, D, sc, true);
 
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;

@@ -140,8 +140,10 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   // grid barrier, which block 0 passes only after this
   if (blockIdx.x == 0 && threadIdx.x < 3) atomicExch(B.cursor + threadIdx.x, 0ull);
   // cons -> prim; the per-cell phases take kCellIlp cells per thread at a time, loads of all of
-  // them before any store (the persistent grid has few warps per SM to hide memory latency)
-  for (long long i0 = t0, k = k0; i0 < ncell; i0 += kCellIlp * nth) {
+  // them before any store (the persistent grid has few warps per SM to hide memory latency).
+  // Stage 2's primitives come from stage 1's update phase unless flux correction changed its state.
+  const bool prim_given = B.stage == 1 && *(volatile unsigned long long*)(B.counters + 0) == 0;
+  for (long long i0 = t0, k = k0; i0 < ncell && !prim_given; i0 += kCellIlp * nth) {
     double w[kCellIlp][8];
     const Dev* Dp[kCellIlp];
     long long X[kCellIlp];
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   // update and validity flags (every lane of a warp runs the same number of passes for the ballot)
   int kf = k0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kCellIlp * nth) {
-    double w[kCellIlp][8];
+    double w[kCellIlp][8], hi[kCellIlp][3];
     bool f[kCellIlp];
     const Dev* Dp[kCellIlp];
     long long X[kCellIlp];
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
         kf = advance_pos(B.cell_pref, kf, i);
         Dp[g] = &B.patches[B.order[kf]];
         X[g] = i - B.cell_pref[kf];
-        f[g] = update_flag_vals(*Dp[g], X[g], w[g]);
+        f[g] = update_flag_vals(*Dp[g], X[g], w[g], hi[g]);
       }
     }
     unsigned cnt = 0;
@@ -215,6 +217,11 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
       if (Dp[g]) {
         store_update(*Dp[g], X[g], w[g]);
         Dp[g]->flag[X[g]] = f[g] ? 1 : 0;
+        if (B.stage == 0) {  // the primitives of S^{n+1/2}, stage 2's input
+          double pw[8];
+          prim_from(*Dp[g], w[g], w[g] + 5, hi[g], pw);
+          for (int v = 0; v < 8; ++v) Dp[g]->P[v * Dp[g]->N + X[g]] = pw[v];
+        }
       }
       cnt += __popc(__ballot_sync(0xffffffffu, f[g]));
     }

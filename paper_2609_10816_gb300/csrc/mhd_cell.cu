@@ -11,6 +11,13 @@ __global__ void __launch_bounds__(256) k_prim(Dev D) {
   const long long X = cell_id();
   if (X < D.N) prim_cell(D, X);
 }
+// the primitives of a stage input that the previous stage's flag pass wrote, redone only when
+// flux correction changed that state
+__global__ void __launch_bounds__(256) k_prim_if_flagged(Dev D, int prev_stage) {
+  if (D.counters[prev_stage] == 0) return;
+  const long long X = cell_id();
+  if (X < D.N) prim_cell(D, X);
+}
 __global__ void __launch_bounds__(256) k_update(Dev D) {
   const long long X = cell_id();
   if (X < D.N) update_cell(D, X);
@@ -127,6 +134,9 @@ static unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 void launch_prim(const Dev& d, cudaStream_t st) { k_prim<<<blocks_for(d.N, 256), 256, 0, st>>>(d); }
 void launch_update(const Dev& d, cudaStream_t st) { k_update<<<blocks_for(d.N, 256), 256, 0, st>>>(d); }
 void launch_flag(const Dev& d, cudaStream_t st) { k_flag<<<blocks_for(d.N, 256), 256, 0, st>>>(d); }
+void launch_prim_if_flagged(const Dev& d, int prev_stage, cudaStream_t st) {
+  k_prim_if_flagged<<<blocks_for(d.N, 256), 256, 0, st>>>(d, prev_stage);
+}
 void launch_fofc(const Dev& d, cudaStream_t st) {
   k_fo_faces<<<blocks_for(d.N, 128), 128, 0, st>>>(d);
   k_fo_edges<<<blocks_for(d.N, 128), 128, 0, st>>>(d);

@@ -11,21 +11,38 @@ namespace mhd {
 __device__ __forceinline__ long long cell_id() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 
 // ---- cons -> prim (Eq. state:primitive), with the face-averaged cell field ----------------
-__device__ __forceinline__ void prim_of(const Dev& D, const double* U, const double* const* B,
-                                        long long X, double* w) {
-  const long long N = D.N;
-  const double rho = U[X];
+// from a cell's 5 conserved values u and its lower / upper face fields
+__device__ __forceinline__ void prim_from(const Dev& D, const double* u, const double* lo, const double* hi,
+                                          double* w) {
+  const double rho = u[0];
   const double rinv = rcp(rho);
-  const double u0 = U[N + X] * rinv, u1 = U[2 * N + X] * rinv, u2 = U[3 * N + X] * rinv;
-  const double b0 = 0.5 * (B[0][X] + B[0][shift(D, X, 0, 1)]);
-  const double b1 = 0.5 * (B[1][X] + B[1][shift(D, X, 1, 1)]);
-  const double b2 = 0.5 * (B[2][X] + B[2][shift(D, X, 2, 1)]);
+  const double u0 = u[1] * rinv, u1 = u[2] * rinv, u2 = u[3] * rinv;
+  const double b0 = 0.5 * (lo[0] + hi[0]);
+  const double b1 = 0.5 * (lo[1] + hi[1]);
+  const double b2 = 0.5 * (lo[2] + hi[2]);
   const double u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
   const double b2s = fma(b0, b0, fma(b1, b1, b2 * b2));
-  const double eint = U[4 * N + X] - 0.5 * fma(rho, u2s, b2s);
+  const double eint = u[4] - 0.5 * fma(rho, u2s, b2s);
   w[0] = rho; w[1] = u0; w[2] = u1; w[3] = u2;
   w[4] = (D.gam - 1.0) * eint;
   w[5] = b0; w[6] = b1; w[7] = b2;
+}
+__device__ __forceinline__ void load_cell(const Dev& D, const double* U, const double* const* B, long long X,
+                                          double* u, double* lo, double* hi) {
+  const long long N = D.N;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = U[v * N + X];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = B[d][X];
+    hi[d] = B[d][shift(D, X, d, 1)];
+  }
+}
+__device__ __forceinline__ void prim_of(const Dev& D, const double* U, const double* const* B,
+                                        long long X, double* w) {
+  double u[5], lo[3], hi[3];
+  load_cell(D, U, B, X, u, lo, hi);
+  prim_from(D, u, lo, hi, w);
 }
 
 // ---- CFL signal speed (Sec. 2.4, Eq. waves:fast-speed) ----------------------------------------
@@ -166,19 +183,26 @@ __device__ __forceinline__ bool invalid_cell(const Dev& D, const double* U, doub
 // neighbours compute them) instead of read back, so no separate pass over the new state is needed
 // (the batched stage's fused phase; on a single box two passes are faster: the recomputed faces'
 // EMFs of the next plane come from L2, while the flag pass streams the new state)
-__device__ __forceinline__ bool update_flag_vals(const Dev& D, long long X, double* out) {
+__device__ __forceinline__ bool update_flag_vals(const Dev& D, long long X, double* out, double* hi) {
   const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
   update_vals(D, X, Xp, out);
-  double hi[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) hi[d] = upper_face_new(D, d, Xp[d]);
   return invalid_vals(D, out, out + 5, hi);
 }
 
-// flag of cell X (written) and whether it is set
+// flag of cell X (written) and whether it is set; with D.Pnext also the cell's primitives
 __device__ __forceinline__ bool flag_cell(const Dev& D, long long X) {
-  const unsigned char f = invalid_cell(D, D.Uout, D.Bout, X) ? 1 : 0;
+  double u[5], lo[3], hi[3];
+  load_cell(D, D.Uout, D.Bout, X, u, lo, hi);
+  const unsigned char f = invalid_vals(D, u, lo, hi) ? 1 : 0;
   D.flag[X] = f;
+  if (D.Pnext) {
+    double w[8];
+    prim_from(D, u, lo, hi, w);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) D.Pnext[v * D.N + X] = w[v];
+  }
   return f != 0;
 }
 

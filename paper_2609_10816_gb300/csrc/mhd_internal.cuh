@@ -49,6 +49,8 @@ struct Dev {
   double* EfL;    // [3][2][N] B25a e-EMF on a-faces (L/R) for order (a then c)
   double* EfB;    // [3][2][N] B25a e-EMF on c-faces (B/T) for order (c then a)
   unsigned char* flag;         // [N]
+  double* Pnext;  // when set, the flag pass also writes the primitives of its state here (the next
+                  // stage's input, whose prim pass then runs only if flux correction changed it)
   unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
   // work-list cursors of the dynamically scheduled sweeps ([dir] face, [3 + e] edge_bt,
   // [6 + e] edge_lr), zeroed before every stage; NULL: one segment per thread, no cursor
@@ -96,6 +98,7 @@ void launch_edges_bt(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_update(const Dev& d, cudaStream_t st);
 void launch_flag(const Dev& d, cudaStream_t st);
+void launch_prim_if_flagged(const Dev& d, int prev_stage, cudaStream_t st);
 void launch_fofc(const Dev& d, cudaStream_t st);
 void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st);
 void launch_divb(const Dev& d, Ptr3 B, unsigned long long* out, cudaStream_t st);

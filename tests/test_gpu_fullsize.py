@@ -162,6 +162,38 @@ def test_reconnection_512x512x4_sampled(gpu_lib):
     assert worst <= 1e-12, worst
 
 
+def test_reconnection_512x512x4_five_steps_sampled(gpu_lib):
+    """Five full-size steps of the reconnection run (GPU dt sequence) against the oracle on two
+    sub-boxes across the sheets, 192 x 192 x 4 each, compared on the central 32 x 32 x 4 (a margin
+    of 80 cells covers five steps' reach of PLM + Q26 + flux correction)."""
+    shape = (512, 512, 4)
+    cons, b, info = inputs.harris_sheet(shape)
+    sch = mhd.scheme("plm_mc", "hlld", "q26")
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    dts = []
+    for _ in range(5):
+        dts.append(ctx.max_dt(st, 0.3, 1e-4))
+        ctx.step(st, dts[-1], sch, 1e-4)
+    torch.cuda.synchronize()
+    cg, bg = st.cons.cpu().numpy(), st.b.cpu().numpy()
+    md, mb = ctx.divb(st)
+    ctx.close()
+    assert md * info["h"][0] / mb <= 1e-13
+    scales = field_scales(cons, b)
+    widths = (192, 192, 4)
+    for ctr in [(256, 128, 2), (100, 384, 2)]:
+        sc, sb, _ = _cut(cons, b, ctr, widths)
+        cfg = oracle.Config(shape=widths, h=info["h"], recon="plm_mc", riemann="hlld", emf="q26", eta=1e-4)
+        for dt in dts:
+            sc, sb, _ = oracle.step(cfg, sc, sb, dt)
+        gc, gb, _ = _cut(cg, bg, ctr, widths)
+        sl = (slice(None), slice(80, 112), slice(80, 112))
+        errs = [rel_l1(gc[v][sl], sc[v][sl], scales[0][v]) for v in range(5)]
+        errs += [rel_l1(gb[d][sl], sb[d][sl], scales[1][d]) for d in range(3)]
+        assert max(errs) <= 1e-12, (ctr, errs)
+
+
 def test_batch_1024_patches_full(gpu_lib):
     """The 1024-patch batch (edges from {16, 24, 32, 48, 64}) with the autotuned schedule: one
     graph-replayed step; sampled patches equal single-box steps bitwise."""
