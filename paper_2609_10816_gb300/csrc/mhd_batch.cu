@@ -35,6 +35,7 @@ struct BatchDev {
   int barrier_extra;              // test hook: wait for this many blocks more than launched
   unsigned long long* ptime;      // [2][8] global-timer stamps at the phase boundaries of each stage
   unsigned long long* cursor;     // [3] work-list cursors of the face, edge_bt and edge_lr phases
+  unsigned* patch_flags;          // [2][npatch] flagged cells per stage and schedule position
 };
 
 // position k with pref[k] <= i < pref[k + 1]
@@ -139,9 +140,13 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   // the sweep phases' cursors start at zero; no block takes work from them before the first
   // grid barrier, which block 0 passes only after this
   if (blockIdx.x == 0 && threadIdx.x < 3) atomicExch(B.cursor + threadIdx.x, 0ull);
+  // per-patch flag counts of this stage start at zero (read after later barriers only)
+  unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
+  for (long long i = t0; i < B.npatch; i += nth) pflags[i] = 0u;
   // cons -> prim; the per-cell phases take kCellIlp cells per thread at a time, loads of all of
   // them before any store (the persistent grid has few warps per SM to hide memory latency).
   // Stage 2's primitives come from stage 1's update phase unless flux correction changed its state.
+  // (per patch: only patches where stage 1 flagged a cell are redone)
   const bool prim_given = B.stage == 1 && *(volatile unsigned long long*)(B.counters + 0) == 0;
   for (long long i0 = t0, k = k0; i0 < ncell && !prim_given; i0 += kCellIlp * nth) {
     double w[kCellIlp][8];
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
       Dp[g] = nullptr;
       if (i < ncell) {
         k = advance_pos(B.cell_pref, (int)k, i);
+        if (B.stage == 1 && B.patch_flags[k] == 0u) continue;  // stage 1 left this patch's primitives
         Dp[g] = &B.patches[B.order[k]];
         X[g] = i - B.cell_pref[k];
         prim_of(*Dp[g], Dp[g]->Uin, Dp[g]->Bin, X[g], w[g]);
@@ -196,6 +202,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   int kf = k0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kCellIlp * nth) {
     double w[kCellIlp][8], hi[kCellIlp][3];
+    int K[kCellIlp];
     bool f[kCellIlp];
     const Dev* Dp[kCellIlp];
     long long X[kCellIlp];
@@ -208,6 +215,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
         kf = advance_pos(B.cell_pref, kf, i);
         Dp[g] = &B.patches[B.order[kf]];
         X[g] = i - B.cell_pref[kf];
+        K[g] = kf;
         f[g] = update_flag_vals(*Dp[g], X[g], w[g], hi[g]);
       }
     }
@@ -217,6 +225,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
       if (Dp[g]) {
         store_update(*Dp[g], X[g], w[g]);
         Dp[g]->flag[X[g]] = f[g] ? 1 : 0;
+        if (f[g]) atomicAdd(&pflags[K[g]], 1u);
         if (B.stage == 0) {  // the primitives of S^{n+1/2}, stage 2's input
           double pw[8];
           prim_from(*Dp[g], w[g], w[g] + 5, hi[g], pw);
@@ -231,8 +240,10 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   if (!grid_sync(B)) return;
   stamp(B, 5);
   if (*(volatile unsigned long long*)(B.counters + B.stage) == 0) return;  // uniform over the grid
+  // patches are independent boxes: only those with a flagged cell have anything to correct
   for (long long i = t0, k = k0; i < ncell; i += nth) {
     k = advance_pos(B.cell_pref, (int)k, i);
+    if (pflags[k] == 0u) continue;
     const Dev& D = B.patches[B.order[k]];
     fo_faces_cell(D, i - B.cell_pref[k]);
     fo_edges_cell(D, i - B.cell_pref[k]);
@@ -241,6 +252,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   stamp(B, 6);
   for (long long i = t0, k = k0; i < ncell; i += nth) {
     k = advance_pos(B.cell_pref, (int)k, i);
+    if (pflags[k] == 0u) continue;
     fo_recompute_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
   }
 }
@@ -348,6 +360,7 @@ struct mhd_batch {
   unsigned* barrier;              // 2
   unsigned long long* ptime;      // [2][8] phase stamps of the last step
   unsigned long long* cursor;     // [3] sweep-phase work cursors
+  unsigned* patch_flags;          // [2][npatch]
   double* dt_dev;
   mhd::Dev* pdev[2];              // per-patch parameters per stage
   int* order_dev;
@@ -491,6 +504,7 @@ mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc) {
   B.barrier_extra = b->barrier_extra;
   B.ptime = b->ptime;
   B.cursor = b->cursor;
+  B.patch_flags = b->patch_flags;
   return B;
 }
 
@@ -591,7 +605,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->params_ok = false;
   const long long C = b->ncell;
   size_t bytes = (size_t)C * (5 + 3 + 47) * sizeof(double) + (size_t)C + 24 * 256 +
-                 2 * npatch * sizeof(mhd::Dev) + npatch * sizeof(int) + 4 * (npatch + 1) * sizeof(long long);
+                 2 * npatch * sizeof(mhd::Dev) + 3 * npatch * sizeof(int) + 4 * (npatch + 1) * sizeof(long long);
   cudaError_t e = cudaMalloc(&b->mem, bytes);
   if (e != cudaSuccess) {
     g_batch_create_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -608,6 +622,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->barrier = (unsigned*)take(2 * sizeof(unsigned));
   b->ptime = (unsigned long long*)take(16 * sizeof(unsigned long long));
   b->cursor = (unsigned long long*)take(4 * sizeof(unsigned long long));
+  b->patch_flags = (unsigned*)take(2 * npatch * sizeof(unsigned));
   b->dt_dev = (double*)take(sizeof(double));
   b->pdev[0] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
   b->pdev[1] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
