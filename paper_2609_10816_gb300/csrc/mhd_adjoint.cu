@@ -326,14 +326,13 @@ __global__ void __launch_bounds__(128) k_adj_faces(AdjDev A, int dir) {
   if (f >= D.N) return;
   const long long N = D.N;
   const int a = (dir + 1) % 3, c = (dir + 2) % 3;
-  const int slot[7] = {0, 1 + dir, 1 + a, 1 + c, 4, 5 + a, 5 + c};
+  // the face states as the forward sweep reconstructed them (stored by its recompute)
   double WL[7], WR[7];
-  const long long fl = shift(D, f, dir, -1);
+  const double* lr = D.LR + 14LL * dir * N;
 #pragma unroll
   for (int v = 0; v < 7; ++v) {
-    double lo, hi;
-    rec_val<RC>(D, D.P + slot[v] * N, fl, dir, lo, WL[v]);
-    rec_val<RC>(D, D.P + slot[v] * N, f, dir, WR[v], hi);
+    WL[v] = lr[v * N + f];
+    WR[v] = lr[(7 + v) * N + f];
   }
   const double bn = D.Bin[dir][f];
   const double* lF = A.lF + 5LL * dir * N;

@@ -401,8 +401,9 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   const long long N = ctx->base.N;
   cudaStream_t st = ctx->stream;
   // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
-  // lB0 3, lam2 8, and the stage-1 input's P 8 and alpha+- / u* 9 (doubles per cell) + eta
-  const size_t nd = 142;
+  // lB0 3, lam2 8, the stage-1 input's P 8 and alpha+- / u* 9, and the forward face states of
+  // both stage inputs 2 x 42 (doubles per cell) + eta
+  const size_t nd = 226;
   if (!ctx->adj) {
     s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + 8) * sizeof(double)), "cudaMalloc of adjoint scratch");
     if (s != MHD_OK) { ctx->adj = nullptr; return s; }
@@ -425,6 +426,8 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* lamB = take(3);
   double* P0 = take(8);
   double* Apm0 = take(9);
+  double* LR0 = take(42);
+  double* LR1 = take(42);
   double* lEta = q;
 
   mhd::Dev D = ctx->base;
@@ -458,6 +461,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   D0.Ap = Apm0;
   D0.Am = Apm0 + 3 * N;
   D0.Us = Apm0 + 6 * N;
+  D0.LR = LR0;  // the forward face states, which the stage-1 adjoint reads
   run_stage(ctx, D0, sc);
 
   auto adj_dev = [&](const mhd::Dev& Ds, double* lU, double* lB) {
@@ -477,6 +481,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   mhd::Dev D1 = D;
   D1.Uin = ctx->U1;
   for (int d = 0; d < 3; ++d) D1.Bin[d] = ctx->B1[d];
+  D1.LR = LR1;
   recompute(D1);
   mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
   e = zero(lU1, 5);

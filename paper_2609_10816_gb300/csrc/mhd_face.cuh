@@ -62,6 +62,14 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
     double Lv[7], Rv[7];
 #pragma unroll
     for (int v = 0; v < 7; ++v) r[v].step(q[v][Xn], Lv[v], Rv[v]);
+    if (D.LR) {
+      double* lr = D.LR + 14LL * dir * N;
+#pragma unroll
+      for (int v = 0; v < 7; ++v) {
+        lr[v * N + X] = Lv[v];
+        lr[(7 + v) * N + X] = Rv[v];
+      }
+    }
     const FaceState sl = {Lv[0], Lv[1], Lv[2], Lv[3], Lv[4], Lv[5], Lv[6]};
     const FaceState sr = {Rv[0], Rv[1], Rv[2], Rv[3], Rv[4], Rv[5], Rv[6]};
     double f[5], ap, am, us;

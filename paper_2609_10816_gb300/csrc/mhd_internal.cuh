@@ -51,6 +51,8 @@ struct Dev {
   unsigned char* flag;         // [N]
   double* Pnext;  // when set, the flag pass also writes the primitives of its state here (the next
                   // stage's input, whose prim pass then runs only if flux correction changed it)
+  double* LR;     // when set, the face sweep also stores its reconstructed left (7) and right (7)
+                  // face states here, [3][14][N] (for the adjoint)
   unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
   // work-list cursors of the dynamically scheduled sweeps ([dir] face, [3 + e] edge_bt,
   // [6 + e] edge_lr), zeroed before every stage; NULL: one segment per thread, no cursor
