@@ -79,3 +79,30 @@ def test_product_package_never_imports_the_oracle():
         assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
     for f in glob.glob(os.path.join(pkg, "csrc", "*")):
         assert "oracle" not in open(f).read().lower(), f
+
+
+def test_batch_and_noalloc_reject_bad_arguments_before_touching_the_device(lib):
+    from paper_2609_10816_gb300 import mhd
+
+    L = mhd.lib()
+    out = ctypes.c_void_p()
+    for dims in ([4, 4, 0], [4, -1, 4], [2048, 2048, 1024]):  # empty, negative, >= 2^31 cells
+        arr = (ctypes.c_int * 3)(*dims)
+        assert L.mhd_batch_create(arr, 1, 0.1, 5 / 3, None, ctypes.byref(out)) == mhd.ERR_ARG
+        assert out.value is None
+        assert L.mhd_batch_last_error(None)
+    arr = (ctypes.c_int * 3)(4, 4, 4)
+    assert L.mhd_batch_create(arr, 0, 0.1, 5 / 3, None, ctypes.byref(out)) == mhd.ERR_ARG
+    assert L.mhd_batch_create(arr, 1, -0.1, 5 / 3, None, ctypes.byref(out)) == mhd.ERR_ARG
+    assert L.mhd_batch_step(None, None, 0.3, 0, 0.0) == mhd.ERR_ARG
+    assert L.mhd_batch_set_schedule(None, 64, 1, 0, 1) == mhd.ERR_ARG
+    ms = (ctypes.c_double * 12)()
+    assert L.mhd_batch_phase_ms(None, ms) == mhd.ERR_ARG
+    # the allocation-free step refuses boxes above its fixed array before any device work
+    cfg = mhd._Config(64, 64, 64, 0.1, 0.1, 0.1, 5 / 3, 3)
+    fake = ctypes.c_double(0.0)  # never dereferenced: the size check comes first
+    ptr = ctypes.addressof(fake)
+    state = mhd._State(ptr, ptr, ptr, ptr)
+    rc = L.mhd_step_noalloc(ctypes.byref(cfg), ctypes.byref(state), ctypes.c_double(0.1), 0, ctypes.c_double(0.0),
+                            None)
+    assert rc == mhd.ERR_ARG and b"exceeds" in L.mhd_create_error()
