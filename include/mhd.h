@@ -138,11 +138,14 @@ mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches,
 mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_state *lam, double dt, int scheme,
                             double eta, double *dL_deta);
 
-/* Self-check of the reciprocal, reciprocal square root and square root that the kernels use in
- * place of IEEE division and sqrt (hardware approximation + one third-order Newton correction):
- * on n pseudo-random positive inputs spread over [2^-40, 2^40] it returns in max_rel_err[0..2]
- * the largest relative differences from CUDA's IEEE 1/x, 1/sqrt(x) and sqrt(x). Synchronous.
- * The paper has no counterpart. */
+/* Self-check of the arithmetic the kernels use in place of FP64 instructions: on n pseudo-random
+ * positive inputs spread over [2^-40, 2^40], max_rel_err[0..2] receive the largest relative
+ * differences of the reciprocal, reciprocal square root and square root (hardware approximation +
+ * one third-order Newton correction) from CUDA's IEEE 1/x, 1/sqrt(x) and sqrt(x); on n raw bit
+ * patterns (subnormal, smallest, largest and non-finite binades among them), max_rel_err[3] and
+ * [4] receive how many times the integer-pipe halving and quadrupling differ in any bit from the
+ * FP64 multiplies by 0.5 and 4 (0 expected). max_rel_err holds 5 doubles. Synchronous. The
+ * paper has no counterpart. */
 mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
 
 /* Self-check of the adjoint's reverse sweep through the face solve (the Riemann solver of

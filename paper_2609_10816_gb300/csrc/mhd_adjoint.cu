@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(256) k_adj_update(Dev D, const double* lU, con
     }
   }
   for (int e = 0; e < 3; ++e) {
-    // E_e enters B_{e+1} as its "c" EMF and B_{e+2} as its "a" EMF (see incr_face)
+    // E_e enters B_{e+1} as its "c" EMF and B_{e+2} as its "a" EMF (see face_new)
     const int d1 = (e + 1) % 3, a1 = (d1 + 1) % 3;  // B_d1[Y]: +dt/h_a1 E_e[Y] - dt/h_a1 E_e[Y + a1]
     const int d2 = (e + 2) % 3, c2 = (d2 + 2) % 3;  // B_d2[Y]: -dt/h_c2 E_e[Y] + dt/h_c2 E_e[Y + c2]
     const double g = scale * D.dt *

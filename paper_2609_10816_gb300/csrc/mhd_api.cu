@@ -272,6 +272,7 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
   mhd::Dev D = ctx->base;
   const long long N = D.N;
   D.dt = dt;
+  for (int d = 0; d < 3; ++d) D.dth[d] = dt * D.hinv[d];
   D.eta = eta;
   D.resistive = eta != 0.0;
   D.emf = sc.emf;
@@ -432,6 +433,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
 
   mhd::Dev D = ctx->base;
   D.dt = dt;
+  for (int d = 0; d < 3; ++d) D.dth[d] = dt * D.hinv[d];
   D.eta = eta;
   // the resistive terms are linear in eta: their derivative in eta is needed even at eta = 0,
   // where they add exact zeros to the forward values
@@ -548,16 +550,18 @@ mhd_status mhd_math_check(mhd_ctx* ctx, long long n, double* max_rel_err) {
   ctx->err.clear();
   if (!max_rel_err || n < 1 || n > (1LL << 40)) return fail(ctx, MHD_ERR_ARG, "need 1 <= n <= 2^40 and an output");
   const mhd::Dev& D = ctx->base;
-  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 3 * sizeof(unsigned long long), ctx->stream),
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 5 * sizeof(unsigned long long), ctx->stream),
                             "cudaMemsetAsync");
   if (s != MHD_OK) return s;
   mhd::launch_math_check(n, D.counters + 2, ctx->stream);
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
-  unsigned long long h[3] = {0, 0, 0};
-  s = read_counters(ctx, h, 3);
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  s = read_counters(ctx, h, 5);
   if (s != MHD_OK) return s;
   for (int k = 0; k < 3; ++k) std::memcpy(&max_rel_err[k], &h[k], sizeof(double));
+  max_rel_err[3] = (double)h[3];
+  max_rel_err[4] = (double)h[4];
   return MHD_OK;
 }
 

@@ -312,6 +312,10 @@ __global__ void k_batch_set_dt(Dev* p0, Dev* p1, int npatch, const unsigned long
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npatch; k += gridDim.x * blockDim.x) {
     p0[k].dt = dt;
     p1[k].dt = dt;
+    for (int d = 0; d < 3; ++d) {
+      p0[k].dth[d] = dt * p0[k].hinv[d];
+      p1[k].dth[d] = dt * p1[k].hinv[d];
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *dt_out = dt;
 }

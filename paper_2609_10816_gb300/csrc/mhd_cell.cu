@@ -123,6 +123,28 @@ __global__ void __launch_bounds__(256) k_math_check(long long n, unsigned long l
   block_max_atomic(er, out);
   block_max_atomic(es, out + 1);
   block_max_atomic(eq, out + 2);
+  // exactness of the integer-pipe halving and quadrupling against the FP64 multiplies, on raw bit
+  // patterns (every eighth with its exponent forced into the subnormal / smallest / largest
+  // binades, where the integer paths branch)
+  if (i < n) {
+    unsigned long long z = (unsigned long long)(i + n) * 0xD1B54A32D192ED03ull + 0x8CB92BA72F3D8DD7ull;
+    z ^= z >> 33;
+    z *= 0xFF51AFD7ED558CCDull;
+    z ^= z >> 29;
+    long long b = (long long)z;
+    if ((z & 7) == 0) {
+      const long long exps[6] = {0, 1, 2, 2045, 2046, 2047};
+      b = (b & (long long)0x800fffffffffffffULL) | (exps[(z >> 3) % 6] << 52);
+    }
+    const double x = dfrom(b);
+    const double h0 = x * 0.5, h1 = halve(x);
+    const bool hbad = (x == x) ? dbits(h0) != dbits(h1) : (h1 == h1);  // NaN must stay NaN
+    const double m = vabs(x);
+    const double f0 = m * 4.0, f1 = times4(m);
+    const bool fbad = (m == m) ? dbits(f0) != dbits(f1) : false;
+    if (hbad) atomicAdd(out + 3, 1ull);
+    if (fbad) atomicAdd(out + 4, 1ull);
+  }
 }
 
 void launch_math_check(long long n, unsigned long long* out, cudaStream_t st) {

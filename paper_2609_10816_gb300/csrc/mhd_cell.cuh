@@ -17,12 +17,12 @@ __device__ __forceinline__ void prim_from(const Dev& D, const double* u, const d
   const double rho = u[0];
   const double rinv = rcp(rho);
   const double u0 = u[1] * rinv, u1 = u[2] * rinv, u2 = u[3] * rinv;
-  const double b0 = 0.5 * (lo[0] + hi[0]);
-  const double b1 = 0.5 * (lo[1] + hi[1]);
-  const double b2 = 0.5 * (lo[2] + hi[2]);
+  const double b0 = halve(lo[0] + hi[0]);
+  const double b1 = halve(lo[1] + hi[1]);
+  const double b2 = halve(lo[2] + hi[2]);
   const double u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
   const double b2s = fma(b0, b0, fma(b1, b1, b2 * b2));
-  const double eint = u[4] - 0.5 * fma(rho, u2s, b2s);
+  const double eint = u[4] - halve(fma(rho, u2s, b2s));
   w[0] = rho; w[1] = u0; w[2] = u1; w[3] = u2;
   w[4] = (D.gam - 1.0) * eint;
   w[5] = b0; w[6] = b1; w[7] = b2;
@@ -71,7 +71,7 @@ __device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, c
   for (int d = 0; d < 3; ++d) {
     const double bn2 = w[5 + d] * w[5 + d];
     const double disc = pmax(fma(sum, sum, -4.0 * (a2 * bn2 * rinv)), 0.0);
-    const double cf = sqrt_(0.5 * (sum + sqrt_(disc)));
+    const double cf = sqrt_(halve(sum + sqrt_(disc)));
     s = pmax(s, (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]));
   }
   if (!finite_d(s)) s = __longlong_as_double(0x7ff0000000000000LL);  // +inf
@@ -86,32 +86,30 @@ __device__ __forceinline__ void prim_cell(const Dev& D, long long X) {
 }
 
 // ---- update: S_out = S^n + D(F, E) --------------------------------------------------------
-__device__ __forceinline__ double incr_cell(const Dev& D, int v, long long X, const long long* Xp) {
+// U_v^n + dt sum_d (F_d[X] - F_d[X + d]) / h_d (Eq. rk:increment-state), with dt / h_d folded
+// into the FMAs
+__device__ __forceinline__ double cell_new(const Dev& D, int v, long long X, const long long* Xp) {
   const long long N = D.N;
   const double* F0 = D.F + (0 * 5 + v) * N;
   const double* F1 = D.F + (1 * 5 + v) * N;
   const double* F2 = D.F + (2 * 5 + v) * N;
-  const double acc = fma(F0[X] - F0[Xp[0]], D.hinv[0],
-                         fma(F1[X] - F1[Xp[1]], D.hinv[1], (F2[X] - F2[Xp[2]]) * D.hinv[2]));
-  return D.dt * acc;
+  return fma(F0[X] - F0[Xp[0]], D.dth[0],
+             fma(F1[X] - F1[Xp[1]], D.dth[1], fma(F2[X] - F2[Xp[2]], D.dth[2], D.U0[v * N + X])));
 }
-__device__ __forceinline__ double incr_face(const Dev& D, int d, long long X, const long long* Xp) {
+// the updated field on the d-face of cell X (its lower face), by the discrete Stokes theorem
+// (Eq. rk:increment-bfield); Xp[a], Xp[c] = X + 1 along a, c
+__device__ __forceinline__ double face_new(const Dev& D, int d, long long X, const long long* Xp) {
   const long long N = D.N;
   const int a = (d + 1) % 3, c = (d + 2) % 3;
   const double* Ec = D.E + c * N;
   const double* Ea = D.E + a * N;
-  return D.dt * fma(Ec[X] - Ec[Xp[a]], D.hinv[a], (Ea[Xp[c]] - Ea[X]) * D.hinv[c]);
-}
-
-// the updated field on the d-face of cell X (its lower face); Xp[a], Xp[c] = X + 1 along a, c
-__device__ __forceinline__ double face_new(const Dev& D, int d, long long X, const long long* Xp) {
-  return D.B0[d][X] + incr_face(D, d, X, Xp);
+  return fma(Ec[X] - Ec[Xp[a]], D.dth[a], fma(Ea[Xp[c]] - Ea[X], D.dth[c], D.B0[d][X]));
 }
 // the updated state of cell X (5 conserved values, then its 3 lower faces), not yet stored
 __device__ __forceinline__ void update_vals(const Dev& D, long long X, const long long* Xp, double* out) {
   const long long N = D.N;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) out[v] = D.U0[v * N + X] + incr_cell(D, v, X, Xp);
+  for (int v = 0; v < 5; ++v) out[v] = cell_new(D, v, X, Xp);
 #pragma unroll
   for (int d = 0; d < 3; ++d) out[5 + d] = face_new(D, d, X, Xp);
 }
@@ -151,7 +149,7 @@ __device__ __forceinline__ bool invalid_vals(const Dev& D, const double* u, cons
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     fin = fin && finite_d(lo[d]) && finite_d(hi[d]);
-    bc[d] = 0.5 * (lo[d] + hi[d]);
+    bc[d] = halve(lo[d] + hi[d]);
   }
   if (!fin) return true;
   const double rho = u[0];
@@ -161,7 +159,7 @@ __device__ __forceinline__ bool invalid_vals(const Dev& D, const double* u, cons
     const double u0 = u[1] * rinv, u1 = u[2] * rinv, u2 = u[3] * rinv;
     const double u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
     const double b2s = fma(bc[0], bc[0], fma(bc[1], bc[1], bc[2] * bc[2]));
-    const double p = (D.gam - 1.0) * (u[4] - 0.5 * fma(rho, u2s, b2s));
+    const double p = (D.gam - 1.0) * (u[4] - halve(fma(rho, u2s, b2s)));
     if (!gt0(p)) return true;  // p <= 0 or NaN
   }
   return false;
@@ -321,7 +319,7 @@ __device__ __forceinline__ void fo_recompute_cell(const Dev& D, long long X) {
   bool cell = flagged(D, X);
   for (int d = 0; d < 3; ++d) cell = cell || flagged(D, Xp[d]) || flagged(D, Xm[d]);
   if (cell)
-    for (int v = 0; v < 5; ++v) D.Uout[v * N + X] = D.U0[v * N + X] + incr_cell(D, v, X, Xp);
+    for (int v = 0; v < 5; ++v) D.Uout[v * N + X] = cell_new(D, v, X, Xp);
   // e-edge at Y is masked if one of Y, Y-a, Y-c, Y-a-c is flagged
   auto edge_masked = [&](int e, long long Y) {
     const int a = (e + 1) % 3, c = (e + 2) % 3;
@@ -332,7 +330,7 @@ __device__ __forceinline__ void fo_recompute_cell(const Dev& D, long long X) {
     const int a = (d + 1) % 3, c = (d + 2) % 3;
     // the d-face at X is bounded by c-edges at X and X+a, and a-edges at X and X+c
     if (edge_masked(c, X) || edge_masked(c, Xp[a]) || edge_masked(a, X) || edge_masked(a, Xp[c]))
-      D.Bout[d][X] = D.B0[d][X] + incr_face(D, d, X, Xp);
+      D.Bout[d][X] = face_new(D, d, X, Xp);
   }
 }
 

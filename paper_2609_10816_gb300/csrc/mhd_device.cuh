@@ -145,6 +145,21 @@ __device__ __forceinline__ Dual sqrt_(Dual x) {
   return Dual(z ? 0.0 : x.v * q, z ? 0.0 : 0.5 * q * x.t);
 }
 
+// x / 2 exactly as the FP64 multiply by 0.5 rounds it (ties to even), on the integer pipe: one
+// less in the exponent above the smallest normal binade; below it (where a double is its bit
+// pattern times 2^-1074) the magnitude's integer is halved with ties to even; zero, infinity and
+// NaN pass through.
+__device__ __forceinline__ double halve(double x) {
+  const long long b = dbits(x);
+  const long long sign = b & (long long)0x8000000000000000ULL;
+  const long long mag = b & 0x7fffffffffffffffLL;
+  long long r;
+  if (mag >= (2LL << 52)) r = mag >= 0x7ff0000000000000LL ? mag : mag - (1LL << 52);
+  else r = (mag >> 1) + (mag & (mag >> 1) & 1);
+  return dfrom(r | sign);
+}
+__device__ __forceinline__ Dual halve(Dual x) { return Dual(halve(x.v), halve(x.t)); }
+
 // ------------------------------------------------------------------------------------------
 // Periodic line of points along one axis
 // ------------------------------------------------------------------------------------------
@@ -191,7 +206,7 @@ __device__ __forceinline__ T half_slope_mc(T dl, T dr) {
 template <class T>
 __device__ __forceinline__ T half_slope_minmod(T dl, T dr) {
   if (!same_sign(dl, dr)) return T(0.0);
-  return with_sign(0.5 * pmin(vabs(dl), vabs(dr)), dl);
+  return with_sign(halve(pmin(vabs(dl), vabs(dr))), dl);
 }
 
 template <int R> struct RecPLM {
@@ -371,7 +386,7 @@ __device__ __forceinline__ void phys_speed(const FaceStateT<T>& s, T bn, double 
   const T Sp = P + b2;
   T disc = fma(Sp, Sp, (-4.0 * bn2) * P);
   disc = pmax(disc, T(0.0));
-  o.cf2 = (0.5 * rcp(s.rho)) * (Sp + sqrt_(disc));
+  o.cf2 = halve(rcp(s.rho)) * (Sp + sqrt_(disc));
 }
 
 // Conserved vector and ideal-MHD flux of Eq. (mhd:conservation-laws) in the face frame, with e_tot
@@ -380,7 +395,7 @@ template <class T>
 __device__ __forceinline__ void phys_flux(const FaceStateT<T>& s, T bn, double gm1inv, PhysFluxT<T>& o) {
   const T bn2 = bn * bn;
   const T u2 = fma(s.u, s.u, fma(s.v, s.v, s.w * s.w));
-  const T e = fma(s.p, gm1inv, 0.5 * fma(s.rho, u2, o.b2));
+  const T e = fma(s.p, gm1inv, halve(fma(s.rho, u2, o.b2)));
   const T ub = fma(s.u, bn, fma(s.v, s.by, s.w * s.bz));
   const T mu = s.rho * s.u;
   o.U[0] = s.rho;

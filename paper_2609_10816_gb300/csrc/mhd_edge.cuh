@@ -225,8 +225,8 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
         const double o1c = xp[(4 + 2 * sI + sII) * N + X];
         const double o2a = sI ? hi[1 + sII] : lo[1 + sII];
         const double o2c = sI ? hi[3 + sII] : lo[3 + sII];
-        ua[qq] = 0.5 * (o1a + o2a);
-        uc[qq] = 0.5 * (o1c + o2c);
+        ua[qq] = halve(o1a + o2a);
+        uc[qq] = halve(o1c + o2c);
       }
       eLB = fma(-ua[0], bcL, uc[0] * baB);
       eRB = fma(-ua[1], bcR, uc[1] * baB);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
         const int sI = qq & 1, sII = qq >> 1;
         const double o1 = xp[(2 * sI + sII) * N + X];
         const double o2 = sI ? hi[1 + sII] : lo[1 + sII];
-        ec[qq] = 0.5 * (o1 + o2);
+        ec[qq] = halve(o1 + o2);
       }
       eLB = ec[0];
       eRB = ec[1];
@@ -253,7 +253,7 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
       const double j = (Bc[X] - Bc[Xa]) * D.hinv[a] - (Ba[X] - Ba[Xc]) * D.hinv[c];
       emf = fma(D.eta, j, emf);
     }
-    E[X] = D.combine ? 0.5 * (E[X] + emf) : emf;
+    E[X] = D.combine ? halve(E[X] + emf) : emf;
   }
 }
 

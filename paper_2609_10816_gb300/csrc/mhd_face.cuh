@@ -84,7 +84,7 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
     g[4] = f[4];
     if (D.combine) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) F[v * N + X] = 0.5 * (Fold[v] + g[v]);
+      for (int v = 0; v < 5; ++v) F[v * N + X] = halve(Fold[v] + g[v]);
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) F[v * N + X] = g[v];

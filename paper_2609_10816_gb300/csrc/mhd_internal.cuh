@@ -22,6 +22,7 @@ struct Dev {
   double hinv[3];
   double gam, gm1inv;
   double dt, eta;
+  double dth[3];        // dt / h_d
   int resistive;        // eta != 0
   int combine;          // stage 2: store (old + new) / 2 into fluxes and EMFs
   int fofc_criteria;    // bit 0 rho <= 0, bit 1 p <= 0

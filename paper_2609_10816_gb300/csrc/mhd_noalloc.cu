@@ -109,6 +109,7 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_config* cfg, const mhd_state* s
   D.gm1inv = 1.0 / (cfg->gamma - 1.0);
   D.fofc_criteria = fofc ? (cfg->fofc_criteria ? cfg->fofc_criteria : 3) : 0;
   D.dt = dt;
+  for (int d = 0; d < 3; ++d) D.dth[d] = dt * D.hinv[d];
   D.eta = eta;
   D.resistive = eta != 0.0;
   D.emf = emf;

@@ -205,8 +205,9 @@ class Context:
         return out[0], dict(zip(self.ADJ_CHECK_KINDS, out[1:]))
 
     def math_check(self, n: int = 1 << 22):
-        """Largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE."""
-        out = (ctypes.c_double * 3)()
+        """(largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE, bit
+        mismatches of the integer halving, of the integer quadrupling)."""
+        out = (ctypes.c_double * 5)()
         self._err(lib().mhd_math_check(self._h, int(n), out))
         return tuple(out)
 
