@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per GB300 (FP64, plain vs batched vs fwd+adjoint), % HBM roofline"
 UNIT = "cell-updates/s"
 
-# Roofline constants (see DESIGN.md): GB300 FP64 = 152 SMs x 2 DFMA/clk x 2 flops at 2070 MHz
+# Roofline constants: GB300 FP64 = 152 SMs x 2 DFMA/clk x 2 flops at 2070 MHz
 # (the recipe's unit counts and maximum clock; a DFMA microbenchmark measured 1.19 TFLOP/s at
 # ~1990 MHz). Algorithmic FP64 flops per face of the face sweep (reconstruction of 7 primitives
 # along the sweep + Riemann solve + Joule flux), counted by the oracle's op-counting scalar on a
@@ -35,11 +35,11 @@ UNIT = "cell-updates/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FLOPS_PER_FACE = {"ppm/hlld": 316.4, "plm_mc/hll": 249.0, "plm_mc/hlld": 430.9}
 FLOPS_PER_CELL_UPDATE = {"ppm/hlld": 2916.2, "plm_mc/hll": 2325.3, "plm_mc/hlld": 3385.3}
-HBM_PEAK_GBS = 6759.6  # MEASURED_PEAKS.json copy bandwidth
+HBM_PEAK_GBS = 6759.6  # measured copy bandwidth of this GPU model (STREAM-style copy)
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 687.9e6, "cells": 160**3, "src": "30bb96995d7b5da1"}}
+TRAFFIC = {"face": {"bytes_per_launch": 687.6e6, "cells": 160**3, "src": "ee70c79fa42ef125"}}
 
 
 # what the face sweep's machine code is compiled from: its kernel, the numerics and indexing

@@ -131,14 +131,6 @@ __device__ __forceinline__ void rec_scatter(const Dev& D, const double* arr, lon
     if (c != 0.0) atomicAdd(&out[Z[k]], c);
   }
 }
-template <int RC>
-__device__ __forceinline__ void rec_val(const Dev& D, const double* arr, long long m, int dir, double& aL,
-                                        double& aR) {
-  double q[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) q[k] = arr[shift2(D, m, dir, k - 2)];
-  recon_point<RC>(q, aL, aR);
-}
 
 // Reverse sweep of q26_edge_emf (the Q26 corner EMFs of Eq. q26 and the LD04 average of Eq. ld04):
 // g[k] = lam dE/d in[k] for in = (baB, baT, uaB, uaT, bcL, bcR, ucL, ucR, apa, ama, apc, amc).
@@ -207,15 +199,16 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
       continue;
     }
     const long long Xc = shift(D, X, c, -1), Xa = shift(D, X, a, -1);
-    double in[12], dummy;
-    rec_val<RC>(D, D.Bin[a], Xc, c, dummy, in[0]);          // b_a bottom = upper value of a-face X - c
-    rec_val<RC>(D, D.Bin[a], X, c, in[1], dummy);           // b_a top = lower value of a-face X
-    rec_val<RC>(D, D.Us + a * N, Xc, c, dummy, in[2]);      // u_a* bottom
-    rec_val<RC>(D, D.Us + a * N, X, c, in[3], dummy);       // u_a* top
-    rec_val<RC>(D, D.Bin[c], Xa, a, dummy, in[4]);          // b_c left
-    rec_val<RC>(D, D.Bin[c], X, a, in[5], dummy);           // b_c right
-    rec_val<RC>(D, D.Us + c * N, Xa, a, dummy, in[6]);      // u_c* left
-    rec_val<RC>(D, D.Us + c * N, X, a, in[7], dummy);       // u_c* right
+    // the eight reconstructed edge values as the forward edge sweeps formed them: b_a, u_a* bottom
+    // and top (Epart), b_c, u_c* left and right (EdgeC)
+    double in[12];
+    const double* pa = D.Epart + 4LL * e * N;
+    const double* pc = D.EdgeC + 4LL * e * N;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      in[k] = pa[k * N + X];
+      in[4 + k] = pc[k * N + X];
+    }
     const double* Apa = D.Ap + a * N;
     const double* Ama = D.Am + a * N;
     const double* Apc = D.Ap + c * N;

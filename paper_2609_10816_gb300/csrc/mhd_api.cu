@@ -402,9 +402,9 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   const long long N = ctx->base.N;
   cudaStream_t st = ctx->stream;
   // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
-  // lB0 3, lam2 8, the stage-1 input's P 8 and alpha+- / u* 9, and the forward face states of
-  // both stage inputs 2 x 42 (doubles per cell) + eta
-  const size_t nd = 226;
+  // lB0 3, lam2 8, the stage-1 input's P 8 and alpha+- / u* 9, the forward face states of both
+  // stage inputs 2 x 42, and their reconstructed edge values 12 + 2 x 12 (doubles per cell) + eta
+  const size_t nd = 262;
   if (!ctx->adj) {
     s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + 8) * sizeof(double)), "cudaMalloc of adjoint scratch");
     if (s != MHD_OK) { ctx->adj = nullptr; return s; }
@@ -429,6 +429,9 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* Apm0 = take(9);
   double* LR0 = take(42);
   double* LR1 = take(42);
+  double* Epart0 = take(12);
+  double* EdgeC0 = take(12);
+  double* EdgeC1 = take(12);
   double* lEta = q;
 
   mhd::Dev D = ctx->base;
@@ -463,7 +466,9 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   D0.Ap = Apm0;
   D0.Am = Apm0 + 3 * N;
   D0.Us = Apm0 + 6 * N;
-  D0.LR = LR0;  // the forward face states, which the stage-1 adjoint reads
+  D0.LR = LR0;  // the forward face and edge values, which the stage-1 adjoint reads
+  D0.Epart = Epart0;
+  D0.EdgeC = EdgeC0;
   run_stage(ctx, D0, sc);
 
   auto adj_dev = [&](const mhd::Dev& Ds, double* lU, double* lB) {
@@ -473,9 +478,11 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
     A.lU = lU; A.lB = lB; A.lEta = lEta;
     return A;
   };
-  auto recompute = [&](const mhd::Dev& Ds) {  // P, alpha+-, u* of the stage input
+  auto recompute = [&](const mhd::Dev& Ds) {  // P, alpha+-, u*, face and edge values of the stage input
     mhd::launch_prim(Ds, st);
     for (int dir = 0; dir < 3; ++dir) mhd::launch_face(Ds, dir, sc.recon, sc.rs, ctx->seg, st);
+    mhd::launch_edges_bt(Ds, sc.recon, ctx->seg, st);
+    mhd::launch_edges_lr(Ds, sc.recon, ctx->seg, st);
   };
   auto zero = [&](double* p, long long k) { return cudaMemsetAsync(p, 0, k * N * sizeof(double), st); };
 
@@ -484,6 +491,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   D1.Uin = ctx->U1;
   for (int d = 0; d < 3; ++d) D1.Bin[d] = ctx->B1[d];
   D1.LR = LR1;
+  D1.EdgeC = EdgeC1;
   recompute(D1);
   mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
   e = zero(lU1, 5);

@@ -107,7 +107,6 @@ __device__ __forceinline__ double face_new(const Dev& D, int d, long long X, con
 }
 // the updated state of cell X (5 conserved values, then its 3 lower faces), not yet stored
 __device__ __forceinline__ void update_vals(const Dev& D, long long X, const long long* Xp, double* out) {
-  const long long N = D.N;
 #pragma unroll
   for (int v = 0; v < 5; ++v) out[v] = cell_new(D, v, X, Xp);
 #pragma unroll

@@ -335,28 +335,6 @@ template <> struct Rec<REC_PPM> {
   }
 };
 
-// Point-wise form of the sweeps (for the adjoint kernels): lower and upper values of point m from
-// q[0..4] = values at m-2 .. m+2, with the same expressions (and therefore the same values and
-// branch decisions) as the sliding windows above.
-template <int R, class T>
-__device__ __forceinline__ void recon_point(const T* q, T& aL, T& aR) {
-  if (R == REC_PC) {
-    aL = q[2];
-    aR = q[2];
-  } else if (R == REC_PLM_MC || R == REC_PLM_MINMOD) {
-    const T dl = q[2] - q[1], dr = q[3] - q[2];
-    const T h = R == REC_PLM_MC ? half_slope_mc(dl, dr) : half_slope_minmod(dl, dr);
-    aL = q[2] - h;
-    aR = q[2] + h;
-  } else {
-    const T e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3];
-    const T d0 = vl_slope2(e0, e1), d1 = vl_slope2(e1, e2), d2 = vl_slope2(e2, e3);
-    aL = ppm_iface(q[1], e1, d0, d1);
-    aR = ppm_iface(q[2], e2, d1, d2);
-    ppm_mono(q[2], aL, aR);
-  }
-}
-
 // ------------------------------------------------------------------------------------------
 // Riemann problem on one face, in the face frame (n, t1, t2).
 // W = {rho, u_n, u_t1, u_t2, p, b_t1, b_t2}; bn = stored face field.

@@ -213,6 +213,13 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
     if (EMF == EMF_Q26) {
       // Eq. (q26) corners and Eq. (ld04), factored
       emf = q26_edge_emf(baB, baT, part[2 * N + X], part[3 * N + X], bcL, bcR, lo[1], hi[1], apa, ama, apc, amc);
+      if (D.EdgeC) {
+        double* ec = D.EdgeC + 4LL * e * N;
+        ec[X] = bcL;
+        ec[N + X] = bcR;
+        ec[2 * N + X] = lo[1];
+        ec[3 * N + X] = hi[1];
+      }
     } else if (EMF == EMF_FS18) {
       // Eq. (fs18-average): mean of the two reconstruction orders per corner, then Eq. (fs18).
       // order a-then-c partials: slot 2k' + ... = (u_a L:B,T, u_a R:B,T, u_c L:B,T, u_c R:B,T)

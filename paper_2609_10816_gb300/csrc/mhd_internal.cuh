@@ -54,6 +54,8 @@ struct Dev {
                   // stage's input, whose prim pass then runs only if flux correction changed it)
   double* LR;     // when set, the face sweep also stores its reconstructed left (7) and right (7)
                   // face states here, [3][14][N] (for the adjoint)
+  double* EdgeC;  // when set, the c-face edge sweep (Q26) also stores its reconstructed b_c and
+                  // u_c* left / right values here, [3][4][N] (for the adjoint)
   unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
   // work-list cursors of the dynamically scheduled sweeps ([dir] face, [3 + e] edge_bt,
   // [6 + e] edge_lr), zeroed before every stage; NULL: one segment per thread, no cursor
