@@ -144,8 +144,11 @@ mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_stat
  * one third-order Newton correction) from CUDA's IEEE 1/x, 1/sqrt(x) and sqrt(x); on n raw bit
  * patterns (subnormal, smallest, largest and non-finite binades among them), max_rel_err[3] and
  * [4] receive how many times the integer-pipe halving and quadrupling differ in any bit from the
- * FP64 multiplies by 0.5 and 4 (0 expected). max_rel_err holds 5 doubles. Synchronous. The
- * paper has no counterpart. */
+ * FP64 multiplies by 0.5 and 4, and max_rel_err[5] on n pairs of non-NaN doubles (zeros,
+ * subnormals, extreme binades and infinities among them) how many times an integer-pipe sign
+ * test, comparison, min/max, |x|, sign copy or sign flip disagrees with the IEEE operation (0
+ * expected for all three; -0 and +0 are ordered -0 < +0 by the kernels' comparisons, which the
+ * check allows). max_rel_err holds 6 doubles. Synchronous. The paper has no counterpart. */
 mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
 
 /* Self-check of the adjoint's reverse sweep through the face solve (the Riemann solver of

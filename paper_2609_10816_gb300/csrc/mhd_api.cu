@@ -558,18 +558,17 @@ mhd_status mhd_math_check(mhd_ctx* ctx, long long n, double* max_rel_err) {
   ctx->err.clear();
   if (!max_rel_err || n < 1 || n > (1LL << 40)) return fail(ctx, MHD_ERR_ARG, "need 1 <= n <= 2^40 and an output");
   const mhd::Dev& D = ctx->base;
-  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 5 * sizeof(unsigned long long), ctx->stream),
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 6 * sizeof(unsigned long long), ctx->stream),
                             "cudaMemsetAsync");
   if (s != MHD_OK) return s;
   mhd::launch_math_check(n, D.counters + 2, ctx->stream);
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
-  unsigned long long h[5] = {0, 0, 0, 0, 0};
-  s = read_counters(ctx, h, 5);
+  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+  s = read_counters(ctx, h, 6);
   if (s != MHD_OK) return s;
   for (int k = 0; k < 3; ++k) std::memcpy(&max_rel_err[k], &h[k], sizeof(double));
-  max_rel_err[3] = (double)h[3];
-  max_rel_err[4] = (double)h[4];
+  for (int k = 3; k < 6; ++k) max_rel_err[k] = (double)h[k];
   return MHD_OK;
 }
 

@@ -145,6 +145,45 @@ __global__ void __launch_bounds__(256) k_math_check(long long n, unsigned long l
     if (hbad) atomicAdd(out + 3, 1ull);
     if (fbad) atomicAdd(out + 4, 1ull);
   }
+  // the integer-pipe predicates, min/max and sign operations against IEEE comparisons and
+  // operations on pairs of non-NaN doubles (zeros, subnormals, the extreme binades and infinities
+  // forced in often)
+  if (i < n) {
+    auto draw = [](unsigned long long z) {
+      z ^= z >> 31;
+      z *= 0x94D049BB133111EBull;
+      z ^= z >> 30;
+      long long b = (long long)(z & 0x800fffffffffffffULL);
+      const int k = (int)((z >> 52) & 7);
+      long long ex = (long long)((z >> 20) % 2047);  // never 2047 here: no NaN
+      if (k == 0) ex = 0;                             // subnormal (or zero)
+      if (k == 1) { ex = 0; b &= (long long)0x8000000000000000ULL; }  // +-0
+      if (k == 2) { ex = 2047; b &= (long long)0x8000000000000000ULL; }  // +-inf
+      if (k == 3) ex = (long long)((z >> 40) & 1) ? 1 : 2046;
+      return dfrom(b | (ex << 52));
+    };
+    const unsigned long long s0 = (unsigned long long)(i + 2 * n) * 0x9E3779B97F4A7C15ull;
+    const double x = draw(s0 + 0x2545F4914F6CDD1Dull);
+    const double y = (s0 & 0x300) == 0 ? x : draw(s0 ^ 0xDA942042E4DD58B5ull);  // ties now and then
+    int bad = 0;
+    bad |= gt0(x) != (x > 0.0);
+    bad |= lt0(x) != (x < 0.0);
+    bad |= ge0(x) != (x >= 0.0);
+    bad |= le0(x) != (x <= 0.0);
+    bad |= is_zero(x) != (x == 0.0);
+    bad |= same_sign(x, y) != ((x > 0.0 && y > 0.0) || (x < 0.0 && y < 0.0));
+    if (!(x == 0.0 && y == 0.0)) bad |= vgt(x, y) != (x > y);  // -0 orders just below +0
+    bad |= vmax(x, y) != (x >= y ? x : y);
+    bad |= vmin(x, y) != (x <= y ? x : y);
+    const double ax = fabs(x), ay = fabs(y);
+    bad |= dbits(vabs(x)) != dbits(ax);
+    bad |= pmax(ax, ay) != (ax >= ay ? ax : ay);
+    bad |= pmin(ax, ay) != (ax <= ay ? ax : ay);
+    bad |= dbits(with_sign(x, y)) != dbits(copysign(x, y));
+    bad |= dbits(neg_if(true, x)) != dbits(x * -1.0);
+    bad |= dbits(neg_if(false, x)) != dbits(x);
+    if (bad) atomicAdd(out + 5, 1ull);
+  }
 }
 
 void launch_math_check(long long n, unsigned long long* out, cudaStream_t st) {

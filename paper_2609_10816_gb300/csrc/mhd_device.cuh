@@ -22,9 +22,28 @@ enum { EMF_Q26 = 0, EMF_FS18 = 1, EMF_B25A = 2 };
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double dfrom(long long b) { return __longlong_as_double(b); }
+// Bitwise operations on bit patterns as inline PTX: written in C++, a mask of the sign bit is
+// recognised as |x|, copysign, -x or a comparison with zero and issued to the FP64 pipe.
+__device__ __forceinline__ long long band(long long a, long long b) {
+  long long r;
+  asm("and.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ long long bor(long long a, long long b) {
+  long long r;
+  asm("or.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ long long bxor(long long a, long long b) {
+  long long r;
+  asm("xor.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+constexpr long long kMag = 0x7fffffffffffffffLL;
+constexpr long long kSign = (long long)0x8000000000000000ULL;
 __device__ __forceinline__ long long okey(double x) {
   const long long b = dbits(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+  return bxor(b, band(b >> 63, kMag));
 }
 // max/min return the first argument on ties (as in the method's tie rule).
 __device__ __forceinline__ double vmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
@@ -32,27 +51,33 @@ __device__ __forceinline__ double vmin(double a, double b) { return okey(a) <= o
 // for a, b >= 0 (or +-0) the raw bit pattern orders like the value
 __device__ __forceinline__ double pmax(double a, double b) { return dbits(a) >= dbits(b) ? a : b; }
 __device__ __forceinline__ double pmin(double a, double b) { return dbits(a) <= dbits(b) ? a : b; }
-__device__ __forceinline__ double vabs(double x) { return dfrom(dbits(x) & 0x7fffffffffffffffLL); }
+__device__ __forceinline__ double vabs(double x) { return dfrom(band(dbits(x), kMag)); }
 __device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }   // x > 0
-__device__ __forceinline__ bool lt0(double x) { return dbits(-x) > 0; }  // x < 0 (not -0)
+// x < 0 (not -0): sign bit set and a non-zero magnitude, one unsigned compare (forming -x
+// instead would cost an FP64 issue slot)
+__device__ __forceinline__ bool lt0(double x) { return (unsigned long long)dbits(x) > 0x8000000000000000ULL; }
 __device__ __forceinline__ bool ge0(double x) { return okey(x) >= -1; }  // x >= 0 (either zero)
 __device__ __forceinline__ bool le0(double x) { return !gt0(x); }
 __device__ __forceinline__ bool vgt(double a, double b) { return okey(a) > okey(b); }
-__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) & 0x7fffffffffffffffLL) == 0; }
+__device__ __forceinline__ bool is_zero(double x) { return band(dbits(x), kMag) == 0; }
 // strictly of the same sign, both non-zero
 __device__ __forceinline__ bool same_sign(double a, double b) {
   return (gt0(a) && gt0(b)) || (lt0(a) && lt0(b));
 }
 // |m| carrying the sign of s
 __device__ __forceinline__ double with_sign(double m, double s) {
-  return dfrom((dbits(m) & 0x7fffffffffffffffLL) | (dbits(s) & (long long)0x8000000000000000ULL));
+  return dfrom(bor(band(dbits(m), kMag), band(dbits(s), kSign)));
 }
 // sgn(x) in {-1, 0, +1} as a double (bit construction, no FP64 op)
 __device__ __forceinline__ double sgnd(double x) {
   return gt0(x) ? 1.0 : (lt0(x) ? -1.0 : 0.0);
 }
+// x with its sign flipped when neg, on the integer pipe (the value of x * -1)
+__device__ __forceinline__ double neg_if(bool neg, double x) {
+  return dfrom(bxor(dbits(x), neg ? kSign : 0LL));
+}
 __device__ __forceinline__ bool finite_d(double x) {
-  return ((dbits(x) >> 52) & 0x7ff) != 0x7ff;
+  return band(dbits(x), 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
 // Reciprocal, reciprocal square root and square root without the IEEE divide/sqrt sequences
 // (which cost several FP64 issue slots each). The hardware's approximate reciprocal (about
@@ -151,14 +176,15 @@ __device__ __forceinline__ Dual sqrt_(Dual x) {
 // NaN pass through.
 __device__ __forceinline__ double halve(double x) {
   const long long b = dbits(x);
-  const long long sign = b & (long long)0x8000000000000000ULL;
-  const long long mag = b & 0x7fffffffffffffffLL;
+  const long long sign = band(b, kSign);
+  const long long mag = band(b, kMag);
   long long r;
   if (mag >= (2LL << 52)) r = mag >= 0x7ff0000000000000LL ? mag : mag - (1LL << 52);
   else r = (mag >> 1) + (mag & (mag >> 1) & 1);
-  return dfrom(r | sign);
+  return dfrom(bor(r, sign));
 }
 __device__ __forceinline__ Dual halve(Dual x) { return Dual(halve(x.v), halve(x.t)); }
+__device__ __forceinline__ Dual neg_if(bool neg, Dual x) { return Dual(neg_if(neg, x.v), neg_if(neg, x.t)); }
 
 // ------------------------------------------------------------------------------------------
 // Periodic line of points along one axis
@@ -276,7 +302,7 @@ enum { PPM_FLAT = 0, PPM_FIX_L = 1, PPM_FIX_R = 2, PPM_KEEP = 3 };
 // which constraint applies for s1 = aR - a, s2 = a - aL
 __device__ __forceinline__ int ppm_mono_case(double s1, double s2) {
   if (!same_sign(s1, s2)) return PPM_FLAT;                        // a is an extremum
-  const long long m1 = dbits(s1) & 0x7fffffffffffffffLL, m2 = dbits(s2) & 0x7fffffffffffffffLL;
+  const long long m1 = band(dbits(s1), kMag), m2 = band(dbits(s2), kMag);
   if (m2 > twice_bits(m1)) return PPM_FIX_L;                        // aL = 3a - 2aR = a - 2 s1
   if (twice_bits(m2) < m1) return PPM_FIX_R;                        // aR = 3a - 2aL = a + 2 s2
   return PPM_KEEP;
@@ -362,7 +388,7 @@ __device__ __forceinline__ void phys_speed(const FaceStateT<T>& s, T bn, double 
   // needs no 1/rho, which enters once at the end
   const T P = gam * s.p;
   const T Sp = P + b2;
-  T disc = fma(Sp, Sp, (-4.0 * bn2) * P);
+  T disc = fma(Sp, Sp, -(times4(bn2) * P));  // 4 bn^2 exactly, on the integer pipe
   disc = pmax(disc, T(0.0));
   o.cf2 = halve(rcp(s.rho)) * (Sp + sqrt_(disc));
 }
@@ -509,23 +535,24 @@ __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T
   const T bzsL = left ? a.bzs : b.bzs, bzsR = left ? b.bzs : a.bzs;
   const T iL = left ? isqa : isqb, iR = left ? isqb : isqa;
   const T sqL = rsL * iL, sqR = rsR * iR;
-  const double sb = sgnd(bn);
+  // sgn(b_n) is +-1 here (the double-star branch needs b_n != 0: with b_n = 0, S*_side = S_M),
+  // so the products by it are sign flips
+  const bool nb = lt0(bn);
   const T inv = rcp(sqL + sqR);
-  const T vss = fma(sqL, vsL, fma(sqR, vsR, (bysR - bysL) * sb)) * inv;
-  const T wss = fma(sqL, wsL, fma(sqR, wsR, (bzsR - bzsL) * sb)) * inv;
+  const T vss = fma(sqL, vsL, fma(sqR, vsR, neg_if(nb, bysR - bysL))) * inv;
+  const T wss = fma(sqL, wsL, fma(sqR, wsR, neg_if(nb, bzsR - bzsL))) * inv;
   const T sLR = sqL * sqR;
-  const T byss = fma(sqL, bysR, fma(sqR, bysL, sLR * (vsR - vsL) * sb)) * inv;
-  const T bzss = fma(sqL, bzsR, fma(sqR, bzsL, sLR * (wsR - wsL) * sb)) * inv;
+  const T byss = fma(sqL, bysR, fma(sqR, bysL, neg_if(nb, sLR * (vsR - vsL)))) * inv;
+  const T bzss = fma(sqL, bzsR, fma(sqR, bzsL, neg_if(nb, sLR * (wsR - wsL)))) * inv;
   const T vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
   const T sq = left ? sqL : sqR;
-  const double sgn_side = left ? -1.0 : 1.0;
   const T vbs = a.vbs;
   T Uss[5];
   Uss[0] = a.rs;
   Uss[1] = a.rs * SM;
   Uss[2] = a.rs * vss;
   Uss[3] = a.rs * wss;
-  Uss[4] = fma(sgn_side * sq, (vbs - vbss) * sb, a.es);
+  Uss[4] = fma(neg_if(left != nb, sq), vbs - vbss, a.es);  // (-1 on the left) sq (vbs - vbss) sgn(b_n)
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = fma(Ss, Uss[v] - Usa[v], Fs[v]);
 }

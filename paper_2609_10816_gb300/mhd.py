@@ -206,8 +206,9 @@ class Context:
 
     def math_check(self, n: int = 1 << 22):
         """(largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE, bit
-        mismatches of the integer halving, of the integer quadrupling)."""
-        out = (ctypes.c_double * 5)()
+        mismatches of the integer halving, of the integer quadrupling, disagreements of the
+        integer-pipe comparisons and sign operations with IEEE)."""
+        out = (ctypes.c_double * 6)()
         self._err(lib().mhd_math_check(self._h, int(n), out))
         return tuple(out)
 

@@ -140,6 +140,7 @@ def test_max_dt_and_divb(gpu_lib):
 def test_fast_reciprocal_and_sqrt_against_ieee(gpu_lib):
     """The kernels' reciprocal / rsqrt / sqrt stay within a few ulp of CUDA's IEEE results."""
     ctx = mhd.Context((4, 4, 4), (1, 1, 1))
-    er, es, eq, hbad, fbad = ctx.math_check(1 << 22)
+    er, es, eq, hbad, fbad, pbad = ctx.math_check(1 << 22)
     assert er <= 4 * 2.0**-53 and es <= 4 * 2.0**-53 and eq <= 4 * 2.0**-53, (er, es, eq)
     assert hbad == 0 and fbad == 0, (hbad, fbad)  # halving / quadrupling bit-exact
+    assert pbad == 0, pbad  # sign tests, comparisons, min/max, |x|, sign copy / flip
