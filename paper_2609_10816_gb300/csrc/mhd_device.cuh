@@ -22,28 +22,37 @@ enum { EMF_Q26 = 0, EMF_FS18 = 1, EMF_B25A = 2 };
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double dfrom(long long b) { return __longlong_as_double(b); }
-// Bitwise operations on bit patterns as inline PTX: written in C++, a mask of the sign bit is
-// recognised as |x|, copysign, -x or a comparison with zero and issued to the FP64 pipe.
-__device__ __forceinline__ long long band(long long a, long long b) {
-  long long r;
-  asm("and.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+// The sign-bit operations below are inline PTX on the high 32-bit word, with the masks as
+// immediates: written in C++, a mask of the sign bit is recognised as |x|, copysign, -x or a test
+// against zero and issued to the FP64 pipe, and a 64-bit mask constant would hold two registers.
+__device__ __forceinline__ double vabs(double x) {
+  double r;
+  asm("{\n\t.reg .b32 l, h;\n\tmov.b64 {l, h}, %1;\n\tand.b32 h, h, 0x7FFFFFFF;\n\tmov.b64 %0, {l, h};\n\t}"
+      : "=d"(r) : "d"(x));
   return r;
 }
-__device__ __forceinline__ long long bor(long long a, long long b) {
-  long long r;
-  asm("or.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+// |m| carrying the sign of s
+__device__ __forceinline__ double with_sign(double m, double s) {
+  double r;
+  asm("{\n\t.reg .b32 l, h, t, g;\n\tmov.b64 {l, h}, %1;\n\tmov.b64 {t, g}, %2;\n\t"
+      "and.b32 h, h, 0x7FFFFFFF;\n\tand.b32 g, g, 0x80000000;\n\tor.b32 h, h, g;\n\tmov.b64 %0, {l, h};\n\t}"
+      : "=d"(r) : "d"(m), "d"(s));
   return r;
 }
-__device__ __forceinline__ long long bxor(long long a, long long b) {
-  long long r;
-  asm("xor.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+// x with its sign flipped when neg (the value of x * -1)
+__device__ __forceinline__ double neg_if(bool neg, double x) {
+  double r;
+  asm("{\n\t.reg .b32 l, h;\n\tmov.b64 {l, h}, %1;\n\txor.b32 h, h, %2;\n\tmov.b64 %0, {l, h};\n\t}"
+      : "=d"(r) : "d"(x), "r"(neg ? 0x80000000u : 0u));
   return r;
 }
-constexpr long long kMag = 0x7fffffffffffffffLL;
-constexpr long long kSign = (long long)0x8000000000000000ULL;
+// bit pattern of |x|
+__device__ __forceinline__ long long mag_bits(double x) { return dbits(vabs(x)); }
+// total-order key: for non-NaN doubles it orders like the value, with -0 just below +0 (the
+// magnitude bits of a negative pattern are flipped)
 __device__ __forceinline__ long long okey(double x) {
   const long long b = dbits(x);
-  return bxor(b, band(b >> 63, kMag));
+  return b ^ (long long)((unsigned long long)(b >> 63) >> 1);
 }
 // max/min return the first argument on ties (as in the method's tie rule).
 __device__ __forceinline__ double vmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
@@ -51,7 +60,6 @@ __device__ __forceinline__ double vmin(double a, double b) { return okey(a) <= o
 // for a, b >= 0 (or +-0) the raw bit pattern orders like the value
 __device__ __forceinline__ double pmax(double a, double b) { return dbits(a) >= dbits(b) ? a : b; }
 __device__ __forceinline__ double pmin(double a, double b) { return dbits(a) <= dbits(b) ? a : b; }
-__device__ __forceinline__ double vabs(double x) { return dfrom(band(dbits(x), kMag)); }
 __device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }   // x > 0
 // x < 0 (not -0): sign bit set and a non-zero magnitude, one unsigned compare (forming -x
 // instead would cost an FP64 issue slot)
@@ -59,25 +67,17 @@ __device__ __forceinline__ bool lt0(double x) { return (unsigned long long)dbits
 __device__ __forceinline__ bool ge0(double x) { return okey(x) >= -1; }  // x >= 0 (either zero)
 __device__ __forceinline__ bool le0(double x) { return !gt0(x); }
 __device__ __forceinline__ bool vgt(double a, double b) { return okey(a) > okey(b); }
-__device__ __forceinline__ bool is_zero(double x) { return band(dbits(x), kMag) == 0; }
+__device__ __forceinline__ bool is_zero(double x) { return mag_bits(x) == 0; }
 // strictly of the same sign, both non-zero
 __device__ __forceinline__ bool same_sign(double a, double b) {
   return (gt0(a) && gt0(b)) || (lt0(a) && lt0(b));
-}
-// |m| carrying the sign of s
-__device__ __forceinline__ double with_sign(double m, double s) {
-  return dfrom(bor(band(dbits(m), kMag), band(dbits(s), kSign)));
 }
 // sgn(x) in {-1, 0, +1} as a double (bit construction, no FP64 op)
 __device__ __forceinline__ double sgnd(double x) {
   return gt0(x) ? 1.0 : (lt0(x) ? -1.0 : 0.0);
 }
-// x with its sign flipped when neg, on the integer pipe (the value of x * -1)
-__device__ __forceinline__ double neg_if(bool neg, double x) {
-  return dfrom(bxor(dbits(x), neg ? kSign : 0LL));
-}
 __device__ __forceinline__ bool finite_d(double x) {
-  return band(dbits(x), 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+  return (mag_bits(x) >> 52) != 0x7ff;
 }
 // Reciprocal, reciprocal square root and square root without the IEEE divide/sqrt sequences
 // (which cost several FP64 issue slots each). The hardware's approximate reciprocal (about
@@ -175,13 +175,11 @@ __device__ __forceinline__ Dual sqrt_(Dual x) {
 // pattern times 2^-1074) the magnitude's integer is halved with ties to even; zero, infinity and
 // NaN pass through.
 __device__ __forceinline__ double halve(double x) {
-  const long long b = dbits(x);
-  const long long sign = band(b, kSign);
-  const long long mag = band(b, kMag);
+  const long long mag = mag_bits(x);
   long long r;
   if (mag >= (2LL << 52)) r = mag >= 0x7ff0000000000000LL ? mag : mag - (1LL << 52);
   else r = (mag >> 1) + (mag & (mag >> 1) & 1);
-  return dfrom(bor(r, sign));
+  return with_sign(dfrom(r), x);
 }
 __device__ __forceinline__ Dual halve(Dual x) { return Dual(halve(x.v), halve(x.t)); }
 __device__ __forceinline__ Dual neg_if(bool neg, Dual x) { return Dual(neg_if(neg, x.v), neg_if(neg, x.t)); }
@@ -302,7 +300,7 @@ enum { PPM_FLAT = 0, PPM_FIX_L = 1, PPM_FIX_R = 2, PPM_KEEP = 3 };
 // which constraint applies for s1 = aR - a, s2 = a - aL
 __device__ __forceinline__ int ppm_mono_case(double s1, double s2) {
   if (!same_sign(s1, s2)) return PPM_FLAT;                        // a is an extremum
-  const long long m1 = band(dbits(s1), kMag), m2 = band(dbits(s2), kMag);
+  const long long m1 = mag_bits(s1), m2 = mag_bits(s2);
   if (m2 > twice_bits(m1)) return PPM_FIX_L;                        // aL = 3a - 2aR = a - 2 s1
   if (twice_bits(m2) < m1) return PPM_FIX_R;                        // aR = 3a - 2aL = a + 2 s2
   return PPM_KEEP;

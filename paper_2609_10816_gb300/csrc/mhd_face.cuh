@@ -49,7 +49,16 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
     r[v].init(w);
   }
   const double* bnA = D.Bin[dir];
-  double* F = D.F + 5LL * dir * N;
+  // flux slots in the face frame (n, t1, t2): mass, the three momenta, energy
+  double* Fs[5];
+  {
+    double* F = D.F + 5LL * dir * N;
+    Fs[0] = F;
+    Fs[1] = F + (1 + dir) * N;
+    Fs[2] = F + (1 + a) * N;
+    Fs[3] = F + (1 + c) * N;
+    Fs[4] = F + 4 * N;
+  }
   const bool fs18 = D.emf == EMF_FS18;
   for (int m = m0; m < m1; ++m) {
     const long long X = ln.at(m);
@@ -57,7 +66,7 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
     double Fold[5];  // stage 2: the stage-1 flux, loaded before the solve so its latency is hidden
     if (D.combine) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Fold[v] = F[v * N + X];
+      for (int v = 0; v < 5; ++v) Fold[v] = Fs[v][X];
     }
     double Lv[7], Rv[7];
 #pragma unroll
@@ -75,19 +84,12 @@ __device__ __forceinline__ void face_seg(const Dev& D, int dir, const Line& ln, 
     double f[5], ap, am, us;
     riemann<RS>(sl, sr, bnA[X], D.gam, D.gm1inv, f, ap, am, us);
     if (D.resistive) f[4] += joule_flux(D, dir, X);
-    // face frame (n, t1, t2) -> global momentum slots
-    double g[5];
-    g[0] = f[0];
-    g[1 + dir] = f[1];
-    g[1 + a] = f[2];
-    g[1 + c] = f[3];
-    g[4] = f[4];
     if (D.combine) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) F[v * N + X] = halve(Fold[v] + g[v]);
+      for (int v = 0; v < 5; ++v) Fs[v][X] = halve(Fold[v] + f[v]);
     } else {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) F[v * N + X] = g[v];
+      for (int v = 0; v < 5; ++v) Fs[v][X] = f[v];
     }
     D.Ap[dir * N + X] = ap;
     D.Am[dir * N + X] = am;
