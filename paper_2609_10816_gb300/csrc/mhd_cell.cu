@@ -27,20 +27,19 @@ __global__ void __launch_bounds__(256) k_flag(Dev D) {
   const bool f = X < D.N ? flag_cell(D, X) : false;
   count_flags(D, f);
 }
+// First-order fix-up passes: grid-stride loops over a grid of two waves, so that a stage with
+// no flagged cell (the usual case) costs a few microseconds of early exits
 __global__ void __launch_bounds__(128) k_fo_faces(Dev D) {
   if (D.counters[D.stage] == 0) return;
-  const long long X = cell_id();
-  if (X < D.N) fo_faces_cell(D, X);
+  for (long long X = cell_id(); X < D.N; X += (long long)gridDim.x * blockDim.x) fo_faces_cell(D, X);
 }
 __global__ void __launch_bounds__(128) k_fo_edges(Dev D) {
   if (D.counters[D.stage] == 0) return;
-  const long long X = cell_id();
-  if (X < D.N) fo_edges_cell(D, X);
+  for (long long X = cell_id(); X < D.N; X += (long long)gridDim.x * blockDim.x) fo_edges_cell(D, X);
 }
 __global__ void __launch_bounds__(128) k_fo_recompute(Dev D) {
   if (D.counters[D.stage] == 0) return;
-  const long long X = cell_id();
-  if (X < D.N) fo_recompute_cell(D, X);
+  for (long long X = cell_id(); X < D.N; X += (long long)gridDim.x * blockDim.x) fo_recompute_cell(D, X);
 }
 
 // ---- reductions -----------------------------------------------------------------------------
@@ -199,9 +198,12 @@ void launch_prim_if_flagged(const Dev& d, int prev_stage, cudaStream_t st) {
   k_prim_if_flagged<<<blocks_for(d.N, 256), 256, 0, st>>>(d, prev_stage);
 }
 void launch_fofc(const Dev& d, cudaStream_t st) {
-  k_fo_faces<<<blocks_for(d.N, 128), 128, 0, st>>>(d);
-  k_fo_edges<<<blocks_for(d.N, 128), 128, 0, st>>>(d);
-  k_fo_recompute<<<blocks_for(d.N, 128), 128, 0, st>>>(d);
+  auto grid = [&](const void* k) {
+    return (unsigned)std::min((long long)blocks_for(d.N, 128), 2LL * resident_blocks(k, 128));
+  };
+  k_fo_faces<<<grid((const void*)k_fo_faces), 128, 0, st>>>(d);
+  k_fo_edges<<<grid((const void*)k_fo_edges), 128, 0, st>>>(d);
+  k_fo_recompute<<<grid((const void*)k_fo_recompute), 128, 0, st>>>(d);
 }
 void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st) {
   const long long cap = 2LL * resident_blocks((const void*)k_maxspeed, 256);  // two waves of blocks
