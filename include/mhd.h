@@ -90,8 +90,24 @@ void mhd_destroy(mhd_ctx *ctx);
 mhd_status mhd_step(mhd_ctx *ctx, const mhd_state *state, double dt, int scheme, double eta);
 
 /* Largest stable step (Sec. 2.4, Eq. resistivity:cfl): dt = cfl * dx_min / max over cells of
- * max(max_d (|u_d| + c_fm,d) dx_min / dx_d, 2 eta / dx_min). Synchronous (reads one double). */
+ * max(max_d (|u_d| + c_fm,d) dx_min / dx_d, 2 eta / dx_min). Synchronous (reads one double).
+ * MHD_ERR_NONFINITE when a cell holds a value that is not finite, or the largest speed is zero or
+ * infinite (a speed that is not a number, which a cell with p < 0 or rho <= 0 can give, is passed
+ * over). */
 mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double eta, double *dt_out);
+
+/* mhd_max_dt followed by mhd_step without the host in between: the CFL reduction, dt (the same
+ * formula and value as mhd_max_dt's) and dt / dx_d stay in the context's device memory and the
+ * step's kernels read them there, so consecutive calls queue on the stream without a
+ * synchronisation (and a sequence of them can be recorded in a CUDA graph). cfl > 0 and eta >= 0
+ * finite. Where mhd_max_dt would report MHD_ERR_NONFINITE, the step runs with dt = 0 (the state
+ * is then unchanged wherever its fluxes are finite) and mhd_last_dt reports MHD_ERR_NONFINITE.
+ * Asynchronous. */
+mhd_status mhd_step_cfl(mhd_ctx *ctx, const mhd_state *state, double cfl, int scheme, double eta);
+
+/* The dt of the last mhd_step_cfl on this context (0 before any). Synchronous (reads two
+ * doubles); MHD_ERR_NONFINITE when that step found no finite, positive signal speed. */
+mhd_status mhd_last_dt(mhd_ctx *ctx, double *dt_out);
 
 /* Discrete divergence diagnostic (Sec. 2.1; Sec. 4.6 validation): max over cells of
  * |sum_d (b_d(+1/2) - b_d(-1/2)) / dx_d| and max over faces of |b_d|. Synchronous. */
@@ -111,7 +127,7 @@ enum {
   MHD_K_UPDATE = 4,    /* flux divergence and CT update */
   MHD_K_FLAG = 5,      /* validity flags */
   MHD_K_FOFC = 6,      /* first-order flux correction, 3 launches per stage (exit early if no flag) */
-  MHD_K_MAXSPEED = 7,  /* CFL reduction */
+  MHD_K_MAXSPEED = 7,  /* CFL reduction (and, in mhd_step_cfl, the dt kernel) */
   MHD_K_DIVB = 8,      /* divergence reduction */
   MHD_K_EXTRA = 9,     /* scheme-specific extras (FS18 / B25a sweeps) */
   MHD_K_COUNT = 16

@@ -19,6 +19,7 @@ struct mhd_ctx {
   size_t scratch_bytes;
   double* U1;
   double* B1[3];
+  double* dtbuf;  // device: dt, dt / h_d and an error flag of the last mhd_step_cfl
   int seg;
   std::string err;
   // profiling: launch counts per kernel class, and (when enabled) event pairs per launch
@@ -207,7 +208,8 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   D.EfB = take(6);
   D.counters = (unsigned long long*)q;  // 8 counters, then the sweeps' work cursors
   D.work = D.counters + 8;
-  D.flag = (unsigned char*)(q + 8 + 16);
+  c->dtbuf = q + 8 + 16;                  // dt, dt / h_d and an error flag of mhd_step_cfl
+  D.flag = (unsigned char*)(q + 8 + 16 + 8);
   e = cudaMemsetAsync(p, 0, bytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -259,20 +261,10 @@ mhd_status mhd_profile_read(mhd_ctx* ctx, double* total_ms, long long* launches,
   return MHD_OK;
 }
 
-mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme, double eta) {
-  if (!ctx) return MHD_ERR_ARG;
-  ctx->err.clear();
-  if (!state_ok(state)) return fail(ctx, MHD_ERR_ARG, "state has a NULL array");
-  if (!(dt > 0) || !(dt < 1e300)) return fail(ctx, MHD_ERR_ARG, "dt must be finite and > 0");
-  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
-  Decoded sc;
-  mhd_status s = decode(ctx, scheme, sc);
-  if (s != MHD_OK) return s;
-
-  mhd::Dev D = ctx->base;
+// The two stages and the copy-back of one step; D carries dt / h_d (by value or in device memory).
+static mhd_status advance(mhd_ctx* ctx, const mhd_state* state, mhd::Dev D, const Decoded& sc, double eta) {
   const long long N = D.N;
-  D.dt = dt;
-  for (int d = 0; d < 3; ++d) D.dth[d] = dt * D.hinv[d];
+  mhd_status s;
   D.eta = eta;
   D.resistive = eta != 0.0;
   D.emf = sc.emf;
@@ -313,6 +305,63 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
                    "cudaMemcpyAsync");
     if (s != MHD_OK) return s;
   }
+  return MHD_OK;
+}
+
+mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme, double eta) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state)) return fail(ctx, MHD_ERR_ARG, "state has a NULL array");
+  if (!(dt > 0) || !(dt < 1e300)) return fail(ctx, MHD_ERR_ARG, "dt must be finite and > 0");
+  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
+  Decoded sc;
+  mhd_status s = decode(ctx, scheme, sc);
+  if (s != MHD_OK) return s;
+  mhd::Dev D = ctx->base;
+  D.dt = dt;
+  for (int d = 0; d < 3; ++d) D.dth[d] = dt * D.hinv[d];
+  return advance(ctx, state, D, sc, eta);
+}
+
+mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int scheme, double eta) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state)) return fail(ctx, MHD_ERR_ARG, "state has a NULL array");
+  if (!(cfl > 0) || !(cfl < 1e300)) return fail(ctx, MHD_ERR_ARG, "cfl must be finite and > 0");
+  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
+  Decoded sc;
+  mhd_status s = decode(ctx, scheme, sc);
+  if (s != MHD_OK) return s;
+  mhd::Dev D = ctx->base;
+  cudaStream_t st = ctx->stream;
+  s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, sizeof(unsigned long long), st), "cudaMemsetAsync");
+  if (s != MHD_OK) return s;
+  mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
+  const double hmin = std::fmin(D.h[0], std::fmin(D.h[1], D.h[2]));
+  {
+    Timed t(ctx, MHD_K_MAXSPEED, 2);  // the reduction and the dt kernel
+    mhd::launch_maxspeed(D, state->cons, B, D.counters + 2, st);
+    mhd::launch_set_dt(D.counters + 2, cfl, eta, hmin, D.hinv, ctx->dtbuf, st);
+  }
+  s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
+  if (s != MHD_OK) return s;
+  D.dt = 0.0;
+  D.dthp = ctx->dtbuf + 1;
+  return advance(ctx, state, D, sc, eta);
+}
+
+mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt_out) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!dt_out) return fail(ctx, MHD_ERR_ARG, "NULL argument");
+  double h[5] = {0, 0, 0, 0, 0};
+  mhd_status s = cuda_check(ctx, cudaMemcpyAsync(h, ctx->dtbuf, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream),
+                            "cudaMemcpyAsync");
+  if (s != MHD_OK) return s;
+  s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  *dt_out = h[0];
+  if (h[4] != 0.0) return fail(ctx, MHD_ERR_NONFINITE, "signal speed is zero or not finite");
   return MHD_OK;
 }
 

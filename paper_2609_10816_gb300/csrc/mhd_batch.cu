@@ -307,7 +307,7 @@ __global__ void k_batch_set_dt(Dev* p0, Dev* p1, int npatch, const unsigned long
   double dt = cfl * hmin / smax;
   if (!(dt > 0.0) || !finite_d(dt)) {  // non-finite speed: keep the step well defined, flag it
     dt = 0.0;
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err + 1, 1ull);
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err, 1ull);
   }
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npatch; k += gridDim.x * blockDim.x) {
     p0[k].dt = dt;

@@ -42,6 +42,24 @@ __global__ void __launch_bounds__(128) k_fo_recompute(Dev D) {
   for (long long X = cell_id(); X < D.N; X += (long long)gridDim.x * blockDim.x) fo_recompute_cell(D, X);
 }
 
+// dt = cfl hmin / max(smax, 2 eta / hmin) (Eq. resistivity:cfl), the operations of mhd_max_dt
+__global__ void k_set_dt(const unsigned long long* smax_bits, double cfl, double eta, double hmin, double hx,
+                         double hy, double hz, double* out) {
+  double smax = dfrom((long long)*smax_bits);
+  const double sres = 2.0 * eta / hmin;
+  if (sres > smax) smax = sres;
+  double dt = 0.0, bad = 1.0;
+  if (smax > 0.0 && smax < 1e300) {
+    dt = cfl * hmin / smax;
+    bad = 0.0;
+  }
+  out[0] = dt;
+  out[1] = dt * hx;
+  out[2] = dt * hy;
+  out[3] = dt * hz;
+  out[4] = bad;
+}
+
 // ---- reductions -----------------------------------------------------------------------------
 __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* out) {
   // v >= 0: the bit pattern orders like the value
@@ -196,6 +214,10 @@ void launch_update(const Dev& d, cudaStream_t st) { k_update<<<blocks_for(d.N, 2
 void launch_flag(const Dev& d, cudaStream_t st) { k_flag<<<blocks_for(d.N, 256), 256, 0, st>>>(d); }
 void launch_prim_if_flagged(const Dev& d, int prev_stage, cudaStream_t st) {
   k_prim_if_flagged<<<blocks_for(d.N, 256), 256, 0, st>>>(d, prev_stage);
+}
+void launch_set_dt(const unsigned long long* smax_bits, double cfl, double eta, double hmin, const double* hinv,
+                   double* out, cudaStream_t st) {
+  k_set_dt<<<1, 1, 0, st>>>(smax_bits, cfl, eta, hmin, hinv[0], hinv[1], hinv[2], out);
 }
 void launch_fofc(const Dev& d, cudaStream_t st) {
   auto grid = [&](const void* k) {

@@ -56,6 +56,11 @@ __device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, c
                                                 double m) {
   double w[8];
   prim_of(D, U, B, X, w);
+  // a cell with a value that is not finite gives +inf, which the callers report as an error
+  bool ok = true;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) ok = ok && finite_d(w[v]);
+  if (!ok) return __longlong_as_double(0x7ff0000000000000LL);
   const double hmin = fmin(D.h[0], fmin(D.h[1], D.h[2]));
   const double rinv = rcp(w[0]);
   const double a2 = D.gam * w[4] * rinv;
@@ -72,9 +77,11 @@ __device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, c
     const double bn2 = w[5 + d] * w[5 + d];
     const double disc = pmax(fma(sum, sum, -4.0 * (a2 * bn2 * rinv)), 0.0);
     const double cf = sqrt_(halve(sum + sqrt_(disc)));
-    s = pmax(s, (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]));
+    const double v = (vabs(w[1 + d]) + cf) * (hmin * D.hinv[d]);
+    // a speed that is not a number (a state with p < 0 or rho <= 0 can give one) is passed over,
+    // as an ordered comparison with the running maximum passes it over; +inf is kept
+    if (mag_bits(v) <= 0x7ff0000000000000LL) s = pmax(s, v);
   }
-  if (!finite_d(s)) s = __longlong_as_double(0x7ff0000000000000LL);  // +inf
   return pmax(m, s);
 }
 
@@ -86,6 +93,8 @@ __device__ __forceinline__ void prim_cell(const Dev& D, long long X) {
 }
 
 // ---- update: S_out = S^n + D(F, E) --------------------------------------------------------
+// dt / h_d: from device memory when the step's dt came from the device-side CFL reduction
+__device__ __forceinline__ double dth_of(const Dev& D, int d) { return D.dthp ? __ldg(D.dthp + d) : D.dth[d]; }
 // U_v^n + dt sum_d (F_d[X] - F_d[X + d]) / h_d (Eq. rk:increment-state), with dt / h_d folded
 // into the FMAs
 __device__ __forceinline__ double cell_new(const Dev& D, int v, long long X, const long long* Xp) {
@@ -93,8 +102,8 @@ __device__ __forceinline__ double cell_new(const Dev& D, int v, long long X, con
   const double* F0 = D.F + (0 * 5 + v) * N;
   const double* F1 = D.F + (1 * 5 + v) * N;
   const double* F2 = D.F + (2 * 5 + v) * N;
-  return fma(F0[X] - F0[Xp[0]], D.dth[0],
-             fma(F1[X] - F1[Xp[1]], D.dth[1], fma(F2[X] - F2[Xp[2]], D.dth[2], D.U0[v * N + X])));
+  return fma(F0[X] - F0[Xp[0]], dth_of(D, 0),
+             fma(F1[X] - F1[Xp[1]], dth_of(D, 1), fma(F2[X] - F2[Xp[2]], dth_of(D, 2), D.U0[v * N + X])));
 }
 // the updated field on the d-face of cell X (its lower face), by the discrete Stokes theorem
 // (Eq. rk:increment-bfield); Xp[a], Xp[c] = X + 1 along a, c
@@ -103,7 +112,7 @@ __device__ __forceinline__ double face_new(const Dev& D, int d, long long X, con
   const int a = (d + 1) % 3, c = (d + 2) % 3;
   const double* Ec = D.E + c * N;
   const double* Ea = D.E + a * N;
-  return fma(Ec[X] - Ec[Xp[a]], D.dth[a], fma(Ea[Xp[c]] - Ea[X], D.dth[c], D.B0[d][X]));
+  return fma(Ec[X] - Ec[Xp[a]], dth_of(D, a), fma(Ea[Xp[c]] - Ea[X], dth_of(D, c), D.B0[d][X]));
 }
 // the updated state of cell X (5 conserved values, then its 3 lower faces), not yet stored
 __device__ __forceinline__ void update_vals(const Dev& D, long long X, const long long* Xp, double* out) {

@@ -23,6 +23,8 @@ struct Dev {
   double gam, gm1inv;
   double dt, eta;
   double dth[3];        // dt / h_d
+  const double* dthp;   // when set, dt / h_d are read from device memory here instead (a step whose
+                        // dt comes from the device-side CFL reduction)
   int resistive;        // eta != 0
   int combine;          // stage 2: store (old + new) / 2 into fluxes and EMFs
   int fofc_criteria;    // bit 0 rho <= 0, bit 1 p <= 0
@@ -103,6 +105,10 @@ void launch_edges_bt(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_update(const Dev& d, cudaStream_t st);
 void launch_flag(const Dev& d, cudaStream_t st);
+// dt of Eq. (resistivity:cfl) from the reduction's maximum signal speed (bit pattern at smax_bits):
+// out[0] = dt, out[1..3] = dt / h_d, out[4] = 1 when the speed is zero or not finite (dt = 0)
+void launch_set_dt(const unsigned long long* smax_bits, double cfl, double eta, double hmin, const double* hinv,
+                   double* out, cudaStream_t st);
 void launch_prim_if_flagged(const Dev& d, int prev_stage, cudaStream_t st);
 void launch_fofc(const Dev& d, cudaStream_t st);
 void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st);

@@ -85,6 +85,10 @@ def lib():
     L.mhd_create_error.restype = ctypes.c_char_p
     L.mhd_step_adjoint.argtypes = [vp, P(_State), P(_State), d, ctypes.c_int, d, P(d)]
     L.mhd_step_adjoint.restype = ctypes.c_int
+    L.mhd_step_cfl.argtypes = [vp, P(_State), d, ctypes.c_int, d]
+    L.mhd_step_cfl.restype = ctypes.c_int
+    L.mhd_last_dt.argtypes = [vp, P(d)]
+    L.mhd_last_dt.restype = ctypes.c_int
     L.mhd_math_check.argtypes = [vp, ctypes.c_longlong, P(d)]
     L.mhd_math_check.restype = ctypes.c_int
     L.mhd_adjoint_check.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_ulonglong, P(d)]
@@ -173,6 +177,17 @@ class Context:
         s = self._state(st)
         out = ctypes.c_double()
         self._err(lib().mhd_max_dt(self._h, ctypes.byref(s), float(cfl), float(eta), ctypes.byref(out)))
+        return out.value
+
+    def step_cfl(self, st: State, cfl: float, scheme_bits: int, eta: float = 0.0):
+        """max_dt + step with dt kept on the device (no synchronisation)."""
+        s = self._state(st)
+        self._err(lib().mhd_step_cfl(self._h, ctypes.byref(s), float(cfl), int(scheme_bits), float(eta)))
+
+    def last_dt(self) -> float:
+        """dt of the last step_cfl (synchronises)."""
+        out = ctypes.c_double()
+        self._err(lib().mhd_last_dt(self._h, ctypes.byref(out)))
         return out.value
 
     def divb(self, st: State):

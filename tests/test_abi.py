@@ -54,6 +54,8 @@ def test_create_rejects_bad_boxes_before_touching_the_device(lib):
         assert L.mhd_create_error()
     assert L.mhd_create(None, None, ctypes.byref(out)) == mhd.ERR_ARG
     assert L.mhd_step(None, None, 1.0, 0, 0.0) == mhd.ERR_ARG
+    assert L.mhd_step_cfl(None, None, 0.3, 0, 0.0) == mhd.ERR_ARG
+    assert L.mhd_last_dt(None, None) == mhd.ERR_ARG
     L.mhd_destroy(None)
 
 

@@ -137,6 +137,46 @@ def test_max_dt_and_divb(gpu_lib):
     assert abs(md - mdo) <= 1e-12 * mbo / min(info["h"])
 
 
+def test_step_with_device_cfl_equals_host_cfl(gpu_lib):
+    """step_cfl (CFL reduction, dt and dt/h kept on the device) gives bit for bit the state and the
+    dt of max_dt + step, over several steps, ideal and resistive; and the oracle's step agrees."""
+    shape = (18, 10, 7)
+    cons, b, info = inputs.random_smooth(shape, seed=11, rough=0.05)
+    ctx = mhd.Context(shape, info["h"])
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    for eta in (0.0, 4e-3, 50.0):  # the last makes the resistive speed set dt
+        st_h, st_d = mhd.to_device(cons, b), mhd.to_device(cons, b)
+        for _ in range(3):
+            dt = ctx.max_dt(st_h, 0.3, eta)
+            ctx.step(st_h, dt, sch, eta)
+            ctx.step_cfl(st_d, 0.3, sch, eta)
+            assert ctx.last_dt() == dt
+        torch.cuda.synchronize()
+        assert torch.equal(st_h.cons, st_d.cons) and torch.equal(st_h.b, st_d.b)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon="ppm", riemann="hlld", eta=4e-3)
+    co, bo, _ = oracle.step(cfg, cons, b, oracle.max_dt(cfg, cons, b, 0.3))
+    st = mhd.to_device(cons, b)
+    ctx.step_cfl(st, 0.3, sch, 4e-3)
+    torch.cuda.synchronize()
+    assert_parity(st.cons.cpu().numpy(), st.b.cpu().numpy(), co, bo, what="step_cfl")
+
+
+def test_step_cfl_reports_a_non_finite_speed(gpu_lib):
+    """A cell without a finite signal speed: step_cfl runs with dt = 0 and last_dt raises, as
+    max_dt does."""
+    shape = (8, 6, 5)
+    cons, b, info = inputs.random_smooth(shape, seed=5, rough=0.05)
+    cons = cons.copy()
+    cons[4, 2, 3, 1] = np.inf  # infinite energy in one cell
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    ctx.step_cfl(st, 0.3, mhd.scheme("plm_mc", "hll", "q26"))
+    with pytest.raises(RuntimeError):
+        ctx.last_dt()
+    with pytest.raises(RuntimeError):  # the host-side CFL step reports the same cell
+        ctx.max_dt(mhd.to_device(cons, b), 0.3)
+
+
 def test_fast_reciprocal_and_sqrt_against_ieee(gpu_lib):
     """The kernels' reciprocal / rsqrt / sqrt stay within a few ulp of CUDA's IEEE results."""
     ctx = mhd.Context((4, 4, 4), (1, 1, 1))
