@@ -142,7 +142,10 @@ __device__ __forceinline__ Dual vmax(Dual a, Dual b) { return okey(a.v) >= okey(
 __device__ __forceinline__ Dual vmin(Dual a, Dual b) { return okey(a.v) <= okey(b.v) ? a : b; }
 __device__ __forceinline__ Dual pmax(Dual a, Dual b) { return dbits(a.v) >= dbits(b.v) ? a : b; }
 __device__ __forceinline__ Dual pmin(Dual a, Dual b) { return dbits(a.v) <= dbits(b.v) ? a : b; }
-__device__ __forceinline__ Dual vabs(Dual x) { return dbits(x.v) < 0 ? -x : x; }
+__device__ __forceinline__ Dual vabs(Dual x) {
+  const bool neg = dbits(x.v) < 0;
+  return Dual(vabs(x.v), neg_if(neg, x.t));
+}
 __device__ __forceinline__ bool gt0(const Dual& x) { return gt0(x.v); }
 __device__ __forceinline__ bool lt0(const Dual& x) { return lt0(x.v); }
 __device__ __forceinline__ bool ge0(const Dual& x) { return ge0(x.v); }
@@ -153,7 +156,7 @@ __device__ __forceinline__ double sgnd(const Dual& x) { return sgnd(x.v); }
 // |m| with the sign of s
 __device__ __forceinline__ Dual with_sign(Dual m, Dual s) {
   const bool flip = (dbits(m.v) < 0) != (dbits(s.v) < 0);
-  return Dual(with_sign(m.v, s.v), flip ? -m.t : m.t);
+  return Dual(with_sign(m.v, s.v), neg_if(flip, m.t));
 }
 __device__ __forceinline__ Dual rcp(Dual x) {
   const double r = rcp(x.v);
@@ -462,6 +465,17 @@ __device__ __forceinline__ void star_state(const FaceStateT<T>& q, const PhysFlu
   o.es = (fma(su, ph.e, -ph.pt * q.u) + fma(ptS, SM, bn * (vb - o.vbs))) * ssminv;
 }
 
+// Whether the face (x/t = 0) lies inside the rotational wave S*_side = S_M -/+ |b_n| / sqrt(rho*)
+// (MK05 Eq. 51) on the side `left` of the contact (S_M >= 0 on the left): S*_left < 0 and
+// S*_right >= 0 compared as S_M^2 rho* against b_n^2, without the square root (both sides are
+// non-negative, so the bit patterns order them). The reverse sweep takes the same decision.
+template <class T>
+__device__ __forceinline__ bool hlld_in_rotational(bool left, T SM, T rs, T bn2) {
+  const double sm = val(SM);
+  const long long q = dbits(sm * sm * val(rs)), b = dbits(val(bn2));
+  return left ? q < b : q <= b;
+}
+
 template <class T>
 __device__ __forceinline__ FaceStateT<T> pick(bool left, const FaceStateT<T>& a, const FaceStateT<T>& b) {
   FaceStateT<T> r;
@@ -509,17 +523,16 @@ __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T
   const T S = left ? SL : SR;
   StarT<T> a;
   star_state(q, P, S, SM, ptS, bn, bn2, a);
-  const T isqa = rsqrt_(a.rs);
-  const T Ss = left ? SM - abn * isqa : SM + abn * isqa;  // MK05 Eq. 51
   const T Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
   T Fs[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) Fs[v] = fma(S, Usa[v] - P.U[v], P.F[v]);
-  const bool dstar = left ? !ge0(Ss) : ge0(Ss);
-  if (!dstar) {
+  if (!hlld_in_rotational(left, SM, a.rs, bn2)) {
     for (int v = 0; v < 5; ++v) F[v] = Fs[v];
     return;
   }
+  const T isqa = rsqrt_(a.rs);
+  const T Ss = left ? SM - abn * isqa : SM + abn * isqa;  // MK05 Eq. 51
   // inside the rotational wave of this side: the other side's star state (its density, velocity
   // and field only) and the double star
   const FaceStateT<T> qo = pick(!left, sl, sr);

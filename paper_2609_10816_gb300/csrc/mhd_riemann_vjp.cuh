@@ -233,7 +233,7 @@ __device__ __forceinline__ void hlld_rev(const FaceState& sl, const FaceState& s
   const double isqa = rsqrt_(a.rs);
   const double Ss = left ? SM - abn * isqa : SM + abn * isqa;
   const double Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
-  const bool dstar = left ? !ge0(Ss) : ge0(Ss);
+  const bool dstar = hlld_in_rotational(left, SM, a.rs, bn2);
 
   // ---- reverse ----
   double dFs[5], dUsa[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -502,10 +502,10 @@ __device__ __forceinline__ void riemann_vjp(const FaceState& sl, const FaceState
   if (RS == RS_LLF) {
     const double da = dap + dam;
     if (llf_left) {
-      dsl.u += dbits(sl.u) < 0 ? -da : da;
+      dsl.u += neg_if(dbits(sl.u) < 0, da);
       dLcf += da;
     } else {
-      dsr.u += dbits(sr.u) < 0 ? -da : da;
+      dsr.u += neg_if(dbits(sr.u) < 0, da);
       dRcf += da;
     }
   } else {

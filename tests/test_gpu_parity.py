@@ -161,6 +161,31 @@ def test_step_with_device_cfl_equals_host_cfl(gpu_lib):
     assert_parity(st.cons.cpu().numpy(), st.b.cpu().numpy(), co, bo, what="step_cfl")
 
 
+def test_step_cfl_sequence_in_a_cuda_graph(gpu_lib):
+    """Four step_cfl calls recorded in one CUDA graph replay to the eager result bit for bit (the
+    step needs no host round trip, so a sequence of steps can run as one graph launch)."""
+    shape = (16, 12, 10)
+    cons, b, info = inputs.random_smooth(shape, seed=13, rough=0.05)
+    s = torch.cuda.Stream()
+    ctx = mhd.Context(shape, info["h"], stream=s)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    st_e, st_g = mhd.to_device(cons, b), mhd.to_device(cons, b)
+    torch.cuda.synchronize()
+    for _ in range(4):
+        ctx.step_cfl(st_e, 0.3, sch, 1e-3)
+    dt_e = ctx.last_dt()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(4):
+            ctx.step_cfl(st_g, 0.3, sch, 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(st_g.cons, mhd.to_device(cons, b).cons)  # capture ran nothing
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(st_e.cons, st_g.cons) and torch.equal(st_e.b, st_g.b)
+    assert ctx.last_dt() == dt_e
+
+
 def test_step_cfl_reports_a_non_finite_speed(gpu_lib):
     """A cell without a finite signal speed: step_cfl runs with dt = 0 and last_dt raises, as
     max_dt does."""
