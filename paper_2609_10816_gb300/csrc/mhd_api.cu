@@ -97,12 +97,16 @@ struct Timed {
 
 // one RK stage: prim -> faces -> edges -> update -> flags -> flux correction. prim_given: the
 // previous stage's flag pass wrote this stage's primitives (redo them only if it flagged cells).
-void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc, bool prim_given = false) {
+// where the stage input's primitives come from: its own pass, the previous stage's flag pass
+// (redone only for cells flux correction changed), or already in place (the CFL reduction)
+enum PrimSource { PRIM_COMPUTE, PRIM_IF_FLAGGED, PRIM_READY };
+
+void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc, PrimSource prim = PRIM_COMPUTE) {
   cudaStream_t st = c->stream;
-  if (prim_given) {
+  if (prim == PRIM_IF_FLAGGED) {
     Timed t(c, MHD_K_PRIM, 1);
     mhd::launch_prim_if_flagged(D, D.stage - 1, st);
-  } else {
+  } else if (prim == PRIM_COMPUTE) {
     Timed t(c, MHD_K_PRIM, 1);
     mhd::launch_prim(D, st);
   }
@@ -262,7 +266,8 @@ mhd_status mhd_profile_read(mhd_ctx* ctx, double* total_ms, long long* launches,
 }
 
 // The two stages and the copy-back of one step; D carries dt / h_d (by value or in device memory).
-static mhd_status advance(mhd_ctx* ctx, const mhd_state* state, mhd::Dev D, const Decoded& sc, double eta) {
+static mhd_status advance(mhd_ctx* ctx, const mhd_state* state, mhd::Dev D, const Decoded& sc, double eta,
+                          bool prim_ready = false) {
   const long long N = D.N;
   mhd_status s;
   D.eta = eta;
@@ -283,7 +288,7 @@ static mhd_status advance(mhd_ctx* ctx, const mhd_state* state, mhd::Dev D, cons
   D.combine = 0;
   D.stage = 0;
   D.Pnext = D.P;  // stage 1's flag pass leaves the primitives of S^{n+1/2} for stage 2
-  run_stage(ctx, D, sc);
+  run_stage(ctx, D, sc, prim_ready ? PRIM_READY : PRIM_COMPUTE);
 
   // stage 2: S^{n+1} = S^n + D(F_rk), F_rk = (F^n + F^{n+1/2}) / 2  (Eq. rk2:update); the
   // update reads only S^n and the fluxes, so it may overwrite the stage-1 scratch in place.
@@ -292,7 +297,7 @@ static mhd_status advance(mhd_ctx* ctx, const mhd_state* state, mhd::Dev D, cons
   D.combine = 1;
   D.stage = 1;
   D.Pnext = nullptr;
-  run_stage(ctx, D, sc, true);
+  run_stage(ctx, D, sc, PRIM_IF_FLAGGED);
 
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
@@ -339,15 +344,15 @@ mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int sc
   mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
   const double hmin = std::fmin(D.h[0], std::fmin(D.h[1], D.h[2]));
   {
-    Timed t(ctx, MHD_K_MAXSPEED, 2);  // the reduction and the dt kernel
-    mhd::launch_maxspeed(D, state->cons, B, D.counters + 2, st);
+    Timed t(ctx, MHD_K_MAXSPEED, 2);  // the reduction (which also leaves S^n's primitives) and dt
+    mhd::launch_maxspeed(D, state->cons, B, D.counters + 2, st, D.P);
     mhd::launch_set_dt(D.counters + 2, cfl, eta, hmin, D.hinv, ctx->dtbuf, st);
   }
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
   D.dt = 0.0;
   D.dthp = ctx->dtbuf + 1;
-  return advance(ctx, state, D, sc, eta);
+  return advance(ctx, state, D, sc, eta, true);
 }
 
 mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt_out) {

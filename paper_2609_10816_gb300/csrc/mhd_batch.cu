@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   // update and validity flags (every lane of a warp runs the same number of passes for the ballot)
   int kf = k0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kCellIlp * nth) {
-    double w[kCellIlp][8], hi[kCellIlp][3];
+    double w[kCellIlp][8], hi[kCellIlp][3], pw[kCellIlp][8];
     int K[kCellIlp];
     bool f[kCellIlp];
     const Dev* Dp[kCellIlp];
@@ -216,7 +216,11 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
         Dp[g] = &B.patches[B.order[kf]];
         X[g] = i - B.cell_pref[kf];
         K[g] = kf;
-        f[g] = update_flag_vals(*Dp[g], X[g], w[g], hi[g]);
+        update_vals_hi(*Dp[g], X[g], w[g], hi[g]);
+        // stage 1 also forms the primitives of its result (stage 2's input), and reads the
+        // pressure of the validity test from them
+        f[g] = B.stage == 0 ? prim_invalid(*Dp[g], w[g], w[g] + 5, hi[g], pw[g])
+                            : invalid_vals(*Dp[g], w[g], w[g] + 5, hi[g]);
       }
     }
     unsigned cnt = 0;
@@ -226,11 +230,8 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
         store_update(*Dp[g], X[g], w[g]);
         Dp[g]->flag[X[g]] = f[g] ? 1 : 0;
         if (f[g]) atomicAdd(&pflags[K[g]], 1u);
-        if (B.stage == 0) {  // the primitives of S^{n+1/2}, stage 2's input
-          double pw[8];
-          prim_from(*Dp[g], w[g], w[g] + 5, hi[g], pw);
-          for (int v = 0; v < 8; ++v) Dp[g]->P[v * Dp[g]->N + X[g]] = pw[v];
-        }
+        if (B.stage == 0)  // the primitives of S^{n+1/2}, stage 2's input
+          for (int v = 0; v < 8; ++v) Dp[g]->P[v * Dp[g]->N + X[g]] = pw[g][v];
       }
       cnt += __popc(__ballot_sync(0xffffffffu, f[g]));
     }

@@ -87,12 +87,12 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* o
 // max over cells of the CFL signal speed (cfl_speed_max): a grid-stride loop whose warps share
 // their running maximum after every pass, so that most cells are settled by the bound check
 __global__ void __launch_bounds__(256) k_maxspeed(Dev D, const double* U, Ptr3 Bp,
-                                                  unsigned long long* out) {
+                                                  unsigned long long* out, double* Pout) {
   const long long nth = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   double s = 0.0;
   for (long long base = cell_id() - lane; base < D.N; base += nth) {  // uniform over the warp
-    if (base + lane < D.N) s = cfl_speed_max(D, U, Bp.p, base + lane, s);
+    if (base + lane < D.N) s = cfl_speed_max(D, U, Bp.p, base + lane, s, Pout);
     unsigned long long b = (unsigned long long)dbits(s);
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
@@ -227,9 +227,10 @@ void launch_fofc(const Dev& d, cudaStream_t st) {
   k_fo_edges<<<grid((const void*)k_fo_edges), 128, 0, st>>>(d);
   k_fo_recompute<<<grid((const void*)k_fo_recompute), 128, 0, st>>>(d);
 }
-void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st) {
+void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st,
+                     double* Pout) {
   const long long cap = 2LL * resident_blocks((const void*)k_maxspeed, 256);  // two waves of blocks
-  k_maxspeed<<<(unsigned)std::min((long long)blocks_for(d.N, 256), cap), 256, 0, st>>>(d, U, B, out);
+  k_maxspeed<<<(unsigned)std::min((long long)blocks_for(d.N, 256), cap), 256, 0, st>>>(d, U, B, out, Pout);
 }
 void launch_divb(const Dev& d, Ptr3 B, unsigned long long* out, cudaStream_t st) {
   k_divb<<<blocks_for(d.N, 256), 256, 0, st>>>(d, B, out);

@@ -53,9 +53,13 @@ __device__ __forceinline__ void prim_of(const Dev& D, const double* U, const dou
 // rounding, reaches m: the running maximum is the same value, with two square roots for most
 // cells instead of six. A non-finite speed gives +inf.
 __device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, const double* const* B, long long X,
-                                                double m) {
+                                                double m, double* Pout = nullptr) {
   double w[8];
   prim_of(D, U, B, X, w);
+  if (Pout) {  // the primitives of the state, for a stage that starts from it
+#pragma unroll
+    for (int v = 0; v < 8; ++v) Pout[v * D.N + X] = w[v];
+  }
   // a cell with a value that is not finite gives +inf, which the callers report as an error
   bool ok = true;
 #pragma unroll
@@ -185,30 +189,46 @@ __device__ __forceinline__ bool invalid_cell(const Dev& D, const double* U, doub
   return invalid_vals(D, u, lo, hi);
 }
 
-// update of cell X with its validity flag: the upper faces are recomputed here (as the
-// neighbours compute them) instead of read back, so no separate pass over the new state is needed
-// (the batched stage's fused phase; on a single box two passes are faster: the recomputed faces'
-// EMFs of the next plane come from L2, while the flag pass streams the new state)
-__device__ __forceinline__ bool update_flag_vals(const Dev& D, long long X, double* out, double* hi) {
+// update of cell X and its three upper faces, recomputed here (as the neighbours compute them)
+// instead of read back, so that the cell's validity can be tested without a separate pass over the
+// new state (the batched stage's fused phase; on a single box two passes are faster: the
+// recomputed faces' EMFs of the next plane come from L2, while the flag pass streams the new state)
+__device__ __forceinline__ void update_vals_hi(const Dev& D, long long X, double* out, double* hi) {
   const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
   update_vals(D, X, Xp, out);
 #pragma unroll
   for (int d = 0; d < 3; ++d) hi[d] = upper_face_new(D, d, Xp[d]);
-  return invalid_vals(D, out, out + 5, hi);
+}
+
+// invalid_vals and the primitives w of the same state in one pass: the pressure the test needs
+// is w[4], formed by the same operations (so the flag is the same bit for bit)
+__device__ __forceinline__ bool prim_invalid(const Dev& D, const double* u, const double* lo, const double* hi,
+                                             double* w) {
+  prim_from(D, u, lo, hi, w);
+  bool fin = true;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fin = fin && finite_d(u[v]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) fin = fin && finite_d(lo[d]) && finite_d(hi[d]);
+  if (!fin) return true;
+  if ((D.fofc_criteria & 1) && le0(u[0])) return true;
+  return (D.fofc_criteria & 2) && !gt0(w[4]);
 }
 
 // flag of cell X (written) and whether it is set; with D.Pnext also the cell's primitives
 __device__ __forceinline__ bool flag_cell(const Dev& D, long long X) {
   double u[5], lo[3], hi[3];
   load_cell(D, D.Uout, D.Bout, X, u, lo, hi);
-  const unsigned char f = invalid_vals(D, u, lo, hi) ? 1 : 0;
-  D.flag[X] = f;
-  if (D.Pnext) {
-    double w[8];
-    prim_from(D, u, lo, hi, w);
-#pragma unroll
-    for (int v = 0; v < 8; ++v) D.Pnext[v * D.N + X] = w[v];
+  if (!D.Pnext) {
+    const unsigned char f = invalid_vals(D, u, lo, hi) ? 1 : 0;
+    D.flag[X] = f;
+    return f != 0;
   }
+  double w[8];
+  const unsigned char f = prim_invalid(D, u, lo, hi, w) ? 1 : 0;
+  D.flag[X] = f;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) D.Pnext[v * D.N + X] = w[v];
   return f != 0;
 }
 

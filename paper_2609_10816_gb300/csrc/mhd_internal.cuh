@@ -111,7 +111,9 @@ void launch_set_dt(const unsigned long long* smax_bits, double cfl, double eta, 
                    double* out, cudaStream_t st);
 void launch_prim_if_flagged(const Dev& d, int prev_stage, cudaStream_t st);
 void launch_fofc(const Dev& d, cudaStream_t st);
-void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st);
+// Pout (may be NULL): the primitives of U, B written as the reduction forms them
+void launch_maxspeed(const Dev& d, const double* U, Ptr3 B, unsigned long long* out, cudaStream_t st,
+                     double* Pout = nullptr);
 void launch_divb(const Dev& d, Ptr3 B, unsigned long long* out, cudaStream_t st);
 void launch_math_check(long long n, unsigned long long* out, cudaStream_t st);
 
