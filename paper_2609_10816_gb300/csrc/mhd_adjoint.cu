@@ -268,6 +268,140 @@ __global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
   }
 }
 
+// ---- reconstructions as reverse sweeps (PPM) ------------------------------------------------
+// The adjoint of Rec<REC_PPM> walking a line: with e_k = q_{k+1} - q_k, the doubled slope
+// d_k = vl_slope2(e_{k-1}, e_k) (linear on its branch, d_k = a_k e_{k-1} + b_k e_k), the interface
+// value f_{k+1/2} = q_k + e_k / 2 - (d_{k+1} - d_k) / 12 and the monotonicity constraint of point k
+// acting on (f_{k-1/2}, f_{k+1/2}), the adjoints flow back through these relations in the order
+// they were formed. Step i takes the adjoints of point i's lower and upper values; the adjoint of
+// q_{i-2} is then complete and is returned. A thread walks its segment [m0, m1) from m0 - 2 to
+// m1 + 1 (the windows of every point whose window holds a point of the segment), with the
+// forward values recomputed by the forward functions (the same values and branch decisions) and
+// no atomics: each point's sum is formed by one thread.
+struct RevPPM {
+  double q0, q1, q2;          // q_i, q_{i+1}, q_{i+2}
+  double e1;                  // e_{i+1}
+  double d0, d1;              // d_i, d_{i+1}
+  double am, bm, a0, b0, a1, b1;  // slope jacobians of d_{i-1}, d_i, d_{i+1}
+  double fL, fR;              // f_{i-1/2}, f_{i+1/2}
+  double lfp, ld, le, g2, g1;  // adjoints: upper value of point i-1, d_{i-1}, e_{i-2}, q_{i-2}, q_{i-1}
+
+  // v = q_{i-2} .. q_{i+2} for the first step i
+  __device__ __forceinline__ void init(const double* v) {
+    const double e0 = v[1] - v[0], e1_ = v[2] - v[1], e2 = v[3] - v[2], e3 = v[4] - v[3];
+    const double dm = vl_slope2(e0, e1_);
+    vl_slope2_jac(e0, e1_, am, bm);
+    d0 = vl_slope2(e1_, e2);
+    vl_slope2_jac(e1_, e2, a0, b0);
+    d1 = vl_slope2(e2, e3);
+    vl_slope2_jac(e2, e3, a1, b1);
+    fL = ppm_iface(v[1], e1_, dm, d0);
+    fR = ppm_iface(v[2], e2, d0, d1);
+    q0 = v[2]; q1 = v[3]; q2 = v[4];
+    e1 = e3;
+    lfp = ld = le = g2 = g1 = 0.0;
+  }
+  // lam_lo, lam_hi: adjoints of point i's lower / upper values; qn = q_{i+3}. Returns the adjoint of
+  // q_{i-2}.
+  __device__ __forceinline__ double step(double lam_lo, double lam_hi, double qn) {
+    double lL = lam_lo, lR = lam_hi, gi = 0.0;
+    const int mc = ppm_mono_case(fR - q0, q0 - fL);
+    if (mc == PPM_FLAT) {  // aL = aR = q_i
+      gi = lam_lo + lam_hi;
+      lL = lR = 0.0;
+    } else if (mc == PPM_FIX_L) {  // aL = 3 q_i - 2 aR
+      gi = 3.0 * lam_lo;
+      lR = fma(-2.0, lam_lo, lam_hi);
+      lL = 0.0;
+    } else if (mc == PPM_FIX_R) {  // aR = 3 q_i - 2 aL
+      gi = 3.0 * lam_hi;
+      lL = fma(-2.0, lam_hi, lam_lo);
+      lR = 0.0;
+    }
+    const double lf = lfp + lL;           // f_{i-1/2}, complete
+    g1 += lf;                             // its q_{i-1}
+    double le1 = halve(lf);               // its e_{i-1}
+    const double ldi = lf * (-1.0 / 12.0);  // its d_i
+    ld = fma(lf, 1.0 / 12.0, ld);         // its d_{i-1}: complete
+    le = fma(am, ld, le);                 // d_{i-1} -> e_{i-2} (complete), e_{i-1}
+    le1 = fma(bm, ld, le1);
+    g1 += le;                             // e_{i-2} = q_{i-1} - q_{i-2}
+    const double out = g2 - le;
+    g2 = g1; g1 = gi; le = le1; ld = ldi; lfp = lR;
+    // forward values of the next step
+    const double en = qn - q2;            // e_{i+2}
+    const double dn = vl_slope2(e1, en);  // d_{i+2}
+    double an, bn;
+    vl_slope2_jac(e1, en, an, bn);
+    const double fn = ppm_iface(q1, e1, d1, dn);  // f_{i+3/2}
+    am = a0; bm = b0; a0 = a1; b0 = b1; a1 = an; b1 = bn;
+    d0 = d1; d1 = dn;
+    e1 = en;
+    q0 = q1; q1 = q2; q2 = qn;
+    fL = fR; fR = fn;
+    return out;
+  }
+};
+
+// One reconstruction source of the reverse sweeps along s: the reconstructed array, the adjoints
+// of the lower value at X and of the upper value at X (stored at X + s), and where the result
+// accumulates.
+struct RecSrc {
+  const double* q;
+  const double* lam_lo;
+  const double* lam_hi;
+  double* out;
+};
+// face states (k_adj_face_rec): the 7 reconstructed primitives of the s-faces
+__device__ __forceinline__ RecSrc face_src(const AdjDev& A, int s, int v) {
+  const long long N = A.D.N;
+  const int a = (s + 1) % 3, c = (s + 2) % 3;
+  const int slot = v == 0 ? 0 : v == 1 ? 1 + s : v == 2 ? 1 + a : v == 3 ? 1 + c : v == 4 ? 4 : v == 5 ? 5 + a : 5 + c;
+  const double* lLR = A.lLR + 14LL * s * N;
+  return {A.D.P + slot * N, lLR + (7 + v) * N, lLR + v * N, A.lP + slot * N};
+}
+// edge values (k_adj_edge_rec): b_d and u_d^* reconstructed along s, for the face arrays d = s - 1
+// (s is their "c" direction, e-edges e = s + 1: bottom / top values) and d = s + 1 (s is their "a"
+// direction, e-edges e = s + 2: left / right values)
+__device__ __forceinline__ RecSrc edge_src(const AdjDev& A, int s, int v) {
+  const long long N = A.D.N;
+  const bool bt = v < 2;
+  const int d = bt ? (s + 2) % 3 : (s + 1) % 3;
+  const int e = bt ? (s + 1) % 3 : (s + 2) % 3;
+  const bool vel = v & 1;
+  const double* L = A.lEdge + 8LL * e * N;
+  const int lo = bt ? (vel ? 3 : 1) : (vel ? 7 : 5), hi = lo - 1;
+  return {vel ? A.D.Us + d * N : A.D.Bin[d], L + lo * N, L + hi * N, (vel ? A.lUs : A.lB) + d * N};
+}
+
+// Reverse PPM sweeps along s over all sources of one kind: thread = (source, line segment).
+template <bool FACE>
+__global__ void __launch_bounds__(128) k_adj_rec_sweep(AdjDev A, int s, int seg) {
+  const Dev& D = A.D;
+  const long long nsw = sweep_threads(D, s, seg);
+  const long long tid = aid();
+  const int nsrc = FACE ? 7 : 4;
+  if (tid >= nsw * nsrc) return;
+  const int v = (int)(tid / nsw);
+  Line ln;
+  int m0, m1;
+  if (!sweep_line_at(D, s, seg, tid - v * nsw, ln, m0, m1, s == 0)) return;
+  const RecSrc r = FACE ? face_src(A, s, v) : edge_src(A, s, v);
+  RevPPM w;
+  double v5[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) v5[t] = r.q[ln.at(m0 - 4 + t)];
+  w.init(v5);
+  for (int i = m0 - 2; i <= m1 + 1; ++i) {
+    const long long X = ln.at(i);
+    const double g = w.step(r.lam_lo[X], r.lam_hi[ln.at(i + 1)], r.q[ln.at(i + 3)]);
+    if (i - 2 >= m0) {
+      const long long Y = ln.at(i - 2);
+      r.out[Y] += g;
+    }
+  }
+}
+
 // ---- faces: adjoint of the Riemann solve -------------------------------------------------
 // gradient of the weighted face outputs in the 15 inputs by the dual numbers: one forward pass
 // per input (the reference that the reverse sweep of mhd_riemann_vjp.cuh is checked against)
@@ -562,18 +696,31 @@ __global__ void __launch_bounds__(256) k_adj_update(Dev D, const double* lU, con
   }
 }
 
+// reverse sweeps of the PPM reconstructions along each direction (one launch per direction, so
+// that every output element has one writer per launch); kind FACE or edge values
+template <bool FACE>
+static void rec_sweeps(const AdjDev& A, cudaStream_t st) {
+  for (int s = 0; s < 3; ++s) {
+    const int seg = 32;
+    const long long n = sweep_threads(A.D, s, seg) * (FACE ? 7 : 4);
+    k_adj_rec_sweep<FACE><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, s, seg);
+  }
+}
+
 template <int RC>
 static void adj_flux_r(const AdjDev& A, int rs, cudaStream_t st) {
   const unsigned nb = (unsigned)((A.D.N + 127) / 128);
   k_adj_edges<RC><<<nb, 128, 0, st>>>(A);
-  k_adj_edge_rec<RC><<<nb, 128, 0, st>>>(A);
+  if (RC == REC_PPM) rec_sweeps<false>(A, st);
+  else k_adj_edge_rec<RC><<<nb, 128, 0, st>>>(A);
   for (int dir = 0; dir < 3; ++dir) {
     if (rs == RS_HLL) k_adj_faces<RC, RS_HLL><<<nb, 128, 0, st>>>(A, dir);
     else if (rs == RS_HLLD) k_adj_faces<RC, RS_HLLD><<<nb, 128, 0, st>>>(A, dir);
     else k_adj_faces<RC, RS_LLF><<<nb, 128, 0, st>>>(A, dir);
     if (A.D.resistive) k_adj_joule<<<nb, 128, 0, st>>>(A, dir);
   }
-  k_adj_face_rec<RC><<<nb, 128, 0, st>>>(A);
+  if (RC == REC_PPM) rec_sweeps<true>(A, st);
+  else k_adj_face_rec<RC><<<nb, 128, 0, st>>>(A);
   k_adj_prim<<<nb, 128, 0, st>>>(A);
 }
 
