@@ -617,54 +617,54 @@ __global__ void __launch_bounds__(128) k_adj_face_rec(AdjDev A) {
 }
 
 // ---- primitives: adjoint of cons -> prim ------------------------------------------------
-template <class T>
-__device__ __forceinline__ void prim_t(double gam, const T* u, const T* blo, const T* bhi, T* w) {
-  const T rho = u[0];
-  const T rinv = rcp(rho);
-  const T u0 = u[1] * rinv, u1 = u[2] * rinv, u2 = u[3] * rinv;
-  const T b0 = 0.5 * (blo[0] + bhi[0]);
-  const T b1 = 0.5 * (blo[1] + bhi[1]);
-  const T b2 = 0.5 * (blo[2] + bhi[2]);
-  const T u2s = fma(u0, u0, fma(u1, u1, u2 * u2));
-  const T b2s = fma(b0, b0, fma(b1, b1, b2 * b2));
-  const T eint = u[4] - 0.5 * fma(rho, u2s, b2s);
-  w[0] = rho; w[1] = u0; w[2] = u1; w[3] = u2;
-  w[4] = (gam - 1.0) * eint;
-  w[5] = b0; w[6] = b1; w[7] = b2;
+// reverse of cons -> prim (prim_from) for cell X, given the adjoints lp of its 8 primitives: adds
+// the adjoints of its conserved variables to lU and returns, per direction, the adjoint of its
+// cell-centred field b_d = (b_d^lo + b_d^hi) / 2 (the faces get half of it each)
+__device__ __forceinline__ void prim_rev(const AdjDev& A, long long X, double* lbc) {
+  const Dev& D = A.D;
+  const long long N = D.N;
+  double lp[8], u[5], b[3];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) lp[v] = A.lP[v * N + X];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = D.Uin[v * N + X];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) b[d] = 0.5 * (D.Bin[d][X] + D.Bin[d][shift(D, X, d, 1)]);
+  const double rho = u[0], rinv = rcp(rho);
+  const double ui[3] = {u[1] * rinv, u[2] * rinv, u[3] * rinv};
+  const double u2s = fma(ui[0], ui[0], fma(ui[1], ui[1], ui[2] * ui[2]));
+  const double leint = (D.gam - 1.0) * lp[4];        // p = (gamma - 1) eint
+  const double lq = -0.5 * leint;                     // eint = e - (rho u2s + b2s) / 2
+  double lrinv = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double lu = fma(2.0 * ui[i], lq * rho, lp[1 + i]);  // u_i directly and through u2s
+    A.lU[(1 + i) * N + X] += lu * rinv;                       // u_i = m_i / rho
+    lrinv = fma(lu, u[1 + i], lrinv);
+  }
+  A.lU[4 * N + X] += leint;
+  A.lU[0 * N + X] += fma(lq, u2s, lp[0]) - lrinv * rinv * rinv;  // rho directly, via u2s, via 1/rho
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lbc[d] = fma(2.0 * b[d], lq, lp[5 + d]);
 }
 
+// adjoint of cons -> prim, by hand: each thread owns cell X's conserved adjoints and the lower
+// d-face of X, which gets half of the cell-centred field adjoint of X and of X - d (no atomics)
 __global__ void __launch_bounds__(128) k_adj_prim(AdjDev A) {
   const Dev& D = A.D;
   const long long X = aid();
   if (X >= D.N) return;
   const long long N = D.N;
-  double lp[8];
-  for (int v = 0; v < 8; ++v) lp[v] = A.lP[v * N + X];
-  double u[5], blo[3], bhi[3];
-  long long Xp[3];
-  for (int v = 0; v < 5; ++v) u[v] = D.Uin[v * N + X];
+  double lbc[3];
+  prim_rev(A, X, lbc);
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    Xp[d] = shift(D, X, d, 1);
-    blo[d] = D.Bin[d][X];
-    bhi[d] = D.Bin[d][Xp[d]];
-  }
-#pragma unroll 1
-  for (int i = 0; i < 11; ++i) {
-    Dual du[5], dl[3], dh[3], w[8];
-    for (int v = 0; v < 5; ++v) du[v] = Dual(u[v], i == v ? 1.0 : 0.0);
-    for (int d = 0; d < 3; ++d) {
-      dl[d] = Dual(blo[d], i == 5 + d ? 1.0 : 0.0);
-      dh[d] = Dual(bhi[d], i == 8 + d ? 1.0 : 0.0);
-    }
-    prim_t(D.gam, du, dl, dh, w);
-    double g = 0.0;
-    for (int v = 0; v < 8; ++v) g = fma(lp[v], w[v].t, g);
-    if (i < 5)
-      A.lU[i * N + X] += g;
-    else if (i < 8)
-      atomicAdd(&A.lB[(i - 5) * N + X], g);
-    else
-      atomicAdd(&A.lB[(i - 8) * N + Xp[i - 8]], g);
+    // the same quantity for cell X - d (its upper d-face is X's lower one)
+    const long long Xm = shift(D, X, d, -1);
+    const double bm = 0.5 * (D.Bin[d][Xm] + D.Bin[d][X]);
+    const double lqm = -0.5 * ((D.gam - 1.0) * A.lP[4 * N + Xm]);
+    const double lbm = fma(2.0 * bm, lqm, A.lP[(5 + d) * N + Xm]);
+    A.lB[d * N + X] += 0.5 * (lbc[d] + lbm);
   }
 }
 
