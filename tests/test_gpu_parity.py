@@ -171,6 +171,7 @@ def test_step_cfl_sequence_in_a_cuda_graph(gpu_lib):
     sch = mhd.scheme("ppm", "hlld", "q26")
     st_e, st_g = mhd.to_device(cons, b), mhd.to_device(cons, b)
     torch.cuda.synchronize()
+    assert ctx.last_dt() == 0.0  # no step_cfl yet
     for _ in range(4):
         ctx.step_cfl(st_e, 0.3, sch, 1e-3)
     dt_e = ctx.last_dt()
