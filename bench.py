@@ -252,6 +252,8 @@ def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
         ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         bt.last_dt()
         out[f"batched_1x{n0}cubed_same_state"] = whole_job_rate(n0**3 * args.steps, world, ms)
+        out["batched_config"]["same_state_phase_ms_last_step"] = {
+            f"stage{st + 1}": {k: round(v, 3) for k, v in ph.items()} for st, ph in bt.phase_ms().items()}
         bt.close()
     return out
 

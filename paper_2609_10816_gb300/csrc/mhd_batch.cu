@@ -145,9 +145,10 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   for (long long i = t0; i < B.npatch; i += nth) pflags[i] = 0u;
   // cons -> prim; the per-cell phases take kCellIlp cells per thread at a time, loads of all of
   // them before any store (the persistent grid has few warps per SM to hide memory latency).
-  // Stage 2's primitives come from stage 1's update phase unless flux correction changed its state.
-  // (per patch: only patches where stage 1 flagged a cell are redone)
-  const bool prim_given = B.stage == 1 && *(volatile unsigned long long*)(B.counters + 0) == 0;
+  // Stage 1's primitives come from the CFL reduction, stage 2's from stage 1's update phase unless
+  // flux correction changed its state (per patch: only patches where stage 1 flagged a cell are
+  // redone).
+  const bool prim_given = B.stage == 0 || *(volatile unsigned long long*)(B.counters + 0) == 0;
   for (long long i0 = t0, k = k0; i0 < ncell && !prim_given; i0 += kCellIlp * nth) {
     double w[kCellIlp][8];
     const Dev* Dp[kCellIlp];
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(256) k_batch_maxspeed(BatchDev B) {
     if (i < ncell) {
       k = advance_pos(B.cell_pref, k, i);
       const Dev& D = B.patches[B.order[k]];
-      s = cfl_speed_max(D, D.U0, D.B0, i - B.cell_pref[k], s);
+      s = cfl_speed_max(D, D.U0, D.B0, i - B.cell_pref[k], s, D.P);  // and stage 1's primitives
     }
     unsigned long long b = (unsigned long long)dbits(s);
     for (int o = 16; o > 0; o >>= 1) {
