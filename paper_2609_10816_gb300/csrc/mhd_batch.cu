@@ -199,10 +199,35 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   }
   if (!grid_sync(B)) return;
   stamp(B, 4);
-  // update and validity flags (every lane of a warp runs the same number of passes for the ballot)
+  // update, then (after a grid barrier) the validity flags of the new state, which the flag pass
+  // reads back instead of recomputing each cell's upper faces
+  {
+    int ku = k0;
+    for (long long base = t0; base < ncell; base += kCellIlp * nth) {
+      double w[kCellIlp][8];
+      const Dev* Dp[kCellIlp];
+      long long X[kCellIlp];
+#pragma unroll
+      for (int g = 0; g < kCellIlp; ++g) {
+        const long long i = base + g * nth;
+        Dp[g] = nullptr;
+        if (i < ncell) {
+          ku = advance_pos(B.cell_pref, ku, i);
+          Dp[g] = &B.patches[B.order[ku]];
+          X[g] = i - B.cell_pref[ku];
+          update_vals(*Dp[g], X[g], w[g]);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < kCellIlp; ++g)
+        if (Dp[g]) store_update(*Dp[g], X[g], w[g]);
+    }
+  }
+  if (!grid_sync(B)) return;
+  // (every lane of a warp runs the same number of passes for the ballot)
   int kf = k0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kCellIlp * nth) {
-    double w[kCellIlp][8], hi[kCellIlp][3], pw[kCellIlp][8];
+    double u[kCellIlp][5], lo[kCellIlp][3], hi[kCellIlp][3], pw[kCellIlp][8];
     int K[kCellIlp];
     bool f[kCellIlp];
     const Dev* Dp[kCellIlp];
@@ -210,25 +235,24 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
 #pragma unroll
     for (int g = 0; g < kCellIlp; ++g) {
       const long long i = base + g * nth + threadIdx.x;
-      f[g] = false;
       Dp[g] = nullptr;
       if (i < ncell) {
         kf = advance_pos(B.cell_pref, kf, i);
         Dp[g] = &B.patches[B.order[kf]];
         X[g] = i - B.cell_pref[kf];
         K[g] = kf;
-        update_vals_hi(*Dp[g], X[g], w[g], hi[g]);
-        // stage 1 also forms the primitives of its result (stage 2's input), and reads the
-        // pressure of the validity test from them
-        f[g] = B.stage == 0 ? prim_invalid(*Dp[g], w[g], w[g] + 5, hi[g], pw[g])
-                            : invalid_vals(*Dp[g], w[g], w[g] + 5, hi[g]);
+        load_cell(*Dp[g], Dp[g]->Uout, Dp[g]->Bout, X[g], u[g], lo[g], hi[g]);
       }
     }
     unsigned cnt = 0;
 #pragma unroll
     for (int g = 0; g < kCellIlp; ++g) {
+      f[g] = false;
       if (Dp[g]) {
-        store_update(*Dp[g], X[g], w[g]);
+        // stage 1 also forms the primitives of its result (stage 2's input), and reads the
+        // pressure of the validity test from them
+        f[g] = B.stage == 0 ? prim_invalid(*Dp[g], u[g], lo[g], hi[g], pw[g])
+                            : invalid_vals(*Dp[g], u[g], lo[g], hi[g]);
         Dp[g]->flag[X[g]] = f[g] ? 1 : 0;
         if (f[g]) atomicAdd(&pflags[K[g]], 1u);
         if (B.stage == 0)  // the primitives of S^{n+1/2}, stage 2's input
