@@ -129,15 +129,6 @@ __device__ __forceinline__ void update_vals(const Dev& D, long long X, double* o
   const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
   update_vals(D, X, Xp, out);
 }
-// the updated field on the upper d-face of cell X (the lower d-face of X + 1 along d), computed as
-// the neighbour computes it, so that a cell's validity can be tested where it is updated
-__device__ __forceinline__ double upper_face_new(const Dev& D, int d, long long Xd) {
-  long long Yp[3];
-  Yp[d] = Xd;  // not used by face_new
-  Yp[(d + 1) % 3] = shift(D, Xd, (d + 1) % 3, 1);
-  Yp[(d + 2) % 3] = shift(D, Xd, (d + 2) % 3, 1);
-  return face_new(D, d, Xd, Yp);
-}
 __device__ __forceinline__ void store_update(const Dev& D, long long X, const double* out) {
   const long long N = D.N;
 #pragma unroll
@@ -189,16 +180,6 @@ __device__ __forceinline__ bool invalid_cell(const Dev& D, const double* U, doub
   return invalid_vals(D, u, lo, hi);
 }
 
-// update of cell X and its three upper faces, recomputed here (as the neighbours compute them)
-// instead of read back, so that the cell's validity can be tested without a separate pass over the
-// new state (the batched stage's fused phase; on a single box two passes are faster: the
-// recomputed faces' EMFs of the next plane come from L2, while the flag pass streams the new state)
-__device__ __forceinline__ void update_vals_hi(const Dev& D, long long X, double* out, double* hi) {
-  const long long Xp[3] = {shift(D, X, 0, 1), shift(D, X, 1, 1), shift(D, X, 2, 1)};
-  update_vals(D, X, Xp, out);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) hi[d] = upper_face_new(D, d, Xp[d]);
-}
 
 // invalid_vals and the primitives w of the same state in one pass: the pressure the test needs
 // is w[4], formed by the same operations (so the flag is the same bit for bit)
