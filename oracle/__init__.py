@@ -63,6 +63,7 @@ def _L():
         d = ctypes.c_double
         _lib.oracle_step.argtypes = [P(_Cfg), P(d), P(d), d, P(ctypes.c_longlong)]
         _lib.oracle_fluxes.argtypes = [P(_Cfg), P(d), P(d), P(d), P(d)]
+        _lib.oracle_corner_emfs.argtypes = [P(_Cfg), P(d), P(d), P(d)]
         u8 = P(ctypes.c_ubyte)
         _lib.oracle_step_flags.argtypes = [P(_Cfg), P(d), P(d), d, u8, u8, P(ctypes.c_longlong)]
         _lib.oracle_prim.argtypes = [P(_Cfg), P(d), P(d), P(d)]
@@ -156,6 +157,20 @@ def fluxes(cfg: Config, cons: np.ndarray, b: np.ndarray):
     c = cfg.c()
     _L().oracle_fluxes(ctypes.byref(c), _ptr(cons), _ptr(b), _ptr(F), _ptr(E))
     return F, E
+
+
+def corner_emfs(cfg: Config, cons: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """The four corner EMFs of every edge, (3, 4, nz, ny, nx): [e][q] with q = 0 LB, 1 RB, 2 LT,
+    3 RT (L/R the sides of the a-face, B/T of the c-face, a = e+1, c = e+2), as the EMF compute
+    scheme (Q26, FS18 or B25a) forms them before the averaging of Eq. (ld04)."""
+    _check(cfg, cons, b)
+    cons = np.ascontiguousarray(cons, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    nx, ny, nz = cfg.shape
+    C = np.zeros((3, 4, nz, ny, nx))
+    c = cfg.c()
+    _L().oracle_corner_emfs(ctypes.byref(c), _ptr(cons), _ptr(b), _ptr(C))
+    return C
 
 
 def prim(cfg: Config, cons: np.ndarray, b: np.ndarray) -> np.ndarray:

@@ -407,6 +407,8 @@ void riemann(int solver, double gam, const T* WL, const T* WR, T bn, T* F, T& ap
 template <class T> struct FluxSet {
   std::vector<T> F;  // [3][5][N]
   std::vector<T> E;  // [3][N]
+  bool keep_corners = false;  // also return the four corner EMFs of every edge (pins only)
+  std::vector<T> C;  // [3][4][N], corners LB, RB, LT, RT before the averaging of Eq. (ld04)
 };
 
 template <class T>
@@ -419,6 +421,7 @@ void fluxes_and_emfs(const Grid& g, const Scheme<T>& sc, const std::vector<T>& U
 
   out.F.assign(15 * N, T(0.0));
   out.E.assign(3 * N, T(0.0));
+  if (out.keep_corners) out.C.assign(12 * N, T(0.0));
   std::vector<T> Ap(3 * N), Am(3 * N), Us(3 * N);
   // face-centred left/right velocity states (FS18 only): [d][k][N]
   std::vector<T> VL, VR;
@@ -557,6 +560,9 @@ void fluxes_and_emfs(const Grid& g, const Scheme<T>& sc, const std::vector<T>& U
         }
       }
     }
+
+    if (out.keep_corners)
+      for (long I = 0; I < 4 * N; ++I) out.C[4 * e * N + I] = corner[I];
 
     // Eq. (alpha-edge) and Eq. (ld04).
     for (long X = 0; X < N; ++X) {
@@ -874,6 +880,19 @@ int oracle_fluxes(const oracle_cfg* c, const double* cons, const double* b, doub
   fluxes_and_emfs(g, scheme_of(c), U, B, f);
   std::memcpy(flux, f.F.data(), sizeof(double) * 15 * g.N);
   std::memcpy(emf, f.E.data(), sizeof(double) * 3 * g.N);
+  return 0;
+}
+
+// The four corner EMFs of every edge (12N: [e][q][X], q = 0 LB, 1 RB, 2 LT, 3 RT, where L/R
+// are the sides of the a-face and B/T those of the c-face, a = e+1, c = e+2) of one state,
+// as the configured EMF compute scheme forms them before the averaging of Eq. (ld04).
+int oracle_corner_emfs(const oracle_cfg* c, const double* cons, const double* b, double* corners) {
+  Grid g = make_grid(c->n, c->h, c->gamma);
+  std::vector<double> U(cons, cons + 5 * g.N), B(b, b + 3 * g.N);
+  FluxSet<double> f;
+  f.keep_corners = true;
+  fluxes_and_emfs(g, scheme_of(c), U, B, f);
+  std::memcpy(corners, f.C.data(), sizeof(double) * 12 * g.N);
   return 0;
 }
 

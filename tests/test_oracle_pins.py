@@ -278,6 +278,112 @@ def test_point_reflection_symmetry(recon, rs, emf):
 
 
 # ---------------------------------------------------------------------------------------
+# EMF compute schemes (Sec. 2.3.1): corner EMFs of Q26, FS18 and B25a
+# ---------------------------------------------------------------------------------------
+def _uniform_state(shape, rho, u, p, bvec):
+    nx, ny, nz = shape
+    cons = np.empty((5, nz, ny, nx))
+    cons[0] = rho
+    for d in range(3):
+        cons[1 + d] = rho * u[d]
+    cons[4] = p / (G - 1.0) + 0.5 * rho * float(np.dot(u, u)) + 0.5 * float(np.dot(bvec, bvec))
+    b = np.empty((3, nz, ny, nx))
+    for d in range(3):
+        b[d] = bvec[d]
+    return cons, b
+
+
+@pytest.mark.parametrize("recon", ["pc", "plm_mc", "plm_minmod", "ppm"])
+@pytest.mark.parametrize("rs", ["hll", "hlld", "llf"])
+@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
+def test_uniform_state_corner_and_edge_emf_is_minus_u_cross_b(recon, rs, emf):
+    """For a uniform state every reconstruction returns the cell value, so each of the four
+    corner estimates of every compute scheme (Eqs. q26, fs18 with fs18-average, b25a-*) and
+    the averaged edge EMF of Eq. (ld04) must equal eps = -u x b, whatever the averaging weights
+    and the speeds; a wrong weight, sign or component in any scheme breaks this."""
+    shape = (5, 4, 3)
+    u = np.array([0.3, -0.7, 0.45])
+    bvec = np.array([0.8, 0.35, -0.6])
+    cons, b = _uniform_state(shape, 1.3, u, 0.9, bvec)
+    cfg = oracle.Config(shape=shape, h=(0.2, 0.25, 1.0 / 3.0), recon=recon, riemann=rs, emf=emf)
+    eps = -np.cross(u, bvec)
+    C = oracle.corner_emfs(cfg, cons, b)
+    _, E = oracle.fluxes(cfg, cons, b)
+    for e in range(3):
+        assert np.abs(C[e] - eps[e]).max() <= 4e-16 * np.abs(eps).max(), (e, C[e].ravel()[:4], eps[e])
+        assert np.abs(E[e] - eps[e]).max() <= 4e-16 * np.abs(eps).max(), (e, E[e].ravel()[:4], eps[e])
+
+
+def _golden_corners():
+    rows = []
+    with open(os.path.join(GOLDEN, "corner_emf_cases.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            case, emf, table, expect = [x.strip() for x in line.split(";")]
+            vals = np.array([float(v) for v in table.split()]).reshape(6, 6)  # [j][i]
+            exp = {int(k): float(v) for k, v in (t.split(":") for t in expect.split())}
+            rows.append((case, emf, vals, exp))
+    return rows
+
+
+@pytest.mark.parametrize("case,emf,table,expect", _golden_corners())
+def test_corner_emfs_hand_computed(case, emf, table, expect):
+    """FS18 and B25a corner EMFs on a 6 x 6 x 1 stencil, each corner derived by hand in
+    tests/golden/corner_emf_cases.txt from Eqs. (fs18-average), (fs18), (b25a-b-avg),
+    (b25a-emf-centre) and (b25a-average) with PLM-minmod: both reconstruction orders, their
+    mean, and the product with the reconstructed field."""
+    shape = (6, 6, 1)
+    cons = np.zeros((5, 1, 6, 6))
+    b = np.zeros((3, 1, 6, 6))
+    cons[0] = 1.0
+    if case == "velocity":
+        cons[1, 0] = table
+        b[1] = 1.0
+    else:
+        cons[1] = 1.0
+        b[1, 0] = table
+    bcell = 0.5 * (b[1] + np.roll(b[1], -1, axis=1))
+    cons[4] = 1.0 / (G - 1.0) + 0.5 * (cons[1] ** 2 + cons[2] ** 2 + cons[3] ** 2) / cons[0] + 0.5 * bcell**2
+    cfg = oracle.Config(shape=shape, h=(1.0, 1.0, 1.0), recon="plm_minmod", riemann="hll", emf=emf)
+    C = oracle.corner_emfs(cfg, cons, b)
+    for q, v in expect.items():
+        assert C[2, q, 0, 2, 2] == v, (case, emf, q, C[2, :, 0, 2, 2], v)
+
+
+@pytest.mark.parametrize("emf", ["fs18", "b25a"])
+def test_fast_wave_second_order_3d_diagonal_fs18_b25a(emf):
+    """Sec. 3.1.5: every compute scheme converges at second order. The oblique-diagonal fast
+    eigenmode of the 32^3 workload with PLM-MC + HLL at 16^3 and 32^3."""
+    errs = []
+    for n in (16, 32):
+        shape = (n, n, n)
+        cons, b, info = inputs.fast_wave(shape)
+        cbg, bbg, _ = inputs.fast_wave(shape, amp=0.0)
+        cfg = cfg_for(shape, info, recon="plm_mc", riemann="hll", emf=emf)
+        c, bb = _one_period(cfg, cons, b, info["period"])
+        errs.append(_relerr_pert(cons, b, c, bb, cbg, bbg))
+    assert errs[0] / errs[1] > 3.0, errs
+
+
+@pytest.mark.parametrize("emf", ["fs18", "b25a"])
+def test_oblique_alfven_wave_second_order_ppm_hlld_fs18_b25a(emf):
+    """Sec. 3.1.5 for the comparison schemes: the oblique linear Alfven wave of the throughput
+    workload with PPM + HLLD returns to its initial state after one period, the error falling
+    towards second order from 16^3 to 32^3."""
+    errs = []
+    for n in (16, 32):
+        shape = (n, n, n)
+        cons, b, info = inputs.alfven_oblique(shape)
+        cbg, bbg, _ = inputs.alfven_oblique(shape, amp=0.0)
+        cfg = cfg_for(shape, info, recon="ppm", riemann="hlld", emf=emf)
+        c, bb = _one_period(cfg, cons, b, 2 * np.pi / info["omega"])
+        errs.append(_relerr_pert(cons, b, c, bb, cbg, bbg))
+    assert errs[0] / errs[1] > 3.0, errs
+
+
+# ---------------------------------------------------------------------------------------
 # Convergence against closed-form waves (Sec. 3.1, Eq. error:relative)
 # ---------------------------------------------------------------------------------------
 def _relerr_pert(c0, b0, c1, b1, cbg, bbg):
