@@ -188,9 +188,9 @@ const char *mhd_create_error(void);
 #define MHD_NOALLOC_MAX_CELLS 32768
 
 /* mhd_step without any device allocation, for callers that cannot let a library allocate:
- * code recorded inside a CUDA stream capture (where cudaMalloc is not allowed), applications
- * whose memory manager owns all device memory, and loops that cannot afford cudaMalloc's
- * implicit synchronisation. The paper has no counterpart: this is a deployment variant of
+ * applications whose own memory manager owns all device memory (a pool that hands out every byte
+ * and cannot have a library allocate beside it), and loops that cannot afford cudaMalloc's
+ * implicit device synchronisation. The paper has no counterpart: this is a deployment variant of
  * mhd_step, with the same arguments and results, for boxes of at most MHD_NOALLOC_MAX_CELLS
  * cells and the Q26 EMF compute (FS18/B25a -> MHD_ERR_UNSUPPORTED). Larger boxes are rejected
  * with MHD_ERR_ARG (message from mhd_create_error) before any device work.
@@ -236,14 +236,19 @@ void mhd_batch_destroy(mhd_batch *batch);
 mhd_status mhd_batch_offsets(const mhd_batch *batch, long long *cell_offsets);
 
 /* One step of every patch in place (see above). Asynchronous; the first call for a state, scheme,
- * eta and cfl captures the graph. */
+ * eta and cfl captures the graph. The return code covers the enqueue only: check
+ * mhd_batch_last_dt (or mhd_batch_stats) after each step. If a grid barrier of a step gives up
+ * waiting, that step leaves the state unchanged, and so does every later step until one of those
+ * two calls reports MHD_ERR_TIMEOUT (which re-arms the batch). */
 mhd_status mhd_batch_step(mhd_batch *batch, const mhd_batch_state *state, double cfl, int scheme, double eta);
 
-/* dt of the last step (synchronous); MHD_ERR_TIMEOUT if a grid barrier gave up waiting,
- * MHD_ERR_NONFINITE if the signal speed was not finite (then no step was taken). */
+/* dt of the last step (synchronous); MHD_ERR_TIMEOUT if a grid barrier gave up waiting in any
+ * step since the last report (those steps left the state unchanged; the report clears the
+ * condition), MHD_ERR_NONFINITE if the signal speed was not finite (then no step was taken). */
 mhd_status mhd_batch_last_dt(mhd_batch *batch, double *dt);
 
-/* Flagged cells of the last step's two stages, summed over patches (synchronous). */
+/* Flagged cells of the last step's two stages, summed over patches (synchronous); reports and
+ * clears a barrier timeout as mhd_batch_last_dt does. */
 mhd_status mhd_batch_stats(mhd_batch *batch, long long *fofc_cells_stage1, long long *fofc_cells_stage2);
 
 /* Device time of the phases of the last step's two stage launches (synchronous), as measured by

@@ -132,6 +132,9 @@ constexpr int kCellIlp = 4;
 
 template <int RC, int RS>
 __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
+  // a barrier of an earlier stage gave up (the flag stays set until the host reads it): the
+  // step is abandoned and the caller's state left as it was
+  if (*(volatile unsigned long long*)(B.counters + 7)) return;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long ncell = B.cell_pref[B.npatch];
@@ -346,6 +349,19 @@ __global__ void k_batch_set_dt(Dev* p0, Dev* p1, int npatch, const unsigned long
   if (blockIdx.x == 0 && threadIdx.x == 0) *dt_out = dt;
 }
 
+// S^{n+1} from the batch's scratch state into the caller's arrays, unless a grid barrier of this
+// step (or of an unread earlier one) gave up; then the caller's state keeps S^n.
+__global__ void __launch_bounds__(256) k_batch_copy_back(const double* __restrict__ U1, double* __restrict__ cons,
+                                                        const double* __restrict__ B1, double* __restrict__ b,
+                                                        long long ncell, const unsigned long long* timeout) {
+  if (*(volatile const unsigned long long*)timeout) return;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nc = 5 * ncell, nb = 3 * ncell;
+  for (long long i = t0; i < nc; i += nth) cons[i] = U1[i];
+  for (long long i = t0; i < nb; i += nth) b[i] = B1[i];
+}
+
 typedef void (*StageKernel)(BatchDev);
 
 template <int RC>
@@ -538,6 +554,17 @@ mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc) {
   return B;
 }
 
+// A barrier gave up in a step since the last report: clear the sticky flag (steps run again from
+// the next call) and return the error.
+mhd_status report_timeout(mhd_batch* b) {
+  cudaError_t e = cudaMemsetAsync(b->counters + 7, 0, sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "clear the barrier flag");
+  return bfail(b, MHD_ERR_TIMEOUT,
+               "a grid barrier of the batched stage gave up waiting; the steps since the last check left the "
+               "state unchanged");
+}
+
 // enqueue one whole step on the stream (also used for graph capture)
 mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta,
                         cudaStream_t st) {
@@ -550,7 +577,9 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
   if (per_sm < 1) return bfail(b, MHD_ERR_CUDA, "stage kernel cannot be resident");
   const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, per_sm) : per_sm;
   const unsigned grid = (unsigned)(b->nsm * bps);
-  e = cudaMemsetAsync(b->counters, 0, 8 * sizeof(unsigned long long), st);
+  // counters 0..6 start each step at zero; counter 7 (a barrier gave up) is cleared only when
+  // mhd_batch_last_dt or mhd_batch_stats reports it
+  e = cudaMemsetAsync(b->counters, 0, 7 * sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 2 * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ptime, 0, 16 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
@@ -574,10 +603,8 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
     e = cudaLaunchKernelExC(&lc, (const void*)k, args);
     if (e != cudaSuccess) return bcuda(b, e, "cooperative stage launch");
   }
-  e = cudaMemcpyAsync(s->cons, b->U1, 5 * b->ncell * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->b, b->B1, 3 * b->ncell * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  mhd::k_batch_copy_back<<<b->nsm * 8, 256, 0, st>>>(b->U1, s->cons, b->B1, s->b, b->ncell, b->counters + 7);
+  e = cudaGetLastError();
   return bcuda(b, e, "batch step enqueue");
 }
 
@@ -774,7 +801,7 @@ mhd_status mhd_batch_last_dt(mhd_batch* b, double* dt) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   mhd_status s = bcuda(b, e, "read dt");
   if (s != MHD_OK) return s;
-  if (h[7]) return bfail(b, MHD_ERR_TIMEOUT, "a grid barrier of the batched stage gave up waiting");
+  if (h[7]) return report_timeout(b);
   if (h[6]) return bfail(b, MHD_ERR_NONFINITE, "signal speed not finite: no step taken");
   return MHD_OK;
 }
@@ -788,7 +815,7 @@ mhd_status mhd_batch_stats(mhd_batch* b, long long* s1, long long* s2) {
   if (s != MHD_OK) return s;
   if (s1) *s1 = (long long)h[0];
   if (s2) *s2 = (long long)h[1];
-  if (h[7]) return bfail(b, MHD_ERR_TIMEOUT, "a grid barrier of the batched stage gave up waiting");
+  if (h[7]) return report_timeout(b);
   return MHD_OK;
 }
 

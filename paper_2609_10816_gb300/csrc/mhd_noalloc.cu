@@ -1,9 +1,8 @@
 // mhd_noalloc.cu -- mhd_step_noalloc: one step of a small periodic box that allocates nothing.
 //
-// Some callers cannot let a library allocate device memory: code that records the step inside a
-// CUDA stream capture (where cudaMalloc is not allowed), applications whose memory manager owns
-// every byte of the device, and tight loops that cannot afford cudaMalloc's implicit
-// synchronisation. For them this entry point runs the same kernels as mhd_step, with all of the
+// Some callers cannot let a library allocate device memory: applications whose own memory
+// manager owns every byte of the device (a pool that cannot have a library allocate beside it),
+// and tight loops that cannot afford cudaMalloc's implicit device synchronisation. For them this entry point runs the same kernels as mhd_step, with all of the
 // step's scratch in one fixed device array defined below. The array has a fixed size, so the
 // entry point takes boxes of at most MHD_NOALLOC_MAX_CELLS cells; it exists, and occupies
 // device memory, on every GPU that loads the library, until the process exits.

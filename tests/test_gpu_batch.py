@@ -5,7 +5,7 @@ import torch
 
 import oracle
 from paper_2609_10816_gb300 import inputs, mhd
-from tests.util import state_errors
+from tests.util import parity_failures
 
 pytestmark = pytest.mark.gpu
 
@@ -81,8 +81,38 @@ def test_batch_patches_against_oracle(gpu_lib):
     for p, d in enumerate(dims):
         co, bo, _ = oracle.step(cfgs[p], *pats[p], dt)
         c1, b1 = bt.unpack(cons, b, p)
-        errs = state_errors(c1, b1, co, bo)
-        assert all(v <= 1e-12 for v in errs.values()), (p, errs)
+        bad = parity_failures(c1, b1, co, bo)
+        assert not bad, (p, bad)
+
+
+def test_batch_ppm_hlld_patches_against_oracle(gpu_lib):
+    """The benchmarked batch scheme (PPM + HLLD + Q26 + LD04) on patches with edges drawn from the
+    batch workload's {16, 24, 32, 48, 64}, with the autotuned schedule and graph replay, against
+    the oracle patch by patch; one near-vacuum patch sets flux-correction flags."""
+    rng = np.random.default_rng(17)
+    dims = [tuple(int(x) for x in rng.choice((16, 24, 32, 48, 64), size=3)) for _ in range(7)]
+    pats = [inputs.random_patch(d, rng, h=H)[:2] for d in dims]
+    dims.append((16, 16, 16))
+    pats.append(_low_pressure_patch((16, 16, 16), seed=3))
+    bt = mhd.Batch(dims, H)
+    cons, b = bt.pack(pats)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    bt.tune(cons, b, 0.6, sch)
+    bt.step(cons, b, 0.6, sch, 0.0)  # CFL 0.6: the near-vacuum patch's high-order step fails
+    dt = bt.last_dt()
+    flagged = bt.stats()
+    cfgs = [oracle.Config(shape=d, h=(H, H, H), recon="ppm", riemann="hlld") for d in dims]
+    assert dt == pytest.approx(min(oracle.max_dt(c, *pats[p], 0.6) for p, c in enumerate(cfgs)), rel=1e-14)
+    tot = [0, 0]
+    for p, d in enumerate(dims):
+        co, bo, cnt = oracle.step(cfgs[p], *pats[p], dt)
+        tot[0] += cnt[0]
+        tot[1] += cnt[1]
+        c1, b1 = bt.unpack(cons, b, p)
+        bad = parity_failures(c1, b1, co, bo)
+        assert not bad, (p, d, bad)
+    assert tuple(tot) == flagged and tot[0] > 0
+    bt.close()
 
 
 def test_batch_autotune_keeps_results(gpu_lib):
@@ -107,12 +137,19 @@ def test_batch_barrier_wait_is_bounded(gpu_lib):
     bt = mhd.Batch(dims, H)
     cons, b = bt.pack(pats)
     sch = mhd.scheme("plm_mc", "hll", "q26")
+    c_in, b_in = cons.clone(), b.clone()
     bt.test_barrier(1, 2000)  # every barrier waits for one block that is never launched
     bt.step(cons, b, 0.3, sch)
+    torch.cuda.synchronize()
+    assert torch.equal(cons, c_in) and torch.equal(b, b_in)  # the abandoned step left the state
+    bt.test_barrier(0, 1 << 25)
+    bt.step(cons, b, 0.3, sch)  # the timeout is not read yet: this step does nothing either
+    torch.cuda.synchronize()
+    assert torch.equal(cons, c_in) and torch.equal(b, b_in)
     with pytest.raises(mhd.MHDError) as ei:
         bt.last_dt()
     assert ei.value.code == mhd.ERR_TIMEOUT
-    bt.test_barrier(0, 1 << 25)
+    assert bt.stats() == (0, 0)  # the report cleared the condition
     c2, b2 = bt.pack(pats)
     bt.step(c2, b2, 0.3, sch)
     assert bt.last_dt() > 0

@@ -1,8 +1,8 @@
 """mhd_step_noalloc against mhd_step (GPU).
 
-mhd_step_noalloc serves callers that cannot let the library allocate device memory (a step
-recorded inside a stream capture, a memory manager that owns the device, loops that cannot
-afford cudaMalloc's synchronisation): it runs the step with its scratch in a fixed device array
+mhd_step_noalloc serves callers that cannot let the library allocate device memory (an
+application whose own memory manager owns the device, loops that cannot afford cudaMalloc's
+synchronisation): it runs the step with its scratch in a fixed device array
 inside libmhd.so. This test calls it through the C ABI twice in a row on different boxes and
 compares each result with mhd_step's, at the parity tolerance of the other GPU tests; the first
 call sets flux-correction flags and counters in the shared array, so leftovers would show in the

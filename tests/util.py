@@ -1,6 +1,14 @@
 """Shared helpers for the tests (no method arithmetic)."""
 import numpy as np
 
+# Parity bars of the CUDA path against the oracle, per stored field and step:
+#   relative L1 sum|gpu - oracle| / max(sum|oracle|, N * scale) <= L1_TOL, and, element by element,
+#   max|gpu - oracle| / max(mean|oracle|, scale) <= MAX_TOL, so that one wrong cell cannot hide in
+#   the sum of a large box.
+L1_TOL = 1e-12
+MAX_TOL = 1e-11
+
+
 # natural scales of each stored field family, used to floor relative-L1 denominators so that
 # perturbation-sized fields (momentum of a 1e-6 wave) are not judged on roundoff alone
 def field_scales(cons, b):
@@ -20,14 +28,35 @@ def rel_l1(got, ref, scale):
     return float(np.abs(got - ref).sum()) / den
 
 
-def state_errors(cg, bg, co, bo, scales=None):
+def rel_max(got, ref, scale):
+    """max |got - ref| / max(mean |ref|, scale): the element-wise companion of rel_l1."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    if ref.size == 0:
+        return 0.0
+    den = max(float(np.abs(ref).mean()), scale)
+    return float(np.abs(got - ref).max()) / den
+
+
+NAMES = ["rho", "m0", "m1", "m2", "e", "b0", "b1", "b2"]
+
+
+def state_errors(cg, bg, co, bo, scales=None, norm=rel_l1):
     if scales is None:
         scales = field_scales(co, bo)
     sc, sb = scales
     errs = {}
-    names = ["rho", "m0", "m1", "m2", "e"]
     for v in range(5):
-        errs[names[v]] = rel_l1(cg[v], co[v], sc[v])
+        errs[NAMES[v]] = norm(cg[v], co[v], sc[v])
     for d in range(3):
-        errs[f"b{d}"] = rel_l1(bg[d], bo[d], sb[d])
+        errs[NAMES[5 + d]] = norm(bg[d], bo[d], sb[d])
     return errs
+
+
+def parity_failures(cg, bg, co, bo, scales=None, l1_tol=L1_TOL, max_tol=MAX_TOL):
+    """Fields that miss either bar: {name: (rel L1, rel max)}; empty when the states agree."""
+    if scales is None:
+        scales = field_scales(co, bo)
+    l1 = state_errors(cg, bg, co, bo, scales)
+    mx = state_errors(cg, bg, co, bo, scales, norm=rel_max)
+    return {k: (l1[k], mx[k]) for k in l1 if not (l1[k] <= l1_tol and mx[k] <= max_tol)}
