@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mhd_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-RECON = {"pc": 0, "plm_mc": 1, "plm_minmod": 2, "ppm": 3}
+RECON = {"pc": 0, "plm_mc": 1, "plm_minmod": 2, "ppm": 3, "ppm_ep": 4}
 RIEMANN = {"hll": 0, "hlld": 1, "llf": 2}
 EMF = {"q26": 0, "fs18": 1, "b25a": 2}
 

@@ -42,6 +42,19 @@
 //      every cell; invalid first-order results are accepted.
 //   R10 time step (Sec. 2.4): per-cell signal speed max_d (|u_d| + c_f,d) dx_min/dx_d and
 //      2 eta / dx_min; dt = CFL dx_min / max speed.
+//   R11 PPM-EP (Sec. 2.2 cites Rider, Greenough & Kamm 2007 and does not define it): the
+//      parabola of PPM with the unlimited fourth-order interface value, and the monotonicity
+//      limiting in its median-function form, switched off at extrema that are smooth. With the
+//      differences d_{j+1/2} = q_{j+1} - q_j and curvatures D_j = d_{j+1/2} - d_{j-1/2}:
+//      interface j+1/2 lies at an extremum when two of d_{j-1/2}, d_{j+1/2}, d_{j+3/2} have
+//      strictly opposite signs (a peak or trough in one cell, or shared by two equal cells), and
+//      cell j when one of its two interfaces does. The interface value is
+//      (7 (q_j + q_{j+1}) - (q_{j-1} + q_{j+2})) / 12, bounded to median(q_j, ., q_{j+1}) unless it
+//      lies at an extremum with D_j, D_{j+1} both > 0 or both < 0. Cell j then takes the CW84
+//      Eq. 1.10 constraints (in median form aR <- median(q_j, aR, 3 q_j - 2 aL) and
+//      aL <- median(q_j, aL, 3 q_j - 2 aR)) unless it lies at an extremum with D_{j-1}, D_j, D_{j+1}
+//      all > 0 or all < 0: a smooth extremum keeps its parabola, while a discontinuity (where the
+//      curvature changes sign) and the monotone foot of a jump are limited as in PPM.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -112,7 +125,7 @@ template <class T> inline bool same_sign(T a, T b) {
 // ---------------------------------------------------------------------------------------
 // Configuration and grid
 // ---------------------------------------------------------------------------------------
-enum { REC_PC = 0, REC_PLM_MC = 1, REC_PLM_MINMOD = 2, REC_PPM = 3 };
+enum { REC_PC = 0, REC_PLM_MC = 1, REC_PLM_MINMOD = 2, REC_PPM = 3, REC_PPM_EP = 4 };
 enum { RS_HLL = 0, RS_HLLD = 1, RS_LLF = 2 };
 enum { EMF_Q26 = 0, EMF_FS18 = 1, EMF_B25A = 2 };
 
@@ -196,6 +209,24 @@ template <class T> T slope_vl(T qm1, T q0, T qp1) {
   return sgn(dc) * mn(mn(absv(dc), 2.0 * absv(dl)), 2.0 * absv(dr));
 }
 
+// CW84 Eq. 1.10: the parabola (aL, a, aR) of a cell made monotone.
+template <class T> void cw84_monotone(T a, T& aL, T& aR) {
+  if (!same_sign(aR - a, a - aL)) {
+    aL = a;
+    aR = a;
+  } else {
+    const T da = aR - aL;
+    const T a6 = 6.0 * (a - 0.5 * (aL + aR));
+    if (val(da * a6) > val(da * da)) {
+      aL = 3.0 * a - 2.0 * aR;
+    } else if (val(-(da * da)) > val(da * a6)) {
+      aR = 3.0 * a - 2.0 * aL;
+    }
+  }
+}
+// the middle one of three values
+template <class T> T median3(T a, T b, T c) { return mx(mn(a, b), mn(mx(a, b), c)); }
+
 template <class T>
 void recon_field(const Grid& g, int method, const T* q, int d, std::vector<T>& qm,
                  std::vector<T>& qp) {
@@ -216,6 +247,34 @@ void recon_field(const Grid& g, int method, const T* q, int d, std::vector<T>& q
     }
     return;
   }
+  if (method == REC_PPM_EP) {  // reading R11
+    // dif[X] = d_{X-1/2} = q[X] - q[X-1]; curv[X] = D_X; face[X] = interface value at X - 1/2,
+    // ext[X] = whether interface X - 1/2 lies at an extremum
+    std::vector<T> dif(N), curv(N), face(N);
+    std::vector<char> ext(N);
+    for (long X = 0; X < N; ++X) dif[X] = q[X] - q[g.sh(X, d, -1)];
+    for (long X = 0; X < N; ++X) curv[X] = dif[g.sh(X, d, 1)] - dif[X];
+    auto opposite = [](T a, T b) { return (val(a) > 0 && val(b) < 0) || (val(a) < 0 && val(b) > 0); };
+    for (long X = 0; X < N; ++X) {
+      const T dm = dif[g.sh(X, d, -1)], d0 = dif[X], dp = dif[g.sh(X, d, 1)];
+      ext[X] = opposite(dm, d0) || opposite(d0, dp) || opposite(dm, dp);
+    }
+    for (long X = 0; X < N; ++X) {
+      const long Xm = g.sh(X, d, -1);
+      face[X] = (7.0 * (q[Xm] + q[X]) - (q[g.sh(X, d, -2)] + q[g.sh(X, d, 1)])) / 12.0;
+      if (!(ext[X] && same_sign(curv[Xm], curv[X]))) face[X] = median3(q[Xm], face[X], q[X]);
+    }
+    for (long X = 0; X < N; ++X) {
+      const long Xp = g.sh(X, d, 1);
+      T aL = face[X], aR = face[Xp];
+      const T cm = curv[g.sh(X, d, -1)], c0 = curv[X], cp = curv[Xp];
+      const bool smooth_extremum = (ext[X] || ext[Xp]) && same_sign(cm, c0) && same_sign(c0, cp);
+      if (!smooth_extremum) cw84_monotone(q[X], aL, aR);
+      qm[X] = aL;
+      qp[X] = aR;
+    }
+    return;
+  }
   // PPM, reading R3.
   std::vector<T> dq(N), face(N);  // face[X] = interface value at X - 1/2
   for (long X = 0; X < N; ++X) dq[X] = slope_vl(q[g.sh(X, d, -1)], q[X], q[g.sh(X, d, 1)]);
@@ -226,21 +285,8 @@ void recon_field(const Grid& g, int method, const T* q, int d, std::vector<T>& q
     face[X] = 0.5 * (q[Xm] + q[X]) - (dq[X] - dq[Xm]) / 6.0;
   }
   for (long X = 0; X < N; ++X) {
-    const T a = q[X];
     T aL = face[X], aR = face[g.sh(X, d, 1)];
-    // CW84 Eq. 1.10.
-    if (!same_sign(aR - a, a - aL)) {
-      aL = a;
-      aR = a;
-    } else {
-      const T da = aR - aL;
-      const T a6 = 6.0 * (a - 0.5 * (aL + aR));
-      if (val(da * a6) > val(da * da)) {
-        aL = 3.0 * a - 2.0 * aR;
-      } else if (val(-(da * da)) > val(da * a6)) {
-        aR = 3.0 * a - 2.0 * aL;
-      }
-    }
+    cw84_monotone(q[X], aL, aR);  // CW84 Eq. 1.10
     qm[X] = aL;
     qp[X] = aR;
   }
