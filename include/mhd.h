@@ -35,7 +35,7 @@ typedef enum {
   MHD_ERR_ARG = 1,         /* bad argument (null pointer, size, dt <= 0, eta < 0, scheme bits) */
   MHD_ERR_CUDA = 2,        /* a CUDA runtime call failed; see mhd_last_error */
   MHD_ERR_NONFINITE = 3,   /* a non-finite value was produced and flux correction was off */
-  MHD_ERR_UNSUPPORTED = 4, /* a scheme the paper names but does not define (B25b, PPM-EP) */
+  MHD_ERR_UNSUPPORTED = 4, /* a scheme the paper names but does not define (B25b averaging) */
   MHD_ERR_TIMEOUT = 5      /* a bounded device wait gave up (persistent batched kernel) */
 } mhd_status;
 
@@ -46,7 +46,9 @@ enum {
   MHD_RECON_PLM_MC = 1,      /* piecewise linear, monotonised-central limiter */
   MHD_RECON_PLM_MINMOD = 2,  /* piecewise linear, minmod limiter */
   MHD_RECON_PPM = 3,         /* piecewise parabolic, Colella & Woodward 1984 limiting */
-  MHD_RECON_PPM_EP = 4,      /* extremum-preserving PPM: not defined in the paper -> UNSUPPORTED */
+  MHD_RECON_PPM_EP = 4,      /* extremum-preserving PPM (Sec. 2.2, citing Rider, Greenough & Kamm
+                                2007): fourth-order interfaces, CW84 limiting relaxed at smooth
+                                extrema */
   MHD_RIEMANN_HLL = 0 << 4,  /* two-wave HLL with the Eq. (alpha-pm) speeds */
   MHD_RIEMANN_HLLD = 1 << 4, /* Miyoshi & Kusano 2005 HLLD */
   MHD_RIEMANN_LLF = 2 << 4,  /* local Lax-Friedrichs (Rusanov) */

@@ -72,6 +72,41 @@ __device__ __forceinline__ void recon_jac(const double* q, double* JL, double* J
     const double h1 = -gl, h2 = gl - gr, h3 = gr;
     JL[1] = -h1; JL[2] = 1.0 - h2; JL[3] = -h3;
     JR[1] = h1;  JR[2] = 1.0 + h2; JR[3] = h3;
+  } else if (R == REC_PPM_EP) {
+    // the decisions of Rec<REC_PPM_EP> on the same window
+    const double e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3];
+    const int s0 = sgn_code(e0), s1 = sgn_code(e1), s2 = sgn_code(e2), s3 = sgn_code(e3);
+    const int ka = sgn_code(e1 - e0), kb = sgn_code(e2 - e1), kc = sgn_code(e3 - e2);
+    const bool xa = ext_code(s0, s1, s2), xb = ext_code(s1, s2, s3);
+    int pa, pb;  // 0: fourth-order value, 1: the lower cell's value, 2: the upper cell's
+    const double aL = ppm_ep_face(q[0], q[1], q[2], q[3], xa && same_code(ka, kb), pa);
+    const double aR = ppm_ep_face(q[1], q[2], q[3], q[4], xb && same_code(kb, kc), pb);
+    if (pa == 0) {
+      JL[0] = -1.0 / 12.0; JL[1] = 7.0 / 12.0; JL[2] = 7.0 / 12.0; JL[3] = -1.0 / 12.0;
+    } else {
+      JL[pa == 1 ? 1 : 2] = 1.0;
+    }
+    if (pb == 0) {
+      JR[1] = -1.0 / 12.0; JR[2] = 7.0 / 12.0; JR[3] = 7.0 / 12.0; JR[4] = -1.0 / 12.0;
+    } else {
+      JR[pb == 1 ? 2 : 3] = 1.0;
+    }
+    if (!((xa || xb) && same_code(ka, kb) && same_code(kb, kc))) {
+      const int mc = ppm_mono_case(aR - q[2], q[2] - aL);
+      if (mc == PPM_FLAT) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) JL[k] = JR[k] = 0.0;
+        JL[2] = JR[2] = 1.0;
+      } else if (mc == PPM_FIX_L) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) JL[k] = -2.0 * JR[k];
+        JL[2] += 3.0;
+      } else if (mc == PPM_FIX_R) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) JR[k] = -2.0 * JL[k];
+        JR[2] += 3.0;
+      }
+    }
   } else {
     const double e0 = q[1] - q[0], e1 = q[2] - q[1], e2 = q[3] - q[2], e3 = q[4] - q[3];
     double a0, b0, a1, b1, a2, b2;  // d_k = a_k e_k + b_k e_(k+1)
@@ -730,7 +765,8 @@ void launch_adj_flux(const AdjDev& A, int recon, int rs, cudaStream_t st) {
     case REC_PC: adj_flux_r<REC_PC>(A, rs, st); break;
     case REC_PLM_MC: adj_flux_r<REC_PLM_MC>(A, rs, st); break;
     case REC_PLM_MINMOD: adj_flux_r<REC_PLM_MINMOD>(A, rs, st); break;
-    default: adj_flux_r<REC_PPM>(A, rs, st); break;
+    case REC_PPM: adj_flux_r<REC_PPM>(A, rs, st); break;
+    default: adj_flux_r<REC_PPM_EP>(A, rs, st); break;
   }
 }
 

@@ -59,10 +59,8 @@ mhd_status decode(mhd_ctx* c, int scheme, Decoded& d) {
   d.avg = (scheme >> 12) & 0xf;
   d.fofc = !(scheme & MHD_FOFC_OFF);
   if (scheme & ~(0xffff | MHD_FOFC_OFF)) return fail(c, MHD_ERR_ARG, "unknown scheme bits");
-  if (d.recon == MHD_RECON_PPM_EP)
-    return fail(c, MHD_ERR_UNSUPPORTED, "PPM-EP is cited but not defined in the paper");
   if (d.avg == 1) return fail(c, MHD_ERR_UNSUPPORTED, "B25b averaging is cited but not defined in the paper");
-  if (d.recon > 3 || d.rs > 2 || d.emf > 2 || d.avg > 1) return fail(c, MHD_ERR_ARG, "scheme field out of range");
+  if (d.recon > 4 || d.rs > 2 || d.emf > 2 || d.avg > 1) return fail(c, MHD_ERR_ARG, "scheme field out of range");
   return MHD_OK;
 }
 

@@ -377,7 +377,8 @@ static StageKernel stage_kernel(int recon, int rs) {
     case REC_PC: return pick_rs<REC_PC>(rs);
     case REC_PLM_MC: return pick_rs<REC_PLM_MC>(rs);
     case REC_PLM_MINMOD: return pick_rs<REC_PLM_MINMOD>(rs);
-    default: return pick_rs<REC_PPM>(rs);
+    case REC_PPM: return pick_rs<REC_PPM>(rs);
+    default: return pick_rs<REC_PPM_EP>(rs);
   }
 }
 
@@ -752,9 +753,8 @@ mhd_status mhd_batch_step(mhd_batch* b, const mhd_batch_state* s, double cfl, in
   if (!(eta >= 0) || !(eta < 1e300)) return bfail(b, MHD_ERR_ARG, "eta must be finite and >= 0");
   if (scheme & ~(0xffff | MHD_FOFC_OFF)) return bfail(b, MHD_ERR_ARG, "unknown scheme bits");
   const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf, emf = (scheme >> 8) & 0xf, avg = (scheme >> 12) & 0xf;
-  if (recon == MHD_RECON_PPM_EP || avg == 1)
-    return bfail(b, MHD_ERR_UNSUPPORTED, "PPM-EP and B25b are cited but not defined in the paper");
-  if (recon > 3 || rs > 2 || emf > 2 || avg > 1) return bfail(b, MHD_ERR_ARG, "scheme field out of range");
+  if (avg == 1) return bfail(b, MHD_ERR_UNSUPPORTED, "B25b averaging is cited but not defined in the paper");
+  if (recon > 4 || rs > 2 || emf > 2 || avg > 1) return bfail(b, MHD_ERR_ARG, "scheme field out of range");
   if (emf != mhd::EMF_Q26) return bfail(b, MHD_ERR_UNSUPPORTED, "the batched step runs the Q26 EMF compute");
   const bool same = b->params_ok && b->built_cons == s->cons && b->built_b == s->b && b->built_scheme == scheme &&
                     b->built_eta == eta && b->built_cfl == cfl;

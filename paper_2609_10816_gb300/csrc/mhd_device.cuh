@@ -13,7 +13,7 @@ namespace mhd {
 
 using ::fma;  // the double overload stays visible beside the Dual one below
 
-enum { REC_PC = 0, REC_PLM_MC = 1, REC_PLM_MINMOD = 2, REC_PPM = 3 };
+enum { REC_PC = 0, REC_PLM_MC = 1, REC_PLM_MINMOD = 2, REC_PPM = 3, REC_PPM_EP = 4 };
 enum { RS_HLL = 0, RS_HLLD = 1, RS_LLF = 2 };
 enum { EMF_Q26 = 0, EMF_FS18 = 1, EMF_B25A = 2 };
 
@@ -359,6 +359,102 @@ template <> struct Rec<REC_PPM> {
     dq = dn;
     d1 = d2;
     f1 = f2;
+  }
+};
+
+// PPM-EP, the extremum-preserving PPM that Sec. 2.2 cites (Rider, Greenough & Kamm 2007) without
+// defining it; the reading taken: the fourth-order interface value
+// (7 (q_j + q_{j+1}) - (q_{j-1} + q_{j+2})) / 12 is bounded by its two cells (median form), and a
+// cell's parabola takes the CW84 constraints of PPM above, except at smooth extrema. An interface
+// lies at an extremum when two of the three differences around it (d_{j-1/2}, d_{j+1/2},
+// d_{j+3/2}, d_{k+1/2} = q_{k+1} - q_k) have strictly opposite signs, a cell when one of its two
+// interfaces does; "smooth" means the curvatures D_k = d_{k+1/2} - d_{k-1/2} of the two cells of
+// the interface (of the cell and its two neighbours) are all > 0 or all < 0. Differences and
+// curvatures are formed as differences of differences (no FMA), so their signs are exactly those of
+// the definition evaluated in plain FP64.
+// Only the signs of differences and curvatures are used: they are carried as 2-bit codes
+// (1 positive, 2 negative, 0 zero), decided on the integer pipe.
+__device__ __forceinline__ int sgn_code(double x) { return (int)gt0(x) | ((int)lt0(x) << 1); }
+__device__ __forceinline__ bool opp_code(int a, int b) { return (a | b) == 3; }
+__device__ __forceinline__ bool same_code(int a, int b) { return a == b && a != 0; }
+// an interface lies at an extremum: two of the differences around it of strictly opposite sign
+__device__ __forceinline__ bool ext_code(int sm, int s0, int sp) {
+  return opp_code(sm, s0) || opp_code(s0, sp) || opp_code(sm, sp);
+}
+// which of a, b, c is the median, ties resolved as vmin / vmax resolve them: 0, 1 or 2
+template <class T>
+__device__ __forceinline__ int median3_pick(T a, T b, T c) {
+  const long long ka = okey(val(a)), kb = okey(val(b)), kc = okey(val(c));
+  const int lo = ka <= kb ? 0 : 1, hi = ka >= kb ? 0 : 1;
+  const long long klo = lo == 0 ? ka : kb, khi = hi == 0 ? ka : kb;
+  const int m = khi <= kc ? hi : 2;
+  const long long km = m == 2 ? kc : khi;
+  return klo >= km ? lo : m;
+}
+template <class T>
+__device__ __forceinline__ T ppm_ep_iface(T qa, T qb, T qc, T qd) {
+  return fma(7.0 / 12.0, qa + qb, (qc + qd) * (-1.0 / 12.0));
+}
+// Interface between qa and qb (outer neighbours qc before qa, qd after qb); keep: it lies at a
+// smooth extremum (no bound). pick: 0 the fourth-order value, 1 qa, 2 qb.
+template <class T>
+__device__ __forceinline__ T ppm_ep_face(T qc, T qa, T qb, T qd, bool keep, int& pick) {
+  const T f = ppm_ep_iface(qa, qb, qc, qd);
+  pick = 0;
+  if (!keep) {
+    const int k = median3_pick(qa, f, qb);
+    pick = k == 0 ? 1 : (k == 1 ? 0 : 2);
+  }
+  return pick == 0 ? f : (pick == 1 ? qa : qb);
+}
+
+template <> struct Rec<REC_PPM_EP> {
+  static constexpr int LB = 3, LA = 2;
+  double q0, q1, q2;  // q[m-1], q[m], q[m+1]
+  double dq;          // q[m+1] - q[m]
+  double f1;          // interface value at m - 1/2
+  double aRprev;      // upper value of point m-1
+  // sign codes: bits 0-1 of q[m] - q[m-1], 2-3 and 4-5 of the curvatures of points m-1 and m;
+  // bit 6: interface m - 1/2 lies at an extremum
+  int code;
+  __device__ __forceinline__ void init(const double* v) {  // v = q[m0-3 .. m0+1]
+    const double e0 = v[1] - v[0], e1 = v[2] - v[1], e2 = v[3] - v[2], e3 = v[4] - v[3];
+    const int s0 = sgn_code(e0), s1 = sgn_code(e1), s2 = sgn_code(e2), s3 = sgn_code(e3);
+    // curvature codes of points m0-2, m0-1, m0
+    const int ka = sgn_code(e1 - e0), kb = sgn_code(e2 - e1), kc = sgn_code(e3 - e2);
+    const bool xa = ext_code(s0, s1, s2), xb = ext_code(s1, s2, s3);
+    int p;
+    const double fa = ppm_ep_face(v[0], v[1], v[2], v[3], xa && same_code(ka, kb), p);  // m0 - 3/2
+    const double fb = ppm_ep_face(v[1], v[2], v[3], v[4], xb && same_code(kb, kc), p);  // m0 - 1/2
+    double aL = fa, aR = fb;
+    if (!((xa || xb) && same_code(ka, kb) && same_code(kb, kc))) ppm_mono(v[2], aL, aR);
+    aRprev = aR;
+    q0 = v[2];
+    q1 = v[3];
+    q2 = v[4];
+    dq = e3;
+    f1 = fb;
+    code = s2 | (kb << 2) | (kc << 4) | ((int)xb << 6);
+  }
+  __device__ __forceinline__ void step(double qn, double& L, double& R) {
+    const double dn = qn - q2;  // q[m+2] - q[m+1]
+    const int sm = code & 3, c0 = (code >> 2) & 3, c1 = (code >> 4) & 3;
+    const bool x1 = code >> 6;
+    const int s0 = sgn_code(dq), sp = sgn_code(dn), cn = sgn_code(dn - dq);  // cn: point m+1
+    const bool x2 = ext_code(sm, s0, sp);
+    int p;
+    const double f2 = ppm_ep_face(q0, q1, q2, qn, x2 && same_code(c1, cn), p);  // m + 1/2
+    double aL = f1, aR = f2;
+    if (!((x1 || x2) && same_code(c0, c1) && same_code(c1, cn))) ppm_mono(q1, aL, aR);
+    L = aRprev;
+    R = aL;
+    aRprev = aR;
+    q0 = q1;
+    q1 = q2;
+    q2 = qn;
+    dq = dn;
+    f1 = f2;
+    code = s0 | (c1 << 2) | (cn << 4) | ((int)x2 << 6);
   }
 };
 

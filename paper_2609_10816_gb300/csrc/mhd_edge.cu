@@ -119,7 +119,8 @@ void launch_edges_bt(const Dev& d, int recon, int seg, cudaStream_t st) {
     case REC_PC: edges_bt_r<REC_PC>(d, seg, st); break;
     case REC_PLM_MC: edges_bt_r<REC_PLM_MC>(d, seg, st); break;
     case REC_PLM_MINMOD: edges_bt_r<REC_PLM_MINMOD>(d, seg, st); break;
-    default: edges_bt_r<REC_PPM>(d, seg, st); break;
+    case REC_PPM: edges_bt_r<REC_PPM>(d, seg, st); break;
+    default: edges_bt_r<REC_PPM_EP>(d, seg, st); break;
   }
 }
 void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st) {
@@ -127,7 +128,8 @@ void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st) {
     case REC_PC: edges_lr_r<REC_PC>(d, seg, st); break;
     case REC_PLM_MC: edges_lr_r<REC_PLM_MC>(d, seg, st); break;
     case REC_PLM_MINMOD: edges_lr_r<REC_PLM_MINMOD>(d, seg, st); break;
-    default: edges_lr_r<REC_PPM>(d, seg, st); break;
+    case REC_PPM: edges_lr_r<REC_PPM>(d, seg, st); break;
+    default: edges_lr_r<REC_PPM_EP>(d, seg, st); break;
   }
 }
 

@@ -55,7 +55,8 @@ void launch_face(const Dev& d, int dir, int recon, int rs, int seg, cudaStream_t
     case REC_PC: launch_face_r<REC_PC>(d, dir, rs, seg, st); break;
     case REC_PLM_MC: launch_face_r<REC_PLM_MC>(d, dir, rs, seg, st); break;
     case REC_PLM_MINMOD: launch_face_r<REC_PLM_MINMOD>(d, dir, rs, seg, st); break;
-    default: launch_face_r<REC_PPM>(d, dir, rs, seg, st); break;
+    case REC_PPM: launch_face_r<REC_PPM>(d, dir, rs, seg, st); break;
+    default: launch_face_r<REC_PPM_EP>(d, dir, rs, seg, st); break;
   }
 }
 

@@ -86,9 +86,8 @@ extern "C" mhd_status mhd_step_noalloc(const mhd_config* cfg, const mhd_state* s
   if (scheme & ~(0xffff | MHD_FOFC_OFF)) return fail(MHD_ERR_ARG, "unknown scheme bits");
   const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf, emf = (scheme >> 8) & 0xf, avg = (scheme >> 12) & 0xf;
   const bool fofc = !(scheme & MHD_FOFC_OFF);
-  if (recon == MHD_RECON_PPM_EP || avg == 1)
-    return fail(MHD_ERR_UNSUPPORTED, "PPM-EP and B25b are cited but not defined in the paper");
-  if (recon > 3 || rs > 2 || emf > 2 || avg > 1) return fail(MHD_ERR_ARG, "scheme field out of range");
+  if (avg == 1) return fail(MHD_ERR_UNSUPPORTED, "B25b averaging is cited but not defined in the paper");
+  if (recon > 4 || rs > 2 || emf > 2 || avg > 1) return fail(MHD_ERR_ARG, "scheme field out of range");
   if (emf != mhd::EMF_Q26) return fail(MHD_ERR_UNSUPPORTED, "only the Q26 EMF compute runs without allocation");
 
   std::string err;

@@ -15,7 +15,8 @@ from paper_2609_10816_gb300 import adjoint, inputs, mhd
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("recon,rs", [("ppm", "hlld"), ("plm_mc", "hll"), ("plm_minmod", "llf"), ("pc", "hlld")])
+@pytest.mark.parametrize("recon,rs", [("ppm", "hlld"), ("plm_mc", "hll"), ("plm_minmod", "llf"), ("pc", "hlld"),
+                                     ("ppm_ep", "hlld")])
 @pytest.mark.parametrize("eta", [0.0, 3e-3])
 @pytest.mark.parametrize("shape", [(10, 8, 6), (7, 4, 2)])  # the second: windows wrap onto themselves
 def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta, shape):

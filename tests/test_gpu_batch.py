@@ -68,15 +68,16 @@ def test_batch_equals_single_box_steps(gpu_lib, use_graph):
     assert flagged[0] + flagged[1] >= 0
 
 
-def test_batch_patches_against_oracle(gpu_lib):
+@pytest.mark.parametrize("recon", ["plm_mc", "ppm_ep"])
+def test_batch_patches_against_oracle(gpu_lib, recon):
     dims, pats = _patches(6, seed=9, edges=(6, 8, 10))
     bt = mhd.Batch(dims, H)
     cons, b = bt.pack(pats)
-    sch = mhd.scheme("plm_mc", "hlld", "q26")
+    sch = mhd.scheme(recon, "hlld", "q26")
     bt.step(cons, b, 0.3, sch, 0.0)
     dt = bt.last_dt()
     # the batch dt is the CFL step over all patches
-    cfgs = [oracle.Config(shape=d, h=(H, H, H), recon="plm_mc", riemann="hlld") for d in dims]
+    cfgs = [oracle.Config(shape=d, h=(H, H, H), recon=recon, riemann="hlld") for d in dims]
     assert dt == pytest.approx(min(oracle.max_dt(c, *pats[p], 0.3) for p, c in enumerate(cfgs)), rel=1e-14)
     for p, d in enumerate(dims):
         co, bo, _ = oracle.step(cfgs[p], *pats[p], dt)

@@ -111,16 +111,18 @@ def test_turbulence_256cubed_sampled(gpu_lib, emf):
     assert worst <= 1e-12, worst
 
 
-@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
-def test_alfven_oblique_24cubed_full(gpu_lib, emf):
+@pytest.mark.parametrize("recon,emf", [("ppm", "q26"), ("ppm", "fs18"), ("ppm", "b25a"), ("ppm_ep", "q26"),
+                                      ("ppm_ep", "fs18"), ("ppm_ep", "b25a")])
+def test_alfven_oblique_24cubed_full(gpu_lib, recon, emf):
     """The throughput workload's oblique Alfven wave (k ~ (1, 2, 3), theta = pi/4) at 24^3,
-    PPM + HLLD, each EMF compute scheme: 5 CFL steps against the oracle on the whole box."""
+    PPM and the paper's PPM-EP with HLLD, each EMF compute scheme: 5 CFL steps against the oracle
+    on the whole box."""
     shape = (24, 24, 24)
     cons, b, info = inputs.alfven_oblique(shape)
-    cfg = oracle.Config(shape=shape, h=info["h"], recon="ppm", riemann="hlld", emf=emf)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann="hlld", emf=emf)
     ctx = mhd.Context(shape, info["h"])
     st = mhd.to_device(cons, b)
-    sch = mhd.scheme("ppm", "hlld", emf)
+    sch = mhd.scheme(recon, "hlld", emf)
     scales = field_scales(cons, b)
     co, bo = cons, b
     for _ in range(5):
@@ -136,17 +138,17 @@ def test_alfven_oblique_24cubed_full(gpu_lib, emf):
     assert md * info["h"][0] / mb <= 1e-13
 
 
-@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
-def test_alfven_oblique_128cubed_sampled(gpu_lib, emf):
-    """The same wave at the throughput run's 128^3: one full-size GPU step against the oracle
-    on three sampled sub-boxes."""
+@pytest.mark.parametrize("recon,emf", [("ppm", "q26"), ("ppm_ep", "q26"), ("ppm_ep", "fs18"), ("ppm_ep", "b25a")])
+def test_alfven_oblique_128cubed_sampled(gpu_lib, recon, emf):
+    """The same wave at the throughput run's 128^3 with the paper's PPM-EP (and plain PPM): one
+    full-size GPU step against the oracle on three sampled sub-boxes."""
     n = 128
     cons, b, info = inputs.alfven_oblique((n, n, n))
-    sch = mhd.scheme("ppm", "hlld", emf)
+    sch = mhd.scheme(recon, "hlld", emf)
     cg, bg, dt, div, _ = _gpu_step((n, n, n), info["h"], cons, b, sch, 0.0)
     assert div <= 1e-13
     centres = [(0, 0, 0), (64, 32, 100), (17, 90, 45)]
-    worst = _sampled_parity(cons, b, cg, bg, info["h"], dt, dict(recon="ppm", riemann="hlld", emf=emf), 0.0,
+    worst = _sampled_parity(cons, b, cg, bg, info["h"], dt, dict(recon=recon, riemann="hlld", emf=emf), 0.0,
                             centres)
     assert worst <= 1e-12, worst
 

@@ -31,7 +31,7 @@ def assert_parity(cg, bg, co, bo, what=""):
     assert not bad, f"{what}: (relative L1, relative max) above the bars: {bad}"
 
 
-COMBOS = [(r, s, e) for r in ("pc", "plm_mc", "plm_minmod", "ppm") for s in ("hll", "hlld", "llf")
+COMBOS = [(r, s, e) for r in ("pc", "plm_mc", "plm_minmod", "ppm", "ppm_ep") for s in ("hll", "hlld", "llf")
           for e in ("q26", "fs18", "b25a")]
 
 
@@ -51,7 +51,8 @@ def test_one_step_all_schemes(gpu_lib, recon, rs, emf, shape):
 @pytest.mark.parametrize("shape", [(16, 1, 1), (1, 12, 3), (2, 5, 9), (130, 3, 2)])
 def test_degenerate_and_ragged_boxes(gpu_lib, shape):
     cons, b, info = inputs.random_smooth(shape, seed=5, rough=0.02)
-    for recon, rs, emf in (("ppm", "hlld", "q26"), ("plm_mc", "hll", "fs18"), ("ppm", "llf", "b25a")):
+    for recon, rs, emf in (("ppm", "hlld", "q26"), ("plm_mc", "hll", "fs18"), ("ppm", "llf", "b25a"),
+                           ("ppm_ep", "hlld", "q26")):
         cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf=emf)
         dt = oracle.max_dt(cfg, cons, b, 0.3)
         co, bo, _ = oracle.step(cfg, cons, b, dt)
@@ -73,17 +74,17 @@ def _low_pressure_state(shape, seed=1):
     return inputs.assemble(rho, u, p, b), b, info
 
 
-@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
-def test_flux_correction_against_oracle(gpu_lib, emf):
+@pytest.mark.parametrize("recon,emf", [("ppm", "q26"), ("ppm", "fs18"), ("ppm", "b25a"), ("ppm_ep", "q26")])
+def test_flux_correction_against_oracle(gpu_lib, recon, emf):
     """Cells the high-order step leaves invalid take first-order fluxes: same flags and state."""
     shape = (16, 6, 4)
     cons, b, info = _low_pressure_state(shape)
-    cfg = oracle.Config(shape=shape, h=info["h"], recon="ppm", riemann="hlld", emf=emf, eta=1e-3)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann="hlld", emf=emf, eta=1e-3)
     dt = oracle.max_dt(cfg, cons, b, 0.6)
     co, bo, cnt = oracle.step(cfg, cons, b, dt)
     assert cnt[0] + cnt[1] > 0
     ctx = mhd.Context(shape, info["h"])
-    cg, bg, cntg = gpu_step(ctx, cons, b, dt, mhd.scheme("ppm", "hlld", emf), eta=1e-3)
+    cg, bg, cntg = gpu_step(ctx, cons, b, dt, mhd.scheme(recon, "hlld", emf), eta=1e-3)
     assert cntg == cnt
     assert_parity(cg, bg, co, bo, what=f"fofc {emf}")
 
