@@ -78,7 +78,7 @@ typedef struct mhd_ctx mhd_ctx; /* opaque: owns the scratch of one patch size an
 /* Create a context for one patch size. `cuda_stream` is a cudaStream_t (NULL = legacy default
  * stream); all work of the context is enqueued on it. Allocates the step's scratch
  * (112 doubles and one byte per cell, the FS18 / B25a intermediates included) with cudaMalloc on
- * the current device; the first mhd_step_adjoint adds 262 doubles per cell. *out is NULL on
+ * the current device; the first mhd_step_adjoint adds 306 doubles per cell. *out is NULL on
  * error. */
 mhd_status mhd_create(const mhd_config *cfg, void *cuda_stream, mhd_ctx **out);
 
@@ -149,10 +149,12 @@ mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches,
  * dL/dS^{n+1} (same layout as the state), on return dL/dS^n; *dL_deta (if not NULL) is increased
  * by the step's contribution to dL/d(eta). `state` is S^n (unchanged). Limiters, min/max and
  * Riemann-fan branches are differentiated on the branch the forward step takes (the forward
- * stage 1 is recomputed inside). The paper has no counterpart; it makes the step usable inside
- * gradient-based workflows. Covers the Q26 EMF compute and steps in which flux correction
- * flagged no cell (the caller checks mhd_stats of the forward step); the first call allocates
- * 262 doubles per cell of adjoint scratch. Synchronous when dL_deta is not NULL. */
+ * stages are recomputed inside, up to the stage-2 flags). Flux correction (Sec. 2.5) is
+ * differentiated with the cells it flagged held fixed: the first-order fluxes and EMFs of S^n on
+ * the masked faces and edges get their share of the adjoint, the high-order ones the rest. The
+ * paper has no counterpart; it makes the step usable inside gradient-based workflows. Covers the
+ * Q26 EMF compute; the first call allocates 306 doubles per cell of adjoint scratch. Synchronous
+ * when dL_deta is not NULL. */
 mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_state *lam, double dt, int scheme,
                             double eta, double *dL_deta);
 

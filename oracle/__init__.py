@@ -64,6 +64,7 @@ def _L():
         _lib.oracle_step.argtypes = [P(_Cfg), P(d), P(d), d, P(ctypes.c_longlong)]
         _lib.oracle_fluxes.argtypes = [P(_Cfg), P(d), P(d), P(d), P(d)]
         _lib.oracle_corner_emfs.argtypes = [P(_Cfg), P(d), P(d), P(d)]
+        _lib.oracle_fluxes_jvp.argtypes = [P(_Cfg), P(d), P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
         u8 = P(ctypes.c_ubyte)
         _lib.oracle_step_flags.argtypes = [P(_Cfg), P(d), P(d), d, u8, u8, P(ctypes.c_longlong)]
         _lib.oracle_prim.argtypes = [P(_Cfg), P(d), P(d), P(d)]
@@ -157,6 +158,19 @@ def fluxes(cfg: Config, cons: np.ndarray, b: np.ndarray):
     c = cfg.c()
     _L().oracle_fluxes(ctypes.byref(c), _ptr(cons), _ptr(b), _ptr(F), _ptr(E))
     return F, E
+
+
+def fluxes_jvp(cfg: Config, cons, b, dcons, db):
+    """Fluxes and EMFs of one state (as `fluxes`) and their directional derivative along
+    (dcons, db), exact on the branches the values take: (F, E, dF, dE)."""
+    _check(cfg, cons, b)
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (cons, b, dcons, db)]
+    nx, ny, nz = cfg.shape
+    F, dF = np.zeros((3, 5, nz, ny, nx)), np.zeros((3, 5, nz, ny, nx))
+    E, dE = np.zeros((3, nz, ny, nx)), np.zeros((3, nz, ny, nx))
+    c = cfg.c()
+    _L().oracle_fluxes_jvp(ctypes.byref(c), *[_ptr(x) for x in arrs], _ptr(F), _ptr(E), _ptr(dF), _ptr(dE))
+    return F, E, dF, dE
 
 
 def corner_emfs(cfg: Config, cons: np.ndarray, b: np.ndarray) -> np.ndarray:

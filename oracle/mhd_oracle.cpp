@@ -942,6 +942,23 @@ int oracle_corner_emfs(const oracle_cfg* c, const double* cons, const double* b,
   return 0;
 }
 
+// Fluxes and EMFs of one state with their directional derivative along (dcons, db), on dual
+// numbers (the branches taken on the values): flux, emf as in oracle_fluxes, dflux, demf tangents.
+int oracle_fluxes_jvp(const oracle_cfg* c, const double* cons, const double* b, const double* dcons,
+                      const double* db, double* flux, double* emf, double* dflux, double* demf) {
+  Grid g = make_grid(c->n, c->h, c->gamma);
+  const long N = g.N;
+  std::vector<Dual> U(5 * N), B(3 * N);
+  for (long i = 0; i < 5 * N; ++i) U[i] = Dual(cons[i], dcons[i]);
+  for (long i = 0; i < 3 * N; ++i) B[i] = Dual(b[i], db[i]);
+  const Scheme<Dual> sc = {c->recon, c->riemann, c->emf, Dual(c->eta, 0.0), c->eta != 0.0};
+  FluxSet<Dual> f;
+  fluxes_and_emfs(g, sc, U, B, f);
+  for (long i = 0; i < 15 * N; ++i) { flux[i] = f.F[i].v; dflux[i] = f.F[i].t; }
+  for (long i = 0; i < 3 * N; ++i) { emf[i] = f.E[i].v; demf[i] = f.E[i].t; }
+  return 0;
+}
+
 // Primitive variables (8N) of one state.
 int oracle_prim(const oracle_cfg* c, const double* cons, const double* b, double* prim) {
   Grid g = make_grid(c->n, c->h, c->gamma);

@@ -5,6 +5,8 @@ The forward pass runs the steps with a given (frozen) dt sequence and keeps the 
 library's hand-written adjoint step by step in reverse. Gradients flow to the initial conserved
 state, the initial face field and eta; anything upstream of those (for example an initial
 velocity field turned into momentum and energy with torch operations) is handled by autograd.
+Steps in which flux correction replaced fluxes are differentiated with the flagged cells held
+fixed, like every other branch of the step.
 """
 from __future__ import annotations
 
@@ -20,21 +22,16 @@ class MHDEvolve(torch.autograd.Function):
         etaf = float(eta)
         st = mhd.State(cons0.detach().contiguous().clone(), b0.detach().contiguous().clone())
         ckpts = [(st.cons.clone(), st.b.clone())]
-        flagged = 0
         for n, dt in enumerate(dts):
             ctx.step(st, float(dt), scheme, etaf)
-            s1, s2 = ctx.stats()
-            flagged += s1 + s2
             if (n + 1) % every == 0 and n + 1 < len(dts):
                 ckpts.append((st.cons.clone(), st.b.clone()))
         fctx.mctx, fctx.dts, fctx.scheme, fctx.every, fctx.eta = ctx, list(dts), scheme, every, etaf
-        fctx.ckpts, fctx.flagged = ckpts, flagged
+        fctx.ckpts = ckpts
         return st.cons, st.b
 
     @staticmethod
     def backward(fctx, gcons, gb):
-        if fctx.flagged:
-            raise RuntimeError("the adjoint of steps in which flux correction flagged cells is not built")
         ctx, dts, scheme, every, eta = fctx.mctx, fctx.dts, fctx.scheme, fctx.every, fctx.eta
         c0, b0 = fctx.ckpts[0]
         lam = mhd.State(torch.zeros_like(c0) if gcons is None else gcons.contiguous().clone(),

@@ -731,6 +731,179 @@ __global__ void __launch_bounds__(256) k_adj_update(Dev D, const double* lU, con
   }
 }
 
+// ---- first-order flux correction (Sec. 2.5): masks and the adjoint of the first-order fluxes ---
+// With the masks M1, M2 of the cells flagged after stage 1 and stage 2 frozen, the step is
+//   F1 = M1 FO(S^n) + (1 - M1) HO(S^n),        S^{n+1/2} = S^n + D F1,
+//   F2 = M2 FO(S^n) + (1 - M2) (F1 + HO(S^{n+1/2})) / 2,   S^{n+1} = S^n + D F2,
+// for the face fluxes and edge EMFs alike (a face is masked when one of its two cells is flagged,
+// an edge when one of its four cells is). Its transpose, for g = D^T lam: the stage-2 flux
+// function gets (1 - M2) g / 2, F1 gets k = (1 - M2) g / 2 + D^T lam_{n+1/2}, HO(S^n) gets
+// (1 - M1) k and FO(S^n) gets M2 g + M1 k.
+__device__ __forceinline__ bool face_masked(const Dev& D, const unsigned char* fl, int d, long long X) {
+  return fl[X] || fl[shift(D, X, d, -1)];
+}
+__device__ __forceinline__ bool edge_masked(const Dev& D, const unsigned char* fl, int e, long long X) {
+  const int a = (e + 1) % 3, c = (e + 2) % 3;
+  const long long Xa = shift(D, X, a, -1);
+  return fl[X] || fl[Xa] || fl[shift(D, X, c, -1)] || fl[shift(D, Xa, c, -1)];
+}
+// lF, lE <- scale g on faces and edges outside the mask of `fl`, 0 inside
+__global__ void __launch_bounds__(256) k_adj_mask(Dev D, const unsigned char* fl, const double* gF,
+                                                  const double* gE, double* lF, double* lE, double scale) {
+  const long long X = aid();
+  if (X >= D.N) return;
+  const long long N = D.N;
+  for (int d = 0; d < 3; ++d) {
+    const bool m = face_masked(D, fl, d, X);
+    for (int v = 0; v < 5; ++v) lF[(5LL * d + v) * N + X] = m ? 0.0 : scale * gF[(5LL * d + v) * N + X];
+    lE[d * N + X] = edge_masked(D, fl, d, X) ? 0.0 : scale * gE[d * N + X];
+  }
+}
+
+// adds the adjoint of cons -> prim (prim_from) of cell Y of S^n, given its 8 primitives' adjoints
+// lp, to lU (conserved variables) and lB (the cell's six faces): atomics, since several first-order
+// faces share a cell
+__device__ __forceinline__ void prim_vjp_atomic(const AdjDev& A, long long Y, const double* lp) {
+  const Dev& D = A.D;
+  const long long N = D.N;
+  double u[5], lo[3], hi[3];
+  load_cell(D, D.U0, D.B0, Y, u, lo, hi);
+  const double rho = u[0], rinv = rcp(rho);
+  const double ui[3] = {u[1] * rinv, u[2] * rinv, u[3] * rinv};
+  const double u2s = fma(ui[0], ui[0], fma(ui[1], ui[1], ui[2] * ui[2]));
+  const double leint = (D.gam - 1.0) * lp[4];  // p = (gamma - 1) eint
+  const double lq = -0.5 * leint;               // eint = e - (rho u2s + b2s) / 2
+  double lrinv = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double lu = fma(2.0 * ui[i], lq * rho, lp[1 + i]);
+    atomicAdd(&A.lU[(1 + i) * N + Y], lu * rinv);
+    lrinv = fma(lu, u[1 + i], lrinv);
+  }
+  atomicAdd(&A.lU[4 * N + Y], leint);
+  atomicAdd(&A.lU[0 * N + Y], fma(lq, u2s, lp[0]) - lrinv * rinv * rinv);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double lb = 0.5 * fma(2.0 * halve(lo[d] + hi[d]), lq, lp[5 + d]);
+    atomicAdd(&A.lB[d * N + Y], lb);
+    atomicAdd(&A.lB[d * N + shift(D, Y, d, 1)], lb);
+  }
+}
+
+// adjoint of the first-order (piecewise-constant + LLF) face problem on the d-face between cells
+// Xl and Xr of S^n, with weights lf (flux, face frame), lap (alpha) and lus (u*)
+__device__ __forceinline__ void fo_face_vjp(const AdjDev& A, int d, long long Xl, long long Xr, const double* lf,
+                                            double lap, double lus) {
+  const Dev& D = A.D;
+  const int a = (d + 1) % 3, c = (d + 2) % 3;
+  double wl[8], wr[8];
+  prim_of(D, D.U0, D.B0, Xl, wl);
+  prim_of(D, D.U0, D.B0, Xr, wr);
+  const FaceState sl = {wl[0], wl[1 + d], wl[1 + a], wl[1 + c], wl[4], wl[5 + a], wl[5 + c]};
+  const FaceState sr = {wr[0], wr[1 + d], wr[1 + a], wr[1 + c], wr[4], wr[5 + a], wr[5 + c]};
+  FaceState dl, dr;
+  double dbn;
+  riemann_vjp<RS_LLF>(sl, sr, D.B0[d][Xr], D.gam, D.gm1inv, lf, lap, 0.0, lus, dl, dr, dbn);
+  const FaceState* ds[2] = {&dl, &dr};
+  const long long cells[2] = {Xl, Xr};
+  for (int k = 0; k < 2; ++k) {
+    double lp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    lp[0] = ds[k]->rho;
+    lp[1 + d] = ds[k]->u;
+    lp[1 + a] = ds[k]->v;
+    lp[1 + c] = ds[k]->w;
+    lp[4] = ds[k]->p;
+    lp[5 + a] = ds[k]->by;
+    lp[5 + c] = ds[k]->bz;
+    prim_vjp_atomic(A, cells[k], lp);
+  }
+  atomicAdd(&A.lB[d * D.N + Xr], dbn);
+}
+
+// Adjoint of the first-order fluxes and EMFs of S^n on masked faces and edges: weights
+// M2 gF + M1 kF (faces) and M2 gE + M1 kE (edges), fl1 / fl2 the flags after stage 1 / 2. Adds to
+// lU, lB (of S^n) and lEta. Exits at once when neither stage flagged a cell.
+__global__ void __launch_bounds__(128) k_adj_fo(AdjDev A, const unsigned char* fl1, const unsigned char* fl2,
+                                                const double* gF, const double* gE, const double* kF,
+                                                const double* kE) {
+  const Dev& D = A.D;
+  if (*(volatile const unsigned long long*)(D.counters + 0) == 0 &&
+      *(volatile const unsigned long long*)(D.counters + 1) == 0)
+    return;
+  const long long N = D.N;
+  double etaacc = 0.0;
+  for (long long X0 = (long long)blockIdx.x * blockDim.x; X0 < N; X0 += (long long)gridDim.x * blockDim.x) {
+    const long long X = X0 + threadIdx.x;  // the warp stays together for warp_add below
+    if (X < N) {
+      for (int d = 0; d < 3; ++d) {
+        const bool m1 = face_masked(D, fl1, d, X), m2 = face_masked(D, fl2, d, X);
+        if (!(m1 || m2)) continue;
+        const int a = (d + 1) % 3, c = (d + 2) % 3;
+        double w[5];
+        for (int v = 0; v < 5; ++v) {
+          const long long I = (5LL * d + v) * N + X;
+          w[v] = (m2 ? gF[I] : 0.0) + (m1 ? kF[I] : 0.0);
+        }
+        const double lf[5] = {w[0], w[1 + d], w[1 + a], w[1 + c], w[4]};
+        fo_face_vjp(A, d, shift(D, X, d, -1), X, lf, 0.0, 0.0);
+        if (D.resistive && w[4] != 0.0) etaacc += joule_adj(A, d, X, w[4]);  // the Joule flux from S^n
+      }
+      for (int e = 0; e < 3; ++e) {
+        const bool m1 = edge_masked(D, fl1, e, X), m2 = edge_masked(D, fl2, e, X);
+        if (!(m1 || m2)) continue;
+        const double lam = (m2 ? gE[e * N + X] : 0.0) + (m1 ? kE[e * N + X] : 0.0);
+        if (lam == 0.0) continue;
+        const int a = (e + 1) % 3, c = (e + 2) % 3;
+        const long long Xa = shift(D, X, a, -1), Xc = shift(D, X, c, -1), Xac = shift(D, Xa, c, -1);
+        // the first-order edge EMF (Q26 corners of piecewise-constant values, LD04 with the LLF
+        // speeds) as fo_edges_cell forms it: the four faces' alpha and u*, recomputed
+        double f[5], apaB, apaT, apcL, apcR, uaB, uaT, ucL, ucR;
+        fo_face(D, a, Xac, Xc, Xc, f, apaB, uaB);
+        fo_face(D, a, Xa, X, X, f, apaT, uaT);
+        fo_face(D, c, Xac, Xa, Xa, f, apcL, ucL);
+        fo_face(D, c, Xc, X, X, f, apcR, ucR);
+        const bool pickB = dbits(apaB) >= dbits(apaT), pickL = dbits(apcL) >= dbits(apcR);  // pmax
+        const double apa = pickB ? apaB : apaT, apc = pickL ? apcL : apcR;
+        const double in[12] = {D.B0[a][Xc], D.B0[a][X], uaB, uaT, D.B0[c][Xa], D.B0[c][X], ucL, ucR,
+                               apa, apa, apc, apc};
+        double g[12];
+        q26_edge_vjp(in, lam, g);
+        const double dapa = g[8] + g[9], dapc = g[10] + g[11];
+        const double z[5] = {0, 0, 0, 0, 0};
+        fo_face_vjp(A, a, Xac, Xc, z, pickB ? dapa : 0.0, g[2]);
+        fo_face_vjp(A, a, Xa, X, z, pickB ? 0.0 : dapa, g[3]);
+        fo_face_vjp(A, c, Xac, Xa, z, pickL ? dapc : 0.0, g[6]);
+        fo_face_vjp(A, c, Xc, X, z, pickL ? 0.0 : dapc, g[7]);
+        atomicAdd(&A.lB[a * N + Xc], g[0]);
+        atomicAdd(&A.lB[a * N + X], g[1]);
+        atomicAdd(&A.lB[c * N + Xa], g[4]);
+        atomicAdd(&A.lB[c * N + X], g[5]);
+        if (D.resistive) {  // + eta j from S^n
+          const double j = (D.B0[c][X] - D.B0[c][Xa]) * D.hinv[a] - (D.B0[a][X] - D.B0[a][Xc]) * D.hinv[c];
+          etaacc += lam * j;
+          const double la = D.eta * lam * D.hinv[a], lc = D.eta * lam * D.hinv[c];
+          atomicAdd(&A.lB[c * N + X], la);
+          atomicAdd(&A.lB[c * N + Xa], -la);
+          atomicAdd(&A.lB[a * N + X], -lc);
+          atomicAdd(&A.lB[a * N + Xc], lc);
+        }
+      }
+    }
+    warp_add(etaacc, A.lEta);
+    etaacc = 0.0;
+  }
+}
+
+void launch_adj_mask(const Dev& D, const unsigned char* fl, const double* gF, const double* gE, double* lF,
+                     double* lE, double scale, cudaStream_t st) {
+  k_adj_mask<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(D, fl, gF, gE, lF, lE, scale);
+}
+void launch_adj_fo(const AdjDev& A, const unsigned char* fl1, const unsigned char* fl2, const double* gF,
+                   const double* gE, const double* kF, const double* kE, cudaStream_t st) {
+  const long long nb = (A.D.N + 127) / 128;
+  k_adj_fo<<<(unsigned)(nb < 1184 ? nb : 1184), 128, 0, st>>>(A, fl1, fl2, gF, gE, kF, kE);
+}
+
 // reverse sweeps of the PPM reconstructions along each direction (one launch per direction, so
 // that every output element has one writer per launch); kind FACE or edge values
 template <bool FACE>

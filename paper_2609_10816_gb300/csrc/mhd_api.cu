@@ -455,10 +455,13 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   cudaStream_t st = ctx->stream;
   // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
   // lB0 3, lam2 8, the stage-1 input's P 8 and alpha+- / u* 9, the forward face states of both
-  // stage inputs 2 x 42, and their reconstructed edge values 12 + 2 x 12 (doubles per cell) + eta
-  const size_t nd = 262;
+  // stage inputs 2 x 42, and their reconstructed edge values 12 + 2 x 12; for flux correction
+  // D^T lam and the stage-1 flux adjoint 2 x 18, the stage-2 proposal 8 and the stage-1 flags
+  // (doubles per cell) + eta
+  const size_t nd = 306;
   if (!ctx->adj) {
-    s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + 8) * sizeof(double)), "cudaMalloc of adjoint scratch");
+    s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + (N + 7) / 8 + 8) * sizeof(double)),
+                   "cudaMalloc of adjoint scratch");
     if (s != MHD_OK) { ctx->adj = nullptr; return s; }
   }
   double* q = ctx->adj;
@@ -484,7 +487,13 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* Epart0 = take(12);
   double* EdgeC0 = take(12);
   double* EdgeC1 = take(12);
+  double* gF = take(15);  // g = D^T lam
+  double* gE = take(3);
+  double* kF = take(15);  // k: the adjoint of the stage-1 fluxes and EMFs
+  double* kE = take(3);
+  double* U2 = take(8);   // the stage-2 proposal S^n + D((F1 + HO(S^{n+1/2})) / 2), for its flags
   double* lEta = q;
+  unsigned char* flag1 = (unsigned char*)(q + 8);  // the flags after stage 1
 
   mhd::Dev D = ctx->base;
   D.dt = dt;
@@ -522,6 +531,11 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   D0.Epart = Epart0;
   D0.EdgeC = EdgeC0;
   run_stage(ctx, D0, sc);
+  // the stage-1 flags (none without flux correction: the flag pass then marks only cells that are
+  // not finite, and the forward step corrects nothing)
+  e = sc.fofc ? cudaMemcpyAsync(flag1, D.flag, N, cudaMemcpyDeviceToDevice, st) : cudaMemsetAsync(flag1, 0, N, st);
+  if ((s = cuda_check(ctx, e, "flags")) != MHD_OK) return s;
+  const unsigned char* flag2 = sc.fofc ? D.flag : flag1;
 
   auto adj_dev = [&](const mhd::Dev& Ds, double* lU, double* lB) {
     mhd::AdjDev A;
@@ -538,14 +552,29 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   };
   auto zero = [&](double* p, long long k) { return cudaMemsetAsync(p, 0, k * N * sizeof(double), st); };
 
-  // stage 2 flux function at S^{n+1/2}: adjoint inputs (D^T lam) / 2
+  // forward stage 2 again, up to its flags: P, alpha+-, u*, face and edge values of S^{n+1/2},
+  // the fluxes (F1 + HO(S^{n+1/2})) / 2 and the proposal they give, whose invalid cells are the
+  // stage-2 flags (the stage-1 fluxes F1 are still in the flux and EMF arrays)
   mhd::Dev D1 = D;
   D1.Uin = ctx->U1;
   for (int d = 0; d < 3; ++d) D1.Bin[d] = ctx->B1[d];
   D1.LR = LR1;
   D1.EdgeC = EdgeC1;
-  recompute(D1);
-  mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
+  {
+    mhd::Dev D2 = D1;
+    D2.combine = 1;
+    D2.stage = 1;
+    D2.Pnext = nullptr;
+    D2.Uout = U2;
+    for (int d = 0; d < 3; ++d) D2.Bout[d] = U2 + (5 + d) * N;
+    recompute(D2);
+    mhd::launch_update(D2, st);
+    mhd::launch_flag(D2, st);
+  }
+
+  // stage 2 flux function at S^{n+1/2}: adjoint inputs (1 - M2) (D^T lam) / 2
+  mhd::launch_adj_update(D, lamU, lamB, gF, gE, 1.0, 0.0, st);
+  mhd::launch_adj_mask(D, flag2, gF, gE, lF, lE, 0.5, st);
   e = zero(lU1, 5);
   if (e == cudaSuccess) e = zero(lB1, 3);
   if (e == cudaSuccess) e = zero(lAp, 9);  // alpha+-, u* (accumulated)
@@ -553,15 +582,20 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   if ((s = cuda_check(ctx, e, "cudaMemsetAsync")) != MHD_OK) return s;
   mhd::launch_adj_flux(adj_dev(D1, lU1, lB1), sc.recon, sc.rs, st);
 
-  // stage 1 flux function at S^n: (D^T lam) / 2 + D^T lam_{n+1/2}
-  mhd::launch_adj_update(D, lamU, lamB, lF, lE, 0.5, 0.0, st);
-  mhd::launch_adj_update(D, lU1, lB1, lF, lE, 1.0, 1.0, st);
+  // the stage-1 fluxes F1: k = (1 - M2) (D^T lam) / 2 + D^T lam_{n+1/2}; the high-order flux
+  // function at S^n gets (1 - M1) k
+  mhd::launch_adj_mask(D, flag2, gF, gE, kF, kE, 0.5, st);
+  mhd::launch_adj_update(D, lU1, lB1, kF, kE, 1.0, 1.0, st);
+  mhd::launch_adj_mask(D, flag1, kF, kE, lF, lE, 1.0, st);
   e = zero(lU0, 5);
   if (e == cudaSuccess) e = zero(lB0, 3);
   if (e == cudaSuccess) e = zero(lAp, 9);  // alpha+-, u* (accumulated)
   if (e == cudaSuccess) e = zero(lP, 8);   // primitives (accumulated)
   if ((s = cuda_check(ctx, e, "cudaMemsetAsync")) != MHD_OK) return s;
   mhd::launch_adj_flux(adj_dev(D0, lU0, lB0), sc.recon, sc.rs, st);
+  // the first-order fluxes and EMFs of S^n on masked faces and edges get M2 (D^T lam) + M1 k
+  // (the kernel returns at once when neither stage flagged a cell)
+  if (sc.fofc) mhd::launch_adj_fo(adj_dev(D0, lU0, lB0), flag1, flag2, gF, gE, kF, kE, st);
 
   // lam_n = lam_{n+1} + lam_{n+1/2} + (stage-1 part), back into the caller's arrays
   mhd::launch_axpy3(5 * N, lamU, lU1, lU0, st);

@@ -88,6 +88,10 @@ void launch_adj_flux(const AdjDev& A, int recon, int rs, cudaStream_t st);
 void launch_adj_update(const Dev& D, const double* lU, const double* lB, double* lF, double* lE, double scale,
                        double s_old, cudaStream_t st);
 void launch_axpy3(long long n, double* y, const double* a, const double* b, cudaStream_t st);
+void launch_adj_mask(const Dev& D, const unsigned char* fl, const double* gF, const double* gE, double* lF,
+                     double* lE, double scale, cudaStream_t st);
+void launch_adj_fo(const AdjDev& A, const unsigned char* fl1, const unsigned char* fl2, const double* gF,
+                   const double* gE, const double* kF, const double* kE, cudaStream_t st);
 void launch_vjp_check(long long n, unsigned long long seed, double gam, int rs, unsigned long long* out,
                       cudaStream_t st);
 

@@ -41,6 +41,95 @@ def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta, shape):
     assert np.array_equal(st.cons.cpu().numpy(), cons) and np.array_equal(st.b.cpu().numpy(), b)
 
 
+def _shock_state(shape, seed, amp, p0):
+    """A near-vacuum state under a strong expansion: the high-order step leaves cells invalid. The
+    pressure varies smoothly: on a uniform pressure its recomputed cell values differ only by
+    rounding, where the limiters' branches (and so their derivatives) follow rounding noise that
+    two correct implementations need not share."""
+    cons, b, info = inputs.random_smooth(shape, seed=seed, rough=0.0)
+    rng = np.random.default_rng(seed)
+    rho = cons[0]
+    u = [cons[1 + d] / rho for d in range(3)]
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                          indexing="ij")
+    u[0] = u[0] + amp * np.sin(2 * np.pi * x) + 0.1 * amp * rng.uniform(-1, 1, rho.shape)
+    p = p0 * (1.0 + 0.3 * np.sin(2 * np.pi * x + 1.3) * np.cos(2 * np.pi * y - 0.4) + 0.2 * np.sin(2 * np.pi * z + 0.7))
+    return inputs.assemble(rho, u, p, b), b, info
+
+
+# (shape, seed, velocity amplitude, pressure, CFL, reconstruction): a few cells flagged after
+# stage 1; half the box flagged after stage 1 and a few cells after stage 2; a few cells after
+# each stage with PLM
+FOFC_CASES = [((10, 8, 6), 1, 0.3, 1e-2, 0.4, "ppm"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm"),
+              ((10, 8, 6), 4, 0.6, 1e-2, 0.6, "plm_mc")]
+
+
+@pytest.mark.parametrize("case", range(len(FOFC_CASES)))
+@pytest.mark.parametrize("eta", [0.0, 3e-3])
+def test_flux_corrected_step_adjoint_identity(gpu_lib, case, eta):
+    """Steps in which flux correction (Sec. 2.5) replaces fluxes with first-order ones, in stage 1
+    and in stage 2: <lam, J v> from the oracle's dual numbers (the same flagged cells, taken from
+    the values) equals <J^T lam, v> from the adjoint, to ~1e-10 relative."""
+    shape, seed, amp, p0, cfl, recon = FOFC_CASES[case]
+    cons, b, info = _shock_state(shape, seed, amp, p0)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann="hlld", emf="q26", eta=eta)
+    dt = oracle.max_dt(cfg, cons, b, cfl)
+    _, _, cnt = oracle.step(cfg, cons, b, dt)
+    assert cnt[0] > 0 and (case == 0 or cnt[1] > 0), cnt
+    sch = mhd.scheme(recon, "hlld", "q26")
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    ctx.step(mhd.to_device(cons, b), dt, sch, eta)
+    assert ctx.stats() == cnt  # the GPU step flags the same cells' count
+    rng = np.random.default_rng(2 + case)
+    lc, lb = rng.normal(size=cons.shape), rng.normal(size=b.shape)
+    vc, vb, veta = rng.normal(size=cons.shape) * 1e-3, rng.normal(size=b.shape) * 1e-4, 0.7
+    _, _, tc, tb = oracle.steps_jvp(cfg, cons, b, vc, vb, veta, [dt])
+    lhs = (lc * tc).sum() + (lb * tb).sum()
+    lam = mhd.to_device(lc, lb)
+    deta = ctx.step_adjoint(st, lam, dt, sch, eta)
+    torch.cuda.synchronize()
+    rc, rb = lam.cons.cpu().numpy(), lam.b.cpu().numpy()
+    rhs = (rc * vc).sum() + (rb * vb).sum() + deta * veta
+    scale = abs(lhs) + abs((rc * vc).sum()) + abs((rb * vb).sum()) + abs(deta * veta)
+    print(f"ADJ-FOFC {case} eta={eta} flags={cnt}: lhs {lhs:.15e} rhs {rhs:.15e} rel {abs(lhs - rhs) / scale:.2e}")
+    assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs)
+    assert np.array_equal(st.cons.cpu().numpy(), cons) and np.array_equal(st.b.cpu().numpy(), b)
+
+
+def test_multistep_gradient_through_flux_correction(gpu_lib):
+    """Three steps of a state that flux correction acts on, through MHDEvolve (checkpoints every 2):
+    the torch gradient of the final sum of b^2 in the initial state and eta against the oracle's
+    exact directional derivative."""
+    shape = (10, 8, 6)
+    cons, b, info = _shock_state(shape, 1, 0.3, 1e-2)
+    eta0 = 2e-3
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    cfg = oracle.Config(shape=shape, h=info["h"], recon="ppm", riemann="hlld", eta=eta0)
+    dts, c, bb, flagged = [], cons, b, 0
+    for _ in range(3):
+        dts.append(oracle.max_dt(cfg, c, bb, 0.4))
+        c, bb, cnt = oracle.step(cfg, c, bb, dts[-1])
+        flagged += cnt[0] + cnt[1]
+    assert flagged > 0
+    dev = "cuda"
+    c0 = torch.tensor(cons, device=dev, requires_grad=True)
+    b0 = torch.tensor(b, device=dev, requires_grad=True)
+    eta = torch.tensor(eta0, dtype=torch.float64, requires_grad=True)
+    ctx = mhd.Context(shape, info["h"])
+    cf, bf = adjoint.evolve(c0, b0, eta, ctx, dts, sch, every=2)
+    (bf * bf).sum().backward()
+    gc, gb, ge = c0.grad.cpu().numpy(), b0.grad.cpu().numpy(), float(eta.grad)
+    rng = np.random.default_rng(9)
+    for _ in range(2):
+        vc, vb, veta = rng.normal(size=cons.shape) * 1e-3, rng.normal(size=b.shape) * 1e-4, rng.normal()
+        _, bfin, _, tbf = oracle.steps_jvp(cfg, cons, b, vc, vb, veta, dts)
+        exact = 2.0 * (bfin * tbf).sum()
+        got = (gc * vc).sum() + (gb * vb).sum() + ge * veta
+        assert abs(got - exact) <= 1e-9 * (abs(exact) + abs((gc * vc).sum()) + abs((gb * vb).sum())), (got, exact)
+
+
 def _initial(shape, u, rho, p, b):
     """Conserved state from an initial velocity (torch, differentiable), density, pressure, field."""
     bc = 0.5 * (b + torch.stack([torch.roll(b[d], -1, dims=2 - d) for d in range(3)]))

@@ -746,6 +746,24 @@ def test_fofc_without_flags_is_plain_rk2():
 # ---------------------------------------------------------------------------------------
 # Time step (Sec. 2.4) and the dual-number derivative
 # ---------------------------------------------------------------------------------------
+def test_flux_jvp_matches_fluxes_and_central_difference():
+    """The dual-number directional derivative of the fluxes and EMFs returns the fluxes themselves
+    and agrees with a central difference on a smooth state."""
+    shape = (6, 5, 4)
+    cons, b, info = inputs.random_smooth(shape, seed=12, rough=0.0)
+    cfg = cfg_for(shape, info, recon="ppm", riemann="hlld", eta=2e-3)
+    rng = np.random.default_rng(3)
+    dc, db = rng.normal(size=cons.shape) * 1e-2, rng.normal(size=b.shape) * 1e-2
+    F, E, dF, dE = oracle.fluxes_jvp(cfg, cons, b, dc, db)
+    F0, E0 = oracle.fluxes(cfg, cons, b)
+    assert np.array_equal(F, F0) and np.array_equal(E, E0)
+    h = 1e-6
+    Fp, Ep = oracle.fluxes(cfg, cons + h * dc, b + h * db)
+    Fm, Em = oracle.fluxes(cfg, cons - h * dc, b - h * db)
+    assert np.abs((Fp - Fm) / (2 * h) - dF).max() <= 1e-6 * np.abs(dF).max()
+    assert np.abs((Ep - Em) / (2 * h) - dE).max() <= 1e-6 * np.abs(dE).max()
+
+
 def test_max_dt_closed_form():
     shape = (4, 4, 4)
     box = inputs.Box(shape)
