@@ -27,14 +27,19 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per GB300 (FP64, plain vs batched vs fwd+adjoint), % HBM roofline"
 UNIT = "cell-updates/s"
 
-# Roofline constants: GB300 FP64 = 152 SMs x 2 DFMA/clk x 2 flops at 2070 MHz
-# (the recipe's unit counts and maximum clock; a DFMA microbenchmark measured 1.19 TFLOP/s at
-# ~1990 MHz). Algorithmic FP64 flops per face of the face sweep (reconstruction of 7 primitives
-# along the sweep + Riemann solve + Joule flux), counted by the oracle's op-counting scalar on a
-# 32^3 sample of the same workload (oracle/count_flops.py): PPM + HLLD + Q26, turbulence Mach 5.
+# Roofline constants: GB300 FP64 = 152 SMs x 2 DFMA/clk x 2 flops at 2070 MHz (the recipe's SM
+# count and maximum clock; the DFMA rate per SM per clock is measured by mhd_fp64_rate, which the
+# bench runs and reports). Algorithmic FP64 flops (one per +, -, *, /, sqrt) counted by the
+# oracle's op-counting scalar (python -m oracle.count_flops): per face of the face sweep
+# (reconstruction of 7 primitives + Riemann solve + Joule flux) and per cell-update of the whole
+# step, HLLD counted one-sided (the states of the fan region the face lies in; the full count, with
+# both sides' star states formed everywhere, is beside it). Turbulence: four 48^3 cuts of the timed
+# 256^3 state; the others on 32^3 (fast wave, Alfven wave) and 64 x 64 x 4 (Harris sheet) samples.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FLOPS_PER_FACE = {"ppm/hlld": 316.4, "plm_mc/hll": 249.0, "plm_mc/hlld": 430.9}
-FLOPS_PER_CELL_UPDATE = {"ppm/hlld": 2916.2, "plm_mc/hll": 2325.3, "plm_mc/hlld": 3385.3}
+FLOPS_PER_FACE = {"turbulence": 286.0, "turbulence_full_hlld": 303.7, "alfven_ppm_ep": 455.2,
+                  "fast_wave": 249.0, "harris": 361.3}
+FLOPS_PER_CELL_UPDATE = {"turbulence": 2746.0, "turbulence_full_hlld": 2852.6, "alfven_ppm_ep": 3628.6,
+                         "fast_wave": 2325.3, "harris": 2968.1}
 HBM_PEAK_GBS = 6759.6  # measured copy bandwidth of this GPU model (STREAM-style copy)
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
@@ -142,51 +147,84 @@ WORKLOAD_NAME = ("{n}^3 periodic FP64 ideal decaying MHD turbulence: rho=1, B0=(
                  "compute + LD04 averaging, RK2-SSP with first-order flux correction, CFL 0.3")
 
 
-def cpu_baseline(budget_s=12.0, n=48):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+def _oracle_worker_init(n):
+    """Spawned process: the oracle and one box of the timed workload's recipe."""
+    global _W
     import oracle
 
     cons, b, info = workload(n)
-    cfg = oracle.Config(shape=(n, n, n), h=info["h"], recon="ppm", riemann="hlld", emf="q26")
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        dt = oracle.max_dt(cfg, cons, b, 0.3)
-        cons, b, _ = oracle.step(cfg, cons, b, dt)
-        steps += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    return {"value": n**3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps (CFL dt + RK2/FOFC step) of a {n}^3 box of the same recipe, "
-                      f"PPM+HLLD+Q26+LD04, single thread, {el:.1f} s"}
+    _W = {"cfg": oracle.Config(shape=(n, n, n), h=info["h"], recon="ppm", riemann="hlld", emf="q26"),
+          "cons": cons, "b": b}
+
+
+def _oracle_worker_steps(arg):
+    """Advance this process's box by CFL steps for budget_s seconds (or `steps` steps): (steps, s)."""
+    import oracle
+
+    budget_s, steps = arg
+    w = _W
+    k, t0 = 0, time.perf_counter()
+    while (steps is None and time.perf_counter() - t0 < budget_s) or (steps is not None and k < steps):
+        dt = oracle.max_dt(w["cfg"], w["cons"], w["b"], 0.3)
+        w["cons"], w["b"], _ = oracle.step(w["cfg"], w["cons"], w["b"], dt)
+        k += 1
+    return k, time.perf_counter() - t0
+
+
+def _oracle_pool(n, procs):
+    import multiprocessing as mp
+
+    return mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(n,))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(budget_s=12.0, n=48):
+    """The oracle as it stands, single-threaded per process, on every host core at once: one
+    spawned process per core advances its own box of the workload's recipe for budget_s seconds;
+    the rate is the sum over processes."""
+    procs = host_cores()
+    with _oracle_pool(n, procs) as pool:
+        pool.map(_oracle_worker_steps, [(0.0, 1)] * procs)  # warm-up: one step each
+        res = pool.map(_oracle_worker_steps, [(budget_s, None)] * procs)
+    rate = sum(n**3 * k / el for k, el in res)
+    steps = sum(k for k, _ in res)
+    return {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes (one per host core), each advancing its own {n}^3 box of the same recipe "
+                      f"(PPM+HLLD+Q26+LD04, CFL dt + RK2/FOFC step) for {budget_s:.0f} s: {steps} steps in all"}
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle timed on the host, on bounded samples of the workload."""
+    """--impl reference: the CPU oracle timed on every host core (one process per core, each
+    advancing its own 32^3 box of the workload's recipe), one step per process per timed step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     n = 32
-    cons, b, info = workload(n)
-    import oracle
-
-    cfg = oracle.Config(shape=(n, n, n), h=info["h"], recon="ppm", riemann="hlld", emf="q26")
-    for _ in range(args.warmup):
-        cons, b, _ = oracle.step(cfg, cons, b, oracle.max_dt(cfg, cons, b, 0.3))
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        cons, b, _ = oracle.step(cfg, cons, b, oracle.max_dt(cfg, cons, b, 0.3))
-    el = time.perf_counter() - t0
-    v = n**3 * args.steps / el
+    procs = host_cores()
+    with _oracle_pool(n, procs) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker_steps, [(0.0, 1)] * procs)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_worker_steps, [(0.0, 1)] * procs)
+        el = time.perf_counter() - t0
+    v = procs * n**3 * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME.format(n=256), "sample": f"{n}^3 box per step"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} timed oracle steps of a {n}^3 box of the same recipe"},
+        "config": {"workload": WORKLOAD_NAME.format(n=256),
+                   "sample": f"{procs} boxes of {n}^3 per step, one per host core"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"{args.steps} timed steps; each advances {procs} independent {n}^3 boxes of "
+                                   f"the same recipe, one oracle process per host core"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -289,9 +327,87 @@ def run_alfven(args, dev, stream, barrier, dist, world):
     ctx.close()
     out[f"alfven{n}_config"] = {"cells": n**3, "steps": steps,
                                 "scheme": "PPM-EP + HLLD + {Q26, FS18, B25a} + LD04 (and Q26 with PPM)",
+                                "q26_fp64_frac_of_peak": out[f"alfven{n}_q26"] / world * FLOPS_PER_CELL_UPDATE[
+                                    "alfven_ppm_ep"] / 1e12 / FP64_PEAK_TFLOPS,
                                 "q26_speedup_vs_fs18": out[f"alfven{n}_q26"] / out[f"alfven{n}_fs18"] - 1,
                                 "q26_speedup_vs_b25a": out[f"alfven{n}_q26"] / out[f"alfven{n}_b25a"] - 1}
     return out
+
+
+def _timed_steps(ctx, st, sch, eta, steps, stream, barrier, dist, dev, graph=False):
+    """ms of `steps` mhd_step_cfl calls (CFL 0.3) after three warm-up steps; with graph, the steps
+    are recorded once as a CUDA graph and the graph is replayed."""
+    import torch
+
+    for _ in range(3):
+        ctx.step_cfl(st, 0.3, sch, eta)
+    g = None
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(steps):
+                ctx.step_cfl(st, 0.3, sch, eta)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if graph:
+        g.replay()
+    else:
+        for _ in range(steps):
+            ctx.step_cfl(st, 0.3, sch, eta)
+    e1.record(stream)
+    barrier()
+    ctx.last_dt()  # raises on a non-finite signal speed
+    return max_over_ranks(e0.elapsed_time(e1), dist, dev)
+
+
+def run_c1(args, dev, stream, barrier, dist, world):
+    """The 32^3 fast eigenmode along the box diagonal (rho0 = 1, p0 = 1/gamma, b0 oblique, amplitude
+    1e-6), PLM-MC + HLL + Q26 + LD04, CFL 0.3, 100 steps: launch-bound at this size, so it is timed
+    both as eager calls and as one CUDA-graph replay of the 100 steps."""
+    from paper_2609_10816_gb300 import inputs, mhd
+
+    shape, steps = (32, 32, 32), 100
+    cons, b, info = inputs.fast_wave(shape)
+    ctx = mhd.Context(shape, info["h"], stream=stream)
+    sch = mhd.scheme("plm_mc", "hll", "q26")
+    out = {}
+    for graph in (False, True):
+        st = mhd.to_device(cons, b, dev)
+        ms = _timed_steps(ctx, st, sch, 0.0, steps, stream, barrier, dist, dev, graph=graph)
+        out["c1_fast_wave_32cubed" + ("_graph" if graph else "")] = whole_job_rate(32**3 * steps, world, ms)
+    md, mb = ctx.divb(st)
+    ctx.close()
+    r = out["c1_fast_wave_32cubed_graph"] / world
+    out["c1_config"] = {"cells": 32**3, "steps": steps, "scheme": "PLM-MC + HLL + Q26 + LD04",
+                        "fp64_frac_of_peak": r * FLOPS_PER_CELL_UPDATE["fast_wave"] / 1e12 / FP64_PEAK_TFLOPS,
+                        "hbm_frac": r * ALG_BYTES_PER_CELL_UPDATE / 1e9 / HBM_PEAK_GBS,
+                        "max_divb_dx_over_b": md * info["h"][0] / mb}
+    return out
+
+
+def run_c3(args, dev, stream, barrier, dist, world):
+    """512 x 512 x 4 resistive reconnection (periodic double Harris sheet, beta 0.2, seeded 1e-3
+    velocity noise), eta = 1e-4, PLM-MC + HLLD + Q26 + LD04, CFL 0.3, 200 steps."""
+    from paper_2609_10816_gb300 import inputs, mhd
+
+    shape, steps, eta = (512, 512, 4), 200, 1e-4
+    cons, b, info = inputs.harris_sheet(shape)
+    ctx = mhd.Context(shape, info["h"], stream=stream)
+    sch = mhd.scheme("plm_mc", "hlld", "q26")
+    st = mhd.to_device(cons, b, dev)
+    ms = _timed_steps(ctx, st, sch, eta, steps, stream, barrier, dist, dev)
+    N = 512 * 512 * 4
+    md, mb = ctx.divb(st)
+    s1, s2 = ctx.stats()
+    ctx.close()
+    r = N * steps / (ms / 1e3)
+    return {"c3_reconnection_512x512x4": whole_job_rate(N * steps, world, ms),
+            "c3_config": {"cells": N, "steps": steps, "eta": eta, "scheme": "PLM-MC + HLLD + Q26 + LD04",
+                          "ms_per_step": ms / steps,
+                          "fp64_frac_of_peak": r * FLOPS_PER_CELL_UPDATE["harris"] / 1e12 / FP64_PEAK_TFLOPS,
+                          "hbm_frac": r * ALG_BYTES_PER_CELL_UPDATE / 1e9 / HBM_PEAK_GBS,
+                          "max_divb_dx_over_b": md * info["h"][0] / mb, "fofc_flagged_last_step": [s1, s2]}}
 
 
 def run_fwd_adjoint(args, dev, stream, barrier, dist, world):
@@ -380,7 +496,23 @@ def main():
     ap.add_argument("--no-alfven", action="store_true", help="skip the oblique Alfven-wave throughput runs")
     ap.add_argument("--alfven-n", type=int, default=128)
     ap.add_argument("--alfven-steps", type=int, default=100)
+    ap.add_argument("--no-c1", action="store_true", help="skip the 32^3 fast-eigenmode form")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 512x512x4 reconnection form")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated forms to run besides the headline step (emf, batch, alfven, adjoint, c1, c3, "
+                         "e2e, cpu); the rest are skipped")
     args = ap.parse_args()
+    if args.only is not None:
+        keep = set(x.strip() for x in args.only.split(",") if x.strip())
+        args.q26_only = "emf" not in keep
+        args.no_batch = "batch" not in keep
+        args.no_alfven = "alfven" not in keep
+        args.no_adjoint = "adjoint" not in keep
+        args.no_c1 = "c1" not in keep
+        args.no_c3 = "c3" not in keep
+        args.no_cpu_baseline = "cpu" not in keep
+        if "e2e" not in keep:
+            args.e2e_steps = 0
     if args.impl == "reference":
         return run_reference(args)
 
@@ -447,11 +579,12 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     per_launch_s = dom_ms / 1e3 / dom_launches if dom_launches else float("nan")
-    key = "ppm/hlld"
+    key = "turbulence"
     if dom == "face":
         flops_per_launch = FLOPS_PER_FACE[key] * N
     else:
         flops_per_launch = float("nan")
+    fp64_probe = {k: mhd.fp64_rate(k, 1 << 13, stream) for k in ("dfma", "dadd", "dmul")}
     achieved = flops_per_launch / per_launch_s / 1e12
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] * (N / tr["cells"]) if tr and tr.get("src") == kernel_src_hash() else None
@@ -485,6 +618,12 @@ def main():
 
     if not args.no_adjoint:
         forms.update(run_fwd_adjoint(args, dev, stream, barrier, dist, world))
+
+    if not args.no_c1:
+        forms.update(run_c1(args, dev, stream, barrier, dist, world))
+
+    if not args.no_c3:
+        forms.update(run_c3(args, dev, stream, barrier, dist, world))
 
     # ---- end to end through the C ABI with host buffers --------------------------------------
     # Every step copies its input state from pinned host memory and its result back. Two device
@@ -524,7 +663,7 @@ def main():
     f1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
-    e2e_value = whole_job_rate(N * args.e2e_steps, world, e2e_ms)
+    e2e_value = whole_job_rate(N * args.e2e_steps, world, e2e_ms) if args.e2e_steps > 0 else None
     del sts[1]
 
     if rank != 0:
@@ -533,6 +672,7 @@ def main():
         return 0
 
     clocks = clk.summary()
+    clk_mhz = clocks.get("sm_mhz")
     line = {
         "metric": METRIC,
         "value": value,
@@ -562,7 +702,16 @@ def main():
             "traffic": traffic,
             "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (recipe unit counts and max clock)",
             "algorithmic_flops_per_launch": flops_per_launch,
+            "flops_per_unit": f"{FLOPS_PER_FACE[key]} per face (HLLD one-sided; {FLOPS_PER_FACE['turbulence_full_hlld']} "
+                              f"with both sides' star states), x {N} faces per launch",
+            "frac_full_hlld_count": (FLOPS_PER_FACE["turbulence_full_hlld"] * N / per_launch_s / 1e12
+                                     / FP64_PEAK_TFLOPS) if dom == "face" else None,
             "avg_launch_ms": per_launch_s * 1e3,
+        },
+        "fp64_probe": {
+            "ops_per_s": fp64_probe,
+            "per_sm_per_clock": {k: v / 152 / ((clk_mhz or 2070.0) * 1e6) for k, v in fp64_probe.items()},
+            "how": "mhd_fp64_rate: 8 independent chains per thread, 8 x 256 threads per SM, CUDA events",
         },
         "hbm_roofline": {
             "algorithmic_bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE,

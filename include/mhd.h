@@ -171,6 +171,15 @@ mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_stat
  * check allows). max_rel_err holds 6 doubles. Synchronous. The paper has no counterpart. */
 mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
 
+/* Measured rate of one FP64 instruction kind on the current GPU (the pipe that bounds every
+ * kernel of the step, hence the denominator of its roofline; the paper has no counterpart):
+ * kind 0 DFMA, 1 DADD, 2 DMUL, 3 FP32 FFMA for comparison. Independent chains (eight per
+ * thread, 8 blocks of 256 threads per SM) run `iters` steps each, timed with CUDA events on
+ * `cuda_stream` after a shorter warm-up; *ops_per_s receives instructions per second (per
+ * thread-lane). Synchronous; allocates 8 bytes of device memory for the duration of the call.
+ * MHD_ERR_ARG for a kind outside 0-3 or iters outside [1, 2^30]. */
+mhd_status mhd_fp64_rate(int kind, long long iters, void *cuda_stream, double *ops_per_s);
+
 /* Self-check of the adjoint's reverse sweep through the face solve (the Riemann solver of
  * `scheme`'s bits 4-7; mhd_step_adjoint uses it): on n hashed face problems (seed), from equal
  * states to extreme ones, with zero normal field and field along the normal among them, and

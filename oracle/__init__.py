@@ -74,7 +74,8 @@ def _L():
         _lib.oracle_max_dt.restype = d
         _lib.oracle_divb.argtypes = [P(_Cfg), P(d), P(d), P(d)]
         _lib.oracle_steps_jvp.argtypes = [P(_Cfg), P(d), P(d), P(d), P(d), d, P(d), ctypes.c_int]
-        _lib.oracle_count_ops.argtypes = [P(_Cfg), P(d), P(d), d, P(ctypes.c_longlong), P(ctypes.c_longlong)]
+        _lib.oracle_count_ops.argtypes = [P(_Cfg), P(d), P(d), d, P(ctypes.c_longlong), P(ctypes.c_longlong),
+                                          P(ctypes.c_longlong)]
     return _lib
 
 
@@ -271,13 +272,16 @@ def run(cfg: Config, cons, b, nsteps: int, cfl: float = 0.3, dt: float | None = 
 PHASES = ["prim", "recon", "riemann", "edge", "joule", "update", "flag", "fo"]
 
 
-def count_ops(cfg: Config, cons, b, dt: float):
-    """FP64 operations (+, -, *, /, sqrt) of one step of the oracle, by phase."""
+def count_ops(cfg: Config, cons, b, dt: float, with_unused: bool = False):
+    """FP64 operations (+, -, *, /, sqrt) of one step of the oracle, by phase; with_unused also
+    returns the Riemann-phase operations a one-sided HLLD would not form."""
     _check(cfg, cons, b)
     cons = np.ascontiguousarray(cons, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     ops = (ctypes.c_longlong * 8)()
     counts = (ctypes.c_longlong * 2)()
+    unused = ctypes.c_longlong(0)
     c = cfg.c()
-    _L().oracle_count_ops(ctypes.byref(c), _ptr(cons), _ptr(b), float(dt), ops, counts)
-    return {k: int(ops[i]) for i, k in enumerate(PHASES)}, (int(counts[0]), int(counts[1]))
+    _L().oracle_count_ops(ctypes.byref(c), _ptr(cons), _ptr(b), float(dt), ops, counts, ctypes.byref(unused))
+    res = {k: int(ops[i]) for i, k in enumerate(PHASES)}, (int(counts[0]), int(counts[1]))
+    return res + (int(unused.value),) if with_unused else res

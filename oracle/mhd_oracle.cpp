@@ -88,6 +88,10 @@ inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 enum { PH_PRIM = 0, PH_RECON = 1, PH_RIEMANN = 2, PH_EDGE = 3, PH_JOULE = 4, PH_UPDATE = 5,
        PH_FLAG = 6, PH_FO = 7, NPHASE = 8 };
 long long g_ops[NPHASE];
+// Operations of the HLLD solve that a solver forming only what the face's region of the Riemann
+// fan needs would not form (the other side's star state and the double-star states outside the
+// rotational waves); counted on the side so the roofline can state both figures.
+long long g_hlld_unused = 0;
 int g_phase = 0;
 bool g_fo = false;
 inline void set_phase(int p) { g_phase = g_fo ? PH_FO : p; }
@@ -357,7 +361,9 @@ void hlld(const T* WL, const T* WR, T bn, T SL, T SR, const T* UL, const T* FL,
   const T* Ws[2] = {WL, WR};
   const T* Uo[2] = {UL, UR};
   const T Ss[2] = {SL, SR};
+  long long side_ops[2];  // operations of each side's star state (counting pass only)
   for (int s = 0; s < 2; ++s) {
+    const long long o_side = g_ops[g_phase];
     const T* W = Ws[s];
     const T S = Ss[s];
     const T rho = W[0], u = W[1], v = W[2], w = W[3], by = W[5], bz = W[6];
@@ -381,7 +387,9 @@ void hlld(const T* WL, const T* WR, T bn, T SL, T SR, const T* UL, const T* FL,
     const T es = (su * Uo[s][4] - pt * u + ptS * SM + bn * (vb - vbs)) / ssm;
     rS[s] = rs; vS[s] = vs; wS[s] = ws; byS[s] = bys; bzS[s] = bzs;
     Us[s][0] = rs; Us[s][1] = rs * SM; Us[s][2] = rs * vs; Us[s][3] = rs * ws; Us[s][4] = es;
+    side_ops[s] = g_ops[g_phase] - o_side;
   }
+  const long long o_double = g_ops[g_phase];
   // double-star states, MK05 Eqs. 49-63
   const T sqL = sqrt_(rS[0]), sqR = sqrt_(rS[1]);
   const T SsL = SM - absv(bn) / sqL, SsR = SM + absv(bn) / sqR;
@@ -403,6 +411,11 @@ void hlld(const T* WL, const T* WR, T bn, T SL, T SR, const T* UL, const T* FL,
     Uss[s][3] = rS[s] * wss;
     Uss[s][4] = Us[s][4] + side * sq * (vbs - vbss) * sb;
   }
+  // outside both rotational waves the double-star states are not needed (deciding that takes
+  // S_M^2 rho* against b_n^2: two operations), nor the other side's star state
+  const long long double_ops = g_ops[g_phase] - o_double;
+  if (val(SsL) >= 0.0) g_hlld_unused += side_ops[1] + double_ops - 2;
+  else if (val(SsR) < 0.0) g_hlld_unused += side_ops[0] + double_ops - 2;
   // MK05 Eqs. 64-66 and the fan selection.
   if (val(SsL) >= 0.0) {
     for (int v = 0; v < 5; ++v) F[v] = FL[v] + SL * (Us[0][v] - UL[v]);
@@ -1032,20 +1045,23 @@ int oracle_steps_jvp(const oracle_cfg* c, double* cons, double* b, double* dcons
 }
 
 // FP64 operations (+, -, *, /, sqrt) of one step, by phase: prim, face reconstruction, Riemann
-// solves, edge EMFs, Joule flux, update, flags, first-order correction. Returns the phase count.
+// solves, edge EMFs, Joule flux, update, flags, first-order correction; *hlld_unused (if not NULL)
+// the Riemann-phase operations that a one-sided HLLD would not form. Returns the phase count.
 int oracle_count_ops(const oracle_cfg* c, const double* cons, const double* b, double dt,
-                     long long* ops_by_phase, long long* counts) {
+                     long long* ops_by_phase, long long* counts, long long* hlld_unused) {
   Grid g = make_grid(c->n, c->h, c->gamma);
   const long N = g.N;
   std::vector<Cnt> U(5 * N), B(3 * N);
   for (long i = 0; i < 5 * N; ++i) U[i] = Cnt(cons[i]);
   for (long i = 0; i < 3 * N; ++i) B[i] = Cnt(b[i]);
   for (int p = 0; p < NPHASE; ++p) g_ops[p] = 0;
+  g_hlld_unused = 0;
   g_fo = false;
   const Scheme<Cnt> sc = {c->recon, c->riemann, c->emf, Cnt(c->eta), c->eta != 0.0};
   StepOut so;
   step(g, sc, c->fofc_criteria, U, B, dt, so);
   for (int p = 0; p < NPHASE; ++p) ops_by_phase[p] = g_ops[p];
+  if (hlld_unused) *hlld_unused = g_hlld_unused;
   if (counts) { counts[0] = so.flagged[0]; counts[1] = so.flagged[1]; }
   return NPHASE;
 }

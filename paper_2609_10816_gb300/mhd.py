@@ -89,6 +89,8 @@ def lib():
     L.mhd_step_cfl.restype = ctypes.c_int
     L.mhd_last_dt.argtypes = [vp, P(d)]
     L.mhd_last_dt.restype = ctypes.c_int
+    L.mhd_fp64_rate.argtypes = [ctypes.c_int, ctypes.c_longlong, vp, P(d)]
+    L.mhd_fp64_rate.restype = ctypes.c_int
     L.mhd_math_check.argtypes = [vp, ctypes.c_longlong, P(d)]
     L.mhd_math_check.restype = ctypes.c_int
     L.mhd_adjoint_check.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_ulonglong, P(d)]
@@ -123,6 +125,19 @@ def lib():
     L.mhd_batch_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+FP64_RATE_KINDS = {"dfma": 0, "dadd": 1, "dmul": 2, "ffma": 3}
+
+
+def fp64_rate(kind: str = "dfma", iters: int = 1 << 14, stream: torch.cuda.Stream | None = None) -> float:
+    """mhd_fp64_rate: instructions per second (per lane) of one FP64 (or FP32 FFMA) kind."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double()
+    rc = lib().mhd_fp64_rate(FP64_RATE_KINDS[kind], int(iters), ctypes.c_void_p(s.cuda_stream), ctypes.byref(out))
+    if rc != OK:
+        raise MHDError(rc, "mhd_fp64_rate failed")
+    return out.value
 
 
 def _check_field(t: torch.Tensor, shape, name):

@@ -230,3 +230,25 @@ def test_fast_reciprocal_and_sqrt_against_ieee(gpu_lib):
     assert er <= 4 * 2.0**-53 and es <= 4 * 2.0**-53 and eq <= 4 * 2.0**-53, (er, es, eq)
     assert hbad == 0 and fbad == 0, (hbad, fbad)  # halving / quadrupling bit-exact
     assert pbad == 0, pbad  # sign tests, comparisons, min/max, |x|, sign copy / flip
+
+
+def test_fp64_rate_probe(gpu_lib):
+    """The FP64 rate probe: DFMA, DADD and DMUL each at 1-4 lanes per SM per clock at the GPU's
+    clock (GB300's FP64 units), and the FP32 FMA many times faster."""
+    import subprocess
+
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        mhz = float(subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                                    "-i", "0"], capture_output=True, text=True, timeout=30).stdout.split()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        mhz = 2070.0
+    rates = {k: mhd.fp64_rate(k, 1 << 13) for k in ("dfma", "dadd", "dmul", "ffma")}
+    per_sm_clk = {k: v / nsm / (mhz * 1e6) for k, v in rates.items()}
+    print("FP64 probe", {k: f"{v:.3e}/s ({per_sm_clk[k]:.2f}/SM/clk)" for k, v in rates.items()})
+    for k in ("dfma", "dadd", "dmul"):
+        assert 0.5 <= per_sm_clk[k] <= 4.5, per_sm_clk
+    assert rates["ffma"] > 10 * rates["dfma"]
+    with pytest.raises(mhd.MHDError):
+        mhd.fp64_rate("dfma", 0)
+
