@@ -378,6 +378,25 @@ def run_c1(args, dev, stream, barrier, dist, world):
         out["c1_fast_wave_32cubed" + ("_graph" if graph else "")] = whole_job_rate(32**3 * steps, world, ms)
     md, mb = ctx.divb(st)
     ctx.close()
+    # the same box as a batch of one patch: one persistent launch per stage (graph-replayed)
+    bt = mhd.Batch([shape], info["h"][0], stream=stream)
+    bc, bb = bt.pack([(cons, b)], dev)
+    bt.set_schedule(seg=8, order=0, blocks_per_sm=0, use_graph=True)
+    for _ in range(3):
+        bt.step(bc, bb, 0.3, sch)
+    barrier()
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        bt.step(bc, bb, 0.3, sch)
+    e1.record(stream)
+    barrier()
+    bt.last_dt()
+    out["c1_fast_wave_32cubed_one_patch_batch"] = whole_job_rate(32**3 * steps, world,
+                                                                max_over_ranks(e0.elapsed_time(e1), dist, dev))
+    bt.close()
     r = out["c1_fast_wave_32cubed_graph"] / world
     out["c1_config"] = {"cells": 32**3, "steps": steps, "scheme": "PLM-MC + HLL + Q26 + LD04",
                         "fp64_frac_of_peak": r * FLOPS_PER_CELL_UPDATE["fast_wave"] / 1e12 / FP64_PEAK_TFLOPS,
@@ -397,6 +416,14 @@ def run_c3(args, dev, stream, barrier, dist, world):
     sch = mhd.scheme("plm_mc", "hlld", "q26")
     st = mhd.to_device(cons, b, dev)
     ms = _timed_steps(ctx, st, sch, eta, steps, stream, barrier, dist, dev)
+    # the kernel split from 20 more steps with the library's per-class events on
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    for _ in range(20):
+        ctx.step_cfl(st, 0.3, sch, eta)
+    barrier()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
     N = 512 * 512 * 4
     md, mb = ctx.divb(st)
     s1, s2 = ctx.stats()
@@ -407,7 +434,8 @@ def run_c3(args, dev, stream, barrier, dist, world):
                           "ms_per_step": ms / steps,
                           "fp64_frac_of_peak": r * FLOPS_PER_CELL_UPDATE["harris"] / 1e12 / FP64_PEAK_TFLOPS,
                           "hbm_frac": r * ALG_BYTES_PER_CELL_UPDATE / 1e9 / HBM_PEAK_GBS,
-                          "max_divb_dx_over_b": md * info["h"][0] / mb, "fofc_flagged_last_step": [s1, s2]}}
+                          "max_divb_dx_over_b": md * info["h"][0] / mb, "fofc_flagged_last_step": [s1, s2],
+                          "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}}
 
 
 def run_fwd_adjoint(args, dev, stream, barrier, dist, world):
