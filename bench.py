@@ -44,7 +44,7 @@ HBM_PEAK_GBS = 6759.6  # measured copy bandwidth of this GPU model (STREAM-style
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 677.1e6, "cells": 160**3, "src": "2827a46e34d03c7d"}}
+TRAFFIC = {"face": {"bytes_per_launch": 675.5e6, "cells": 160**3, "src": "519176d84ca6a31b"}}
 
 
 # what the face sweep's machine code is compiled from: its kernel, the numerics and indexing
@@ -327,7 +327,7 @@ def run_alfven(args, dev, stream, barrier, dist, world):
     ctx.close()
     out[f"alfven{n}_config"] = {"cells": n**3, "steps": steps,
                                 "scheme": "PPM-EP + HLLD + {Q26, FS18, B25a} + LD04 (and Q26 with PPM)",
-                                "q26_fp64_frac_of_peak": out[f"alfven{n}_q26"] / world * FLOPS_PER_CELL_UPDATE[
+                                "q26_fp64_frac_of_nominal_peak": out[f"alfven{n}_q26"] / world * FLOPS_PER_CELL_UPDATE[
                                     "alfven_ppm_ep"] / 1e12 / FP64_PEAK_TFLOPS,
                                 "q26_speedup_vs_fs18": out[f"alfven{n}_q26"] / out[f"alfven{n}_fs18"] - 1,
                                 "q26_speedup_vs_b25a": out[f"alfven{n}_q26"] / out[f"alfven{n}_b25a"] - 1}
@@ -399,7 +399,7 @@ def run_c1(args, dev, stream, barrier, dist, world):
     bt.close()
     r = out["c1_fast_wave_32cubed_graph"] / world
     out["c1_config"] = {"cells": 32**3, "steps": steps, "scheme": "PLM-MC + HLL + Q26 + LD04",
-                        "fp64_frac_of_peak": r * FLOPS_PER_CELL_UPDATE["fast_wave"] / 1e12 / FP64_PEAK_TFLOPS,
+                        "fp64_frac_of_nominal_peak": r * FLOPS_PER_CELL_UPDATE["fast_wave"] / 1e12 / FP64_PEAK_TFLOPS,
                         "hbm_frac": r * ALG_BYTES_PER_CELL_UPDATE / 1e9 / HBM_PEAK_GBS,
                         "max_divb_dx_over_b": md * info["h"][0] / mb}
     return out
@@ -432,10 +432,40 @@ def run_c3(args, dev, stream, barrier, dist, world):
     return {"c3_reconnection_512x512x4": whole_job_rate(N * steps, world, ms),
             "c3_config": {"cells": N, "steps": steps, "eta": eta, "scheme": "PLM-MC + HLLD + Q26 + LD04",
                           "ms_per_step": ms / steps,
-                          "fp64_frac_of_peak": r * FLOPS_PER_CELL_UPDATE["harris"] / 1e12 / FP64_PEAK_TFLOPS,
+                          "fp64_frac_of_nominal_peak": r * FLOPS_PER_CELL_UPDATE["harris"] / 1e12 / FP64_PEAK_TFLOPS,
                           "hbm_frac": r * ALG_BYTES_PER_CELL_UPDATE / 1e9 / HBM_PEAK_GBS,
                           "max_divb_dx_over_b": md * info["h"][0] / mb, "fofc_flagged_last_step": [s1, s2],
                           "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}}
+
+
+def run_adjoint_step(args, dev, stream, barrier, dist, world):
+    """The adjoint step alone: 64^3 turbulence at Mach 2 (the differentiation workload's state),
+    PPM + HLLD + Q26 + LD04, eta = 1e-3, mhd_step_adjoint called `adj_reps` times with a seeded
+    random adjoint state (each call reruns the forward stages it needs); ms per adjoint step."""
+    import numpy as np
+    import torch
+
+    from paper_2609_10816_gb300 import inputs, mhd
+
+    n, eta = args.adj_n, 1e-3
+    cons, b, info = inputs.turbulence((n, n, n), seed=2, v_rms=2.0)
+    ctx = mhd.Context((n, n, n), info["h"], stream=stream)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    st = mhd.to_device(cons, b, dev)
+    dt = ctx.max_dt(st, 0.3, eta)
+    rng = np.random.default_rng(8)
+    lam = mhd.to_device(rng.normal(size=cons.shape), rng.normal(size=b.shape), dev)
+    ctx.step_adjoint(st, lam, dt, sch, eta)  # warm-up (allocates the adjoint scratch)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.adj_reps):
+        ctx.step_adjoint(st, lam, dt, sch, eta)
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev) / args.adj_reps
+    ctx.close()
+    return {"adjoint_step_ms": ms, "adjoint_step_config": {"cells": n**3, "calls": args.adj_reps, "eta": eta}}
 
 
 def run_fwd_adjoint(args, dev, stream, barrier, dist, world):
@@ -521,15 +551,17 @@ def main():
     ap.add_argument("--npatch", type=int, default=1024)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint form")
     ap.add_argument("--adj-n", type=int, default=64)
+    ap.add_argument("--adj-reps", type=int, default=8, help="calls of the adjoint-step form")
     ap.add_argument("--no-alfven", action="store_true", help="skip the oblique Alfven-wave throughput runs")
     ap.add_argument("--alfven-n", type=int, default=128)
     ap.add_argument("--alfven-steps", type=int, default=100)
     ap.add_argument("--no-c1", action="store_true", help="skip the 32^3 fast-eigenmode form")
     ap.add_argument("--no-c3", action="store_true", help="skip the 512x512x4 reconnection form")
     ap.add_argument("--only", default=None,
-                    help="comma-separated forms to run besides the headline step (emf, batch, alfven, adjoint, c1, c3, "
-                         "e2e, cpu); the rest are skipped")
+                    help="comma-separated forms to run besides the headline step (emf, batch, alfven, adjoint, "
+                         "adjoint_step, c1, c3, e2e, cpu); the rest are skipped (adjoint_step runs only when named)")
     args = ap.parse_args()
+    args.adjoint_step = False
     if args.only is not None:
         keep = set(x.strip() for x in args.only.split(",") if x.strip())
         args.q26_only = "emf" not in keep
@@ -539,6 +571,7 @@ def main():
         args.no_c1 = "c1" not in keep
         args.no_c3 = "c3" not in keep
         args.no_cpu_baseline = "cpu" not in keep
+        args.adjoint_step = "adjoint_step" in keep
         if "e2e" not in keep:
             args.e2e_steps = 0
     if args.impl == "reference":
@@ -584,6 +617,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # the FP64 pipe's measured rate on this GPU (DFMA, DADD, DMUL), the roofline's denominator
+    fp64_probe = {k: mhd.fp64_rate(k, 1 << 14, stream) for k in ("dfma", "dadd", "dmul")}
+    fp64_peak_tflops = 2.0 * fp64_probe["dfma"] / 1e12
+
     # ---- device-resident timed region ------------------------------------------------------
     ctx.profile(True)
     ctx.profile_read(reset=True)
@@ -612,7 +649,7 @@ def main():
         flops_per_launch = FLOPS_PER_FACE[key] * N
     else:
         flops_per_launch = float("nan")
-    fp64_probe = {k: mhd.fp64_rate(k, 1 << 13, stream) for k in ("dfma", "dadd", "dmul")}
+
     achieved = flops_per_launch / per_launch_s / 1e12
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] * (N / tr["cells"]) if tr and tr.get("src") == kernel_src_hash() else None
@@ -643,6 +680,9 @@ def main():
 
     if not args.no_alfven:
         forms.update(run_alfven(args, dev, stream, barrier, dist, world))
+
+    if args.adjoint_step:
+        forms.update(run_adjoint_step(args, dev, stream, barrier, dist, world))
 
     if not args.no_adjoint:
         forms.update(run_fwd_adjoint(args, dev, stream, barrier, dist, world))
@@ -724,16 +764,20 @@ def main():
             "kernel": dom,
             "bound": "alu",
             "achieved": achieved,
-            "peak": FP64_PEAK_TFLOPS,
+            "peak": fp64_peak_tflops,
             "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
+            "frac": achieved / fp64_peak_tflops,
             "traffic": traffic,
-            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (recipe unit counts and max clock)",
+            "peak_source": "FP64 measured on this GPU in this run: 2 flops x the DFMA rate of mhd_fp64_rate "
+                           "(independent chains on every SM)",
+            "frac_of_nominal": achieved / FP64_PEAK_TFLOPS,
+            "nominal_peak": FP64_PEAK_TFLOPS,
+            "nominal_source": "152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (recipe SM count and maximum clock)",
             "algorithmic_flops_per_launch": flops_per_launch,
             "flops_per_unit": f"{FLOPS_PER_FACE[key]} per face (HLLD one-sided; {FLOPS_PER_FACE['turbulence_full_hlld']} "
                               f"with both sides' star states), x {N} faces per launch",
             "frac_full_hlld_count": (FLOPS_PER_FACE["turbulence_full_hlld"] * N / per_launch_s / 1e12
-                                     / FP64_PEAK_TFLOPS) if dom == "face" else None,
+                                     / fp64_peak_tflops) if dom == "face" else None,
             "avg_launch_ms": per_launch_s * 1e3,
         },
         "fp64_probe": {
@@ -750,7 +794,8 @@ def main():
         "fp64_whole_step": {
             "algorithmic_flops_per_cell_update": FLOPS_PER_CELL_UPDATE[key],
             "achieved_TFLOPs": value / world * FLOPS_PER_CELL_UPDATE[key] / 1e12,
-            "frac": value / world * FLOPS_PER_CELL_UPDATE[key] / 1e12 / FP64_PEAK_TFLOPS,
+            "frac": value / world * FLOPS_PER_CELL_UPDATE[key] / 1e12 / fp64_peak_tflops,
+            "frac_of_nominal": value / world * FLOPS_PER_CELL_UPDATE[key] / 1e12 / FP64_PEAK_TFLOPS,
         },
         "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
         "e2e": {
