@@ -147,14 +147,28 @@ WORKLOAD_NAME = ("{n}^3 periodic FP64 ideal decaying MHD turbulence: rho=1, B0=(
                  "compute + LD04 averaging, RK2-SSP with first-order flux correction, CFL 0.3")
 
 
-def _oracle_worker_init(n):
-    """Spawned process: the oracle and one box of the timed workload's recipe."""
+# the CPU oracle's workloads: recipe -> (inputs, scheme)
+ORACLE_RECIPES = {
+    "turbulence": dict(recon="ppm", riemann="hlld", emf="q26", eta=0.0),
+    "fast_wave": dict(recon="plm_mc", riemann="hll", emf="q26", eta=0.0),
+    "harris": dict(recon="plm_mc", riemann="hlld", emf="q26", eta=1e-4),
+}
+
+
+def _oracle_worker_init(recipe, shape):
+    """Spawned process: the oracle and one box of a workload's recipe."""
     global _W
     import oracle
+    from paper_2609_10816_gb300 import inputs
 
-    cons, b, info = workload(n)
-    _W = {"cfg": oracle.Config(shape=(n, n, n), h=info["h"], recon="ppm", riemann="hlld", emf="q26"),
-          "cons": cons, "b": b}
+    if recipe == "turbulence":
+        cons, b, info = inputs.turbulence(shape, seed=2, v_rms=5.0)
+    elif recipe == "fast_wave":
+        cons, b, info = inputs.fast_wave(shape)
+    else:
+        cons, b, info = inputs.harris_sheet(shape)
+    sch = ORACLE_RECIPES[recipe]
+    _W = {"cfg": oracle.Config(shape=shape, h=info["h"], **sch), "cons": cons, "b": b}
 
 
 def _oracle_worker_steps(arg):
@@ -171,10 +185,20 @@ def _oracle_worker_steps(arg):
     return k, time.perf_counter() - t0
 
 
-def _oracle_pool(n, procs):
+def _oracle_pool(n, procs, recipe="turbulence", shape=None):
     import multiprocessing as mp
 
-    return mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(n,))
+    shape = shape or (n, n, n)
+    return mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(recipe, shape))
+
+
+def oracle_rate(recipe, shape, budget_s, procs):
+    """Cell-updates/s of the oracle on `procs` processes, each advancing its own box for budget_s."""
+    with _oracle_pool(0, procs, recipe, shape) as pool:
+        pool.map(_oracle_worker_steps, [(0.0, 1)] * procs)
+        res = pool.map(_oracle_worker_steps, [(budget_s, None)] * procs)
+    ncell = shape[0] * shape[1] * shape[2]
+    return sum(ncell * k / el for k, el in res), sum(k for k, _ in res)
 
 
 def host_cores():
@@ -189,14 +213,16 @@ def cpu_baseline(budget_s=12.0, n=48):
     spawned process per core advances its own box of the workload's recipe for budget_s seconds;
     the rate is the sum over processes."""
     procs = host_cores()
-    with _oracle_pool(n, procs) as pool:
-        pool.map(_oracle_worker_steps, [(0.0, 1)] * procs)  # warm-up: one step each
-        res = pool.map(_oracle_worker_steps, [(budget_s, None)] * procs)
-    rate = sum(n**3 * k / el for k, el in res)
-    steps = sum(k for k, _ in res)
+    rate, steps = oracle_rate("turbulence", (n, n, n), budget_s, procs)
+    one, _ = oracle_rate("turbulence", (n, n, n), budget_s / 3, 1)
+    fw, _ = oracle_rate("fast_wave", (32, 32, 32), budget_s / 3, procs)
+    hs, _ = oracle_rate("harris", (128, 128, 4), budget_s / 3, procs)
     return {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
             "sample": f"{procs} processes (one per host core), each advancing its own {n}^3 box of the same recipe "
-                      f"(PPM+HLLD+Q26+LD04, CFL dt + RK2/FOFC step) for {budget_s:.0f} s: {steps} steps in all"}
+                      f"(PPM+HLLD+Q26+LD04, CFL dt + RK2/FOFC step) for {budget_s:.0f} s: {steps} steps in all",
+            "one_core": one,
+            "other_configs_all_cores": {"fast_wave_32cubed_plm_hll": fw,
+                                        "harris_128x128x4_plm_hlld_eta1e-4": hs}}
 
 
 def run_reference(args):
