@@ -155,6 +155,9 @@ ORACLE_RECIPES = {
 }
 
 
+_W = None  # the oracle worker's box (set in each spawned process)
+
+
 def _oracle_worker_init(recipe, shape):
     """Spawned process: the oracle and one box of a workload's recipe."""
     global _W
