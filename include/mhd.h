@@ -104,7 +104,13 @@ mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double e
  * synchronisation (and a sequence of them can be recorded in a CUDA graph). cfl > 0 and eta >= 0
  * finite. Where mhd_max_dt would report MHD_ERR_NONFINITE, the step runs with dt = 0 (the state
  * is then unchanged wherever its fluxes are finite) and mhd_last_dt reports MHD_ERR_NONFINITE.
- * Asynchronous. */
+ * Asynchronous.
+ * Small boxes (at most 64^3 cells, cubic cells, the Q26 EMF compute, the default validity criteria,
+ * b0, b1, b2 contiguous in that order, profiling off and the stream not being captured) run as a
+ * batch of one patch (see mhd_batch_step: one persistent launch per stage, replayed as a CUDA
+ * graph), with bitwise the same results: the sweeps cannot fill the GPU there. That path allocates
+ * its batch on first use, and synchronises the stream whenever the state arrays, scheme, eta or
+ * cfl differ from its previous call. */
 mhd_status mhd_step_cfl(mhd_ctx *ctx, const mhd_state *state, double cfl, int scheme, double eta);
 
 /* The dt of the last mhd_step_cfl on this context (0 before any). Synchronous (reads two
@@ -116,7 +122,7 @@ mhd_status mhd_last_dt(mhd_ctx *ctx, double *dt_out);
 mhd_status mhd_divb(mhd_ctx *ctx, const mhd_state *state, double *max_abs_divb, double *max_abs_b);
 
 /* Cells flagged invalid by first-order flux correction in stage 1 and stage 2 of the last
- * mhd_step (Sec. 2.5). Synchronous. */
+ * mhd_step or mhd_step_cfl (Sec. 2.5). Synchronous. */
 mhd_status mhd_stats(mhd_ctx *ctx, long long *fofc_cells_stage1, long long *fofc_cells_stage2);
 
 /* Kernel classes reported by mhd_profile_read (one entry per class; a class may cover several
@@ -279,7 +285,9 @@ mhd_status mhd_batch_set_schedule(mhd_batch *batch, int seg, int order, int bloc
 
 /* Autotuner: times one step for every candidate schedule (seg in {16, 32, 64, 128}, both orders,
  * 1 .. max CTAs per SM) on a scratch copy of `state` (left unchanged; the copy is allocated and
- * freed here), keeps the fastest and returns it. */
+ * freed here), keeps the fastest and returns it. The choice is remembered for the process, keyed
+ * by the device, the scheme, whether eta is zero and the histogram of patch sizes: a later call
+ * with the same key (on this batch or another) sets that schedule without timing anything. */
 mhd_status mhd_batch_tune(mhd_batch *batch, const mhd_batch_state *state, double cfl, int scheme, double eta,
                           int *seg, int *order, int *blocks_per_sm);
 

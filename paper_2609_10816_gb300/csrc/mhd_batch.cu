@@ -9,6 +9,10 @@
 // by timing candidates.
 #include <algorithm>
 #include <cstring>
+#include <tuple>
+#include <array>
+#include <mutex>
+#include <map>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -427,6 +431,10 @@ struct mhd_batch {
   bool graph_ok;
 };
 
+// schedules chosen by mhd_batch_tune, keyed by device, scheme and patch-size histogram
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 3>> g_tune_cache;
+
 namespace {
 
 thread_local std::string g_batch_create_err;
@@ -837,6 +845,30 @@ mhd_status mhd_batch_phase_ms(mhd_batch* b, double* ms) {
 mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta, int* seg_out,
                           int* order_out, int* bps_out) {
   if (!b || !s || !s->cons || !s->b) return MHD_ERR_ARG;
+  // the choice depends on the device, the scheme and the patches' sizes (not on their order or
+  // state): a batch with the same histogram of patch sizes reuses an earlier choice untimed
+  std::string key;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::map<std::tuple<int, int, int>, int> hist;
+    for (int p = 0; p < b->npatch; ++p) ++hist[std::make_tuple(b->dims[3 * p], b->dims[3 * p + 1], b->dims[3 * p + 2])];
+    key = std::to_string(dev) + ":" + std::to_string(b->nsm) + ":" + std::to_string(scheme) + ":" +
+          std::to_string(eta != 0.0 ? 1 : 0);
+    for (const auto& kv : hist)
+      key += ":" + std::to_string(std::get<0>(kv.first)) + "x" + std::to_string(std::get<1>(kv.first)) + "x" +
+             std::to_string(std::get<2>(kv.first)) + "*" + std::to_string(kv.second);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const int c_seg = it->second[0], c_order = it->second[1], c_bps = it->second[2];
+      mhd_status st = mhd_batch_set_schedule(b, c_seg, c_order, c_bps, b->use_graph);
+      if (seg_out) *seg_out = c_seg;
+      if (order_out) *order_out = c_order;
+      if (bps_out) *bps_out = c_bps;
+      return st;
+    }
+  }
   // time one step per candidate on a scratch copy of the state (the caller's state is unchanged)
   double* cpy = nullptr;
   cudaError_t e = cudaMalloc(&cpy, 8 * b->ncell * sizeof(double));
@@ -884,6 +916,10 @@ mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, in
   cudaFree(cpy);
   if (st != MHD_OK) return st;
   st = mhd_batch_set_schedule(b, bs, bo, bb, saved_graph);
+  if (st == MHD_OK) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {bs, bo, bb};
+  }
   if (seg_out) *seg_out = bs;
   if (order_out) *order_out = bo;
   if (bps_out) *bps_out = bb;

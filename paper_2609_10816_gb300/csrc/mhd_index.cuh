@@ -100,7 +100,7 @@ __device__ __forceinline__ void for_each_segment(unsigned long long* cursor, lon
 // the sweep has at least two segments per resident thread, so that small boxes still fill the GPU
 // (a shorter segment costs one more window start-up, about two points of reconstruction).
 __host__ __device__ inline int fill_seg(const Dev& D, int dir, int seg, long long resident_threads) {
-  while (seg > 8 && sweep_threads(D, dir, seg) < 2 * resident_threads) seg = (seg + 1) / 2;
+  while (seg > 4 && sweep_threads(D, dir, seg) < 2 * resident_threads) seg = (seg + 1) / 2;
   return seg;
 }
 

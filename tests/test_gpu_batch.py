@@ -1,4 +1,6 @@
 """Batched patches (mhd_batch_*) against the single-box step and the oracle (GPU)."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -122,9 +124,18 @@ def test_batch_autotune_keeps_results(gpu_lib):
     cons, b = bt.pack(pats)
     sch = mhd.scheme("ppm", "hlld", "q26")
     ref_c, ref_b = cons.clone(), b.clone()
+    t0 = time.perf_counter()
     choice = bt.tune(cons, b, 0.3, sch)
+    t_first = time.perf_counter() - t0
     assert choice["seg"] in (16, 32, 64, 128) and choice["order"] in (0, 1) and choice["blocks_per_sm"] >= 1
     assert torch.equal(cons, ref_c) and torch.equal(b, ref_b)  # tuning leaves the state alone
+    # the choice is remembered by patch-size histogram: another batch of the same sizes (in another
+    # order) gets it without timing
+    bt2 = mhd.Batch(dims[::-1], H)
+    t0 = time.perf_counter()
+    again = bt2.tune(*bt2.pack(pats[::-1]), 0.3, sch)
+    assert again == choice and time.perf_counter() - t0 < 0.5 * t_first, (again, choice)
+    bt2.close()
     bt.step(cons, b, 0.3, sch)
     bt.set_schedule(seg=7, order=0, blocks_per_sm=1, use_graph=False)
     bt.step(ref_c, ref_b, 0.3, sch)

@@ -181,6 +181,65 @@ def test_step_with_device_cfl_equals_host_cfl(gpu_lib):
     assert_parity(st.cons.cpu().numpy(), st.b.cpu().numpy(), co, bo, what="step_cfl")
 
 
+@pytest.mark.parametrize("case", ["smooth", "flagged"])
+def test_small_box_step_cfl_equals_sweeps(gpu_lib, case):
+    """A small box of cubic cells: mhd_step_cfl runs it as a batch of one patch; the state, dt and
+    flag counts equal bitwise those of mhd_max_dt + mhd_step (the sweeps), over three steps, and the
+    first step agrees with the oracle."""
+    shape = (20, 12, 8)
+    h = (0.05, 0.05, 0.05)
+    if case == "smooth":
+        cons, b, _ = inputs.random_smooth(shape, seed=17, rough=0.05, h=h)
+        cfl, eta = 0.3, 2e-3
+    else:
+        cons, b, _ = _low_pressure_state(shape)
+        cfl, eta = 0.6, 0.0
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    ctx = mhd.Context(shape, h)
+    st_s, st_b = mhd.to_device(cons, b), mhd.to_device(cons, b)
+    flagged = 0
+    for k in range(3):
+        dt = ctx.max_dt(st_s, cfl, eta)
+        ctx.step(st_s, dt, sch, eta)
+        cnt = ctx.stats()
+        ctx.step_cfl(st_b, cfl, sch, eta)
+        assert ctx.last_dt() == dt and ctx.stats() == cnt
+        flagged += cnt[0] + cnt[1]
+        torch.cuda.synchronize()
+        assert torch.equal(st_s.cons, st_b.cons) and torch.equal(st_s.b, st_b.b), k
+    assert case == "smooth" or flagged > 0
+    cfg = oracle.Config(shape=shape, h=h, recon="ppm", riemann="hlld", eta=eta)
+    co, bo, _ = oracle.step(cfg, cons, b, oracle.max_dt(cfg, cons, b, cfl))
+    st = mhd.to_device(cons, b)
+    ctx.step_cfl(st, cfl, sch, eta)
+    torch.cuda.synchronize()
+    assert_parity(st.cons.cpu().numpy(), st.b.cpu().numpy(), co, bo, what=f"small box {case}")
+
+
+def test_small_box_step_cfl_in_a_cuda_graph(gpu_lib):
+    """While the stream is captured, a small box takes the sweeps (capture-safe); the replayed graph
+    equals the eager steps (taken as a batch of one patch) bitwise."""
+    shape = (12, 10, 8)
+    h = (0.1, 0.1, 0.1)
+    cons, b, _ = inputs.random_smooth(shape, seed=19, rough=0.05, h=h)
+    s = torch.cuda.Stream()
+    ctx = mhd.Context(shape, h, stream=s)
+    sch = mhd.scheme("plm_mc", "hll", "q26")
+    st_e, st_g = mhd.to_device(cons, b), mhd.to_device(cons, b)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        ctx.step_cfl(st_e, 0.3, sch)
+    dt_e = ctx.last_dt()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(3):
+            ctx.step_cfl(st_g, 0.3, sch)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(st_e.cons, st_g.cons) and torch.equal(st_e.b, st_g.b)
+    assert ctx.last_dt() == dt_e
+
+
 def test_step_cfl_sequence_in_a_cuda_graph(gpu_lib):
     """Four step_cfl calls recorded in one CUDA graph replay to the eager result bit for bit (the
     step needs no host round trip, so a sequence of steps can run as one graph launch)."""
