@@ -108,9 +108,10 @@ mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double e
  * Small boxes (at most 64^3 cells, cubic cells, the Q26 EMF compute, the default validity criteria,
  * b0, b1, b2 contiguous in that order, profiling off and the stream not being captured) run as a
  * batch of one patch (see mhd_batch_step: one persistent launch per stage, replayed as a CUDA
- * graph), with bitwise the same results: the sweeps cannot fill the GPU there. That path allocates
- * its batch on first use, and synchronises the stream whenever the state arrays, scheme, eta or
- * cfl differ from its previous call. */
+ * graph), with bitwise the same results: the sweeps cannot fill the GPU there. That path is taken
+ * on the first call and whenever the state arrays, scheme, cfl and eta repeat the previous call's
+ * (otherwise the sweeps run); it allocates its batch on first use and synchronises the stream when
+ * it builds the batch's parameters and graph for new arguments. */
 mhd_status mhd_step_cfl(mhd_ctx *ctx, const mhd_state *state, double cfl, int scheme, double eta);
 
 /* The dt of the last mhd_step_cfl on this context (0 before any). Synchronous (reads two

@@ -34,6 +34,12 @@ struct mhd_ctx {
   // small boxes: mhd_step_cfl runs them as a batch of one patch (created on first use)
   mhd_batch* small;
   bool last_small;  // the last step went through `small` (its dt and flag counts are there)
+  // arguments of the previous mhd_step_cfl: the batch is used only when they repeat (it rebuilds
+  // its parameters and graph, with a synchronisation, whenever they change)
+  const double* prev_cons;
+  const double* prev_b0;
+  int prev_scheme;
+  double prev_cfl, prev_eta;
 };
 
 namespace {
@@ -173,6 +179,10 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   c->adj = nullptr;
   c->small = nullptr;
   c->last_small = false;
+  c->prev_cons = nullptr;
+  c->prev_b0 = nullptr;
+  c->prev_scheme = -1;
+  c->prev_cfl = c->prev_eta = -1.0;
   mhd::Dev& D = c->base;
   std::memset(&D, 0, sizeof(D));
   D.n[0] = cfg->nx; D.n[1] = cfg->ny; D.n[2] = cfg->nz;
@@ -338,7 +348,9 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
 // with short segments is 2-3x faster at 32^3; from about 96^3 the sweeps are faster), with the
 // cubic cells, the EMF compute, the validity criteria and the contiguous face arrays the batched
 // step takes, and not while the stream is being captured (the batch synchronises when it builds its
-// parameters and graph). The results are bitwise those of the sweeps.
+// parameters and graph); and only when the state arrays, scheme, cfl and eta repeat those of the
+// previous call or this is the first call (so alternating states or settings never rebuild the
+// batch's graph every step). The results are bitwise those of the sweeps.
 constexpr long long kSmallBoxCells = 64LL * 64 * 64;
 static bool small_box_route(mhd_ctx* ctx, const mhd_state* state, const Decoded& sc) {
   const mhd::Dev& D = ctx->base;
@@ -359,7 +371,15 @@ mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int sc
   Decoded sc;
   mhd_status s = decode(ctx, scheme, sc);
   if (s != MHD_OK) return s;
-  if (small_box_route(ctx, state, sc)) {
+  const bool repeat = ctx->prev_cons == nullptr ||
+                      (ctx->prev_cons == state->cons && ctx->prev_b0 == state->b0 && ctx->prev_scheme == scheme &&
+                       ctx->prev_cfl == cfl && ctx->prev_eta == eta);
+  ctx->prev_cons = state->cons;
+  ctx->prev_b0 = state->b0;
+  ctx->prev_scheme = scheme;
+  ctx->prev_cfl = cfl;
+  ctx->prev_eta = eta;
+  if (repeat && small_box_route(ctx, state, sc)) {
     if (!ctx->small) {
       const int dims[3] = {ctx->base.n[0], ctx->base.n[1], ctx->base.n[2]};
       s = mhd_batch_create(dims, 1, ctx->base.h[0], ctx->base.gam, ctx->stream, &ctx->small);
