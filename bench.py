@@ -44,7 +44,7 @@ HBM_PEAK_GBS = 6759.6  # measured copy bandwidth of this GPU model (STREAM-style
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
 # DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 675.5e6, "cells": 160**3, "src": "519176d84ca6a31b"}}
+TRAFFIC = {"face": {"bytes_per_launch": 675.1e6, "cells": 160**3, "src": "b71c15425b46c7d1"}}
 
 
 # what the face sweep's machine code is compiled from: its kernel, the numerics and indexing

@@ -96,7 +96,7 @@ __device__ __forceinline__ void for_each_segment(unsigned long long* cursor, lon
   }
 }
 
-// Segment length of a dynamically scheduled sweep: the requested length, halved (down to 8) until
+// Segment length of a dynamically scheduled sweep: the requested length, halved (down to 4) until
 // the sweep has at least two segments per resident thread, so that small boxes still fill the GPU
 // (a shorter segment costs one more window start-up, about two points of reconstruction).
 __host__ __device__ inline int fill_seg(const Dev& D, int dir, int seg, long long resident_threads) {
