@@ -630,6 +630,9 @@ def main():
 
     # the FP64 pipe's measured rate on this GPU (DFMA, DADD, DMUL), the roofline's denominator
     fp64_probe = {k: mhd.fp64_rate(k, 1 << 14, stream) for k in ("dfma", "dadd", "dmul")}
+    # what a binary64 multiply on the integer pipe adds (not used by the step's kernels)
+    fp64_probe.update({k: mhd.fp64_rate(k, 1 << 13, stream) for k in ("int_mul", "dfma_int_mul",
+                                                                      "dfma_int_mul_2x128")})
     fp64_peak_tflops = 2.0 * fp64_probe["dfma"] / 1e12
 
     # ---- device-resident timed region ------------------------------------------------------
@@ -794,7 +797,9 @@ def main():
         "fp64_probe": {
             "ops_per_s": fp64_probe,
             "per_sm_per_clock": {k: v / 152 / ((clk_mhz or 2070.0) * 1e6) for k, v in fp64_probe.items()},
-            "how": "mhd_fp64_rate: 8 independent chains per thread, 8 x 256 threads per SM, CUDA events",
+            "how": "mhd_fp64_rate: 8 independent chains per thread, 8 x 256 threads per SM, CUDA events; "
+                   "int_mul: chains of the integer-pipe binary64 multiply; dfma_int_mul: 4 DFMA + 4 of those "
+                   "chains (operations of both counted); _2x128: at 2 blocks of 128 threads per SM",
         },
         "hbm_roofline": {
             "algorithmic_bytes_per_cell_update": ALG_BYTES_PER_CELL_UPDATE,

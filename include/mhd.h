@@ -173,9 +173,12 @@ mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_stat
  * [4] receive how many times the integer-pipe halving and quadrupling differ in any bit from the
  * FP64 multiplies by 0.5 and 4, and max_rel_err[5] on n pairs of non-NaN doubles (zeros,
  * subnormals, extreme binades and infinities among them) how many times an integer-pipe sign
- * test, comparison, min/max, |x|, sign copy or sign flip disagrees with the IEEE operation (0
- * expected for all three; -0 and +0 are ordered -0 < +0 by the kernels' comparisons, which the
- * check allows). max_rel_err holds 6 doubles. Synchronous. The paper has no counterpart. */
+ * test, comparison, min/max, |x|, sign copy or sign flip disagrees with the IEEE operation;
+ * max_rel_err[6] on n pairs (nearby and extreme exponents, few significand bits for exact
+ * products and ties, any bit pattern, small integers and zeros) how many times the integer-pipe
+ * multiply of mhd_fp64_rate's kinds 4-6 differs in any bit from the FP64 multiply (0 expected
+ * for all four; -0 and +0 are ordered -0 < +0 by the kernels' comparisons, which the check
+ * allows). max_rel_err holds 7 doubles. Synchronous. The paper has no counterpart. */
 mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
 
 /* Measured rate of one FP64 instruction kind on the current GPU (the pipe that bounds every
@@ -183,8 +186,12 @@ mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
  * kind 0 DFMA, 1 DADD, 2 DMUL, 3 FP32 FFMA for comparison. Independent chains (eight per
  * thread, 8 blocks of 256 threads per SM) run `iters` steps each, timed with CUDA events on
  * `cuda_stream` after a shorter warm-up; *ops_per_s receives instructions per second (per
- * thread-lane). Synchronous; allocates 8 bytes of device memory for the duration of the call.
- * MHD_ERR_ARG for a kind outside 0-3 or iters outside [1, 2^30]. */
+ * thread-lane). Kinds 4-6 measure a binary64 multiply done on the integer pipe (bit for bit the
+ * FP64 multiply; mhd_math_check verifies it) that the step's kernels do not use: 4 eight chains
+ * of it, 5 four chains of it beside four DFMA chains, 6 the same mix at 2 blocks of 128 threads
+ * per SM (the face sweep's occupancy); *ops_per_s counts the operations of all chains.
+ * Synchronous; allocates 8 bytes of device memory for the duration of the call.
+ * MHD_ERR_ARG for a kind outside 0-6 or iters outside [1, 2^30]. */
 mhd_status mhd_fp64_rate(int kind, long long iters, void *cuda_stream, double *ops_per_s);
 
 /* Self-check of the adjoint's reverse sweep through the face solve (the Riemann solver of

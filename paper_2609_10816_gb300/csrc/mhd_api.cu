@@ -712,17 +712,20 @@ mhd_status mhd_math_check(mhd_ctx* ctx, long long n, double* max_rel_err) {
   ctx->err.clear();
   if (!max_rel_err || n < 1 || n > (1LL << 40)) return fail(ctx, MHD_ERR_ARG, "need 1 <= n <= 2^40 and an output");
   const mhd::Dev& D = ctx->base;
-  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, 6 * sizeof(unsigned long long), ctx->stream),
+  // 7 results: the scratch's work cursors serve (they are rezeroed before every sweep)
+  unsigned long long* out = D.work;
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(out, 0, 7 * sizeof(unsigned long long), ctx->stream),
                             "cudaMemsetAsync");
   if (s != MHD_OK) return s;
-  mhd::launch_math_check(n, D.counters + 2, ctx->stream);
+  mhd::launch_math_check(n, out, ctx->stream);
   s = cuda_check(ctx, cudaGetLastError(), "kernel launch");
   if (s != MHD_OK) return s;
-  unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
-  s = read_counters(ctx, h, 6);
+  unsigned long long h[7] = {0, 0, 0, 0, 0, 0, 0};
+  s = cuda_check(ctx, cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+  if (s == MHD_OK) s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   if (s != MHD_OK) return s;
   for (int k = 0; k < 3; ++k) std::memcpy(&max_rel_err[k], &h[k], sizeof(double));
-  for (int k = 3; k < 6; ++k) max_rel_err[k] = (double)h[k];
+  for (int k = 3; k < 7; ++k) max_rel_err[k] = (double)h[k];
   return MHD_OK;
 }
 

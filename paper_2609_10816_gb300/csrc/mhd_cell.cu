@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "mhd_cell.cuh"
+#include "mhd_softmul.cuh"
 
 namespace mhd {
 
@@ -200,6 +201,42 @@ __global__ void __launch_bounds__(256) k_math_check(long long n, unsigned long l
     bad |= dbits(neg_if(true, x)) != dbits(x * -1.0);
     bad |= dbits(neg_if(false, x)) != dbits(x);
     if (bad) atomicAdd(out + 5, 1ull);
+  }
+  // the integer-pipe multiply against the FP64 multiply, bit for bit (any two NaNs agree)
+  if (i < n) {
+    auto mix = [](unsigned long long z) {
+      z += 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    auto draw = [&](unsigned long long z, int kind, double other) {
+      const unsigned long long r = mix(z);
+      const unsigned long long sign = r & 0x8000000000000000ull, frac = r & 0x000fffffffffffffull;
+      unsigned long long ex;
+      switch (kind) {
+        case 0: ex = 1023 - 40 + (r >> 52) % 81; break;                       // nearby exponents
+        case 1: return dfrom((long long)r);                                   // any pattern
+        case 2:                                                               // few significand bits
+          return dfrom((long long)(sign | ((1020 + (r >> 56) % 7) << 52) | (frac & 0xff0000000000full)));
+        case 3: ex = (r >> 60) & 1 ? (r >> 52) % 60 : 2046 - (r >> 52) % 60; break;  // extreme binades
+        case 4: {  // the product's exponent at the overflow or the underflow edge
+          const long long edge = (r >> 59) & 1 ? 2046 : 1;
+          ex = (unsigned long long)(edge + (long long)((r >> 52) % 5) - 2 - ((dbits(other) >> 52) & 0x7ff) + 1023) &
+               0x7ff;
+          break;
+        }
+        default: return (double)((long long)(r % 33) - 16) * ((r >> 40) & 1 ? 0.5 : 1.0);  // small, zeros
+      }
+      return dfrom((long long)(sign | (ex << 52) | frac));
+    };
+    const unsigned long long s0 = (unsigned long long)(i + 3 * n) * 0xD6E8FEB86659FD93ull;
+    const int ka = (int)(mix(s0) % 6), kb = (int)(mix(s0 + 1) % 6);
+    const double x = draw(s0 + 2, ka == 4 ? 0 : ka, 0.0);
+    const double y = draw(s0 + 3, kb, x);
+    const double p0 = __dmul_rn(x, y), p1 = mul_int(x, y);
+    const bool mbad = (p0 == p0 || p1 == p1) && dbits(p0) != dbits(p1);
+    if (mbad) atomicAdd(out + 6, 1ull);
   }
 }
 

@@ -127,11 +127,14 @@ def lib():
     return L
 
 
-FP64_RATE_KINDS = {"dfma": 0, "dadd": 1, "dmul": 2, "ffma": 3}
+FP64_RATE_KINDS = {"dfma": 0, "dadd": 1, "dmul": 2, "ffma": 3, "int_mul": 4, "dfma_int_mul": 5,
+                   "dfma_int_mul_2x128": 6}
 
 
 def fp64_rate(kind: str = "dfma", iters: int = 1 << 14, stream: torch.cuda.Stream | None = None) -> float:
-    """mhd_fp64_rate: instructions per second (per lane) of one FP64 (or FP32 FFMA) kind."""
+    """mhd_fp64_rate: instructions per second (per lane) of one FP64 (or FP32 FFMA) kind, or
+    (kinds int_mul, dfma_int_mul, dfma_int_mul_2x128) operations per second of chains of the
+    integer-pipe multiply, alone or beside DFMA chains."""
     s = stream if stream is not None else torch.cuda.current_stream()
     out = ctypes.c_double()
     rc = lib().mhd_fp64_rate(FP64_RATE_KINDS[kind], int(iters), ctypes.c_void_p(s.cuda_stream), ctypes.byref(out))
@@ -237,8 +240,9 @@ class Context:
     def math_check(self, n: int = 1 << 22):
         """(largest relative errors of the kernels' reciprocal, rsqrt and sqrt vs IEEE, bit
         mismatches of the integer halving, of the integer quadrupling, disagreements of the
-        integer-pipe comparisons and sign operations with IEEE)."""
-        out = (ctypes.c_double * 6)()
+        integer-pipe comparisons and sign operations with IEEE, bit mismatches of the integer-pipe
+        multiply)."""
+        out = (ctypes.c_double * 7)()
         self._err(lib().mhd_math_check(self._h, int(n), out))
         return tuple(out)
 

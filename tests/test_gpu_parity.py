@@ -285,10 +285,11 @@ def test_step_cfl_reports_a_non_finite_speed(gpu_lib):
 def test_fast_reciprocal_and_sqrt_against_ieee(gpu_lib):
     """The kernels' reciprocal / rsqrt / sqrt stay within a few ulp of CUDA's IEEE results."""
     ctx = mhd.Context((4, 4, 4), (1, 1, 1))
-    er, es, eq, hbad, fbad, pbad = ctx.math_check(1 << 22)
+    er, es, eq, hbad, fbad, pbad, mbad = ctx.math_check(1 << 22)
     assert er <= 4 * 2.0**-53 and es <= 4 * 2.0**-53 and eq <= 4 * 2.0**-53, (er, es, eq)
     assert hbad == 0 and fbad == 0, (hbad, fbad)  # halving / quadrupling bit-exact
     assert pbad == 0, pbad  # sign tests, comparisons, min/max, |x|, sign copy / flip
+    assert mbad == 0, mbad  # the integer-pipe multiply of the rate probe, bit for bit
 
 
 def test_fp64_rate_probe(gpu_lib):
@@ -308,6 +309,18 @@ def test_fp64_rate_probe(gpu_lib):
     for k in ("dfma", "dadd", "dmul"):
         assert 0.5 <= per_sm_clk[k] <= 4.5, per_sm_clk
     assert rates["ffma"] > 10 * rates["dfma"]
+    # the integer-pipe multiply: a rate of the same order as the FP64 pipe's, alone and mixed
+    mixed = {k: mhd.fp64_rate(k, 1 << 12) / nsm / (mhz * 1e6) for k in ("int_mul", "dfma_int_mul",
+                                                                        "dfma_int_mul_2x128")}
+    print("integer-pipe multiply", {k: f"{v:.2f}/SM/clk" for k, v in mixed.items()})
+    assert all(0.2 <= v <= 8.0 for v in mixed.values()), mixed
     with pytest.raises(mhd.MHDError):
         mhd.fp64_rate("dfma", 0)
+    with pytest.raises(mhd.MHDError):
+        lib = mhd.lib()
+        import ctypes
+        out = ctypes.c_double()
+        rc = lib.mhd_fp64_rate(7, 1 << 10, None, ctypes.byref(out))
+        if rc != mhd.OK:
+            raise mhd.MHDError(rc, "kind 7")
 
