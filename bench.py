@@ -297,7 +297,7 @@ def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
                               "ms_per_step": ms / args.steps, "last_dt": dt,
                               "fofc_flagged_last_step": list(flagged),
                               "phase_ms_last_step": phases,
-                              "launches_per_step": "1 graph: maxspeed, set_dt, 2 persistent stage kernels"}}
+                              "launches_per_step": "1 graph: maxspeed, set_dt, per stage 3 persistent launches (faces; edges, update, flags; first-order correction, which exits at once when nothing is flagged)"}}
     bt.close()
     del cons, b
     if same_state is not None:

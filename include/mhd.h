@@ -107,7 +107,7 @@ mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double e
  * Asynchronous.
  * Small boxes (at most 64^3 cells, cubic cells, the Q26 EMF compute, the default validity criteria,
  * b0, b1, b2 contiguous in that order, profiling off and the stream not being captured) run as a
- * batch of one patch (see mhd_batch_step: one persistent launch per stage, replayed as a CUDA
+ * batch of one patch (see mhd_batch_step: persistent launches per stage, replayed as a CUDA
  * graph), with bitwise the same results: the sweeps cannot fill the GPU there. That path is taken
  * on the first call and whenever the state arrays, scheme, cfl and eta repeat the previous call's
  * (otherwise the sweeps run); it allocates its batch on first use and synchronises the stream when
@@ -237,10 +237,12 @@ mhd_status mhd_step_noalloc(const mhd_config *cfg, const mhd_state *state, doubl
  * A batch is a list of independent triply periodic patches of sizes dims[3p..3p+2] = (nx, ny, nz)
  * and common cell width h (one refinement level of an AMR hierarchy, each patch its own periodic
  * box). One step advances every patch by the same dt = cfl h / (max over all cells of all patches
- * of the CFL signal speed, Eq. resistivity:cfl), computed on the device. Each RK stage runs as one
- * persistent cooperative launch over all patches (grid-wide barriers with a bounded wait), and
- * the whole step is captured once as a CUDA graph and replayed while the state arrays, scheme,
- * eta and cfl stay the same. The batched step supports the Q26 EMF compute (FS18 and B25a ->
+ * of the CFL signal speed, Eq. resistivity:cfl), computed on the device. Each RK stage runs as
+ * persistent cooperative launches over all patches (grid-wide barriers with a bounded wait): the
+ * face sweeps at the face kernel's register budget; the edge sweeps, update and validity flags
+ * at half that budget (twice the warps per SM); and, with flux correction on, the first-order
+ * correction (returning at once when the stage flagged nothing). The whole step is captured once
+ * as a CUDA graph and replayed while the state arrays, scheme, eta and cfl stay the same. The batched step supports the Q26 EMF compute (FS18 and B25a ->
  * MHD_ERR_UNSUPPORTED). */
 typedef struct mhd_batch mhd_batch;
 
@@ -278,21 +280,22 @@ mhd_status mhd_batch_last_dt(mhd_batch *batch, double *dt);
  * clears a barrier timeout as mhd_batch_last_dt does. */
 mhd_status mhd_batch_stats(mhd_batch *batch, long long *fofc_cells_stage1, long long *fofc_cells_stage2);
 
-/* Device time of the phases of the last step's two stage launches (synchronous), as measured by
- * block 0 of the persistent kernel with the GPU global timer at each grid barrier it passes:
+/* Device time of the phases of the last step's two stages (synchronous), as measured by block 0
+ * of the persistent launches with the GPU global timer at each launch start and grid barrier:
  * ms[6 * stage + j] for j = 0 cons->prim, 1 face sweeps (reconstruction + Riemann), 2 a-face
  * quantities to edges, 3 c-face quantities to edges + LD04 EMFs, 4 increments, update and
  * validity flags, 5 first-order fluxes of flagged cells (0 when the phase did not run: no
  * flagged cell, or flux correction off). `ms` holds 12 doubles, written by this call. */
 mhd_status mhd_batch_phase_ms(mhd_batch *batch, double *ms);
 
-/* Schedule of the persistent stage kernel: sweep segment length seg (points per thread), patch
- * order (0 as given, 1 largest first), CTAs per SM (0 = as many as fit), and whether steps are
- * captured and replayed as a CUDA graph. */
+/* Schedule of the persistent stage launches: sweep segment length seg (points per thread), patch
+ * order (0 as given, 1 largest first), CTAs per SM of the face-sweep launch (0 = as many as fit;
+ * the other launches take as many as fit), and whether steps are captured and replayed as a
+ * CUDA graph. */
 mhd_status mhd_batch_set_schedule(mhd_batch *batch, int seg, int order, int blocks_per_sm, int use_graph);
 
 /* Autotuner: times one step for every candidate schedule (seg in {16, 32, 64, 128}, both orders,
- * 1 .. max CTAs per SM) on a scratch copy of `state` (left unchanged; the copy is allocated and
+ * 1 .. max CTAs per SM of the face-sweep launch) on a scratch copy of `state` (left unchanged; the copy is allocated and
  * freed here), keeps the fastest and returns it. The choice is remembered for the process, keyed
  * by the device, the scheme, whether eta is zero and the histogram of patch sizes: a later call
  * with the same key (on this batch or another) sets that schedule without timing anything. */

@@ -1,12 +1,15 @@
 // mhd_batch.cu -- many uneven periodic patches advanced together (the batched form of the step).
 //
-// Each stage of the step runs as ONE persistent cooperative launch: its blocks walk, phase after
-// phase, work lists that span every patch (cells for the per-cell phases, line segments of the
-// sweeps for the face and edge phases), separated by a grid-wide barrier of the library's own
-// with a bounded wait. The CFL reduction and the time step stay on the device, so one step
-// (reduction, dt, stage 1, stage 2, copy back) is captured once as a CUDA graph and replayed.
-// Patch order, sweep segment length and CTAs per SM form the schedule that mhd_batch_tune picks
-// by timing candidates.
+// Each stage of the step runs as two persistent cooperative launches whose blocks walk, phase
+// after phase, work lists that span every patch (cells for the per-cell phases, line segments of
+// the sweeps for the face and edge phases), separated by a grid-wide barrier of the library's own
+// with a bounded wait: the face phase (after stage 2's primitives where flux correction changed
+// stage 1's result) at the face sweep's register budget, then the edge, update, flag and
+// flux-correction phases in a kernel held to half that budget, so that they run with twice the
+// warps per SM. The CFL reduction and the time step stay on the device, so one step (reduction,
+// dt, stage 1, stage 2, copy back) is captured once as a CUDA graph and replayed. Patch order,
+// sweep segment length and the face launch's CTAs per SM form the schedule that mhd_batch_tune
+// picks by timing candidates.
 #include <algorithm>
 #include <cstring>
 #include <tuple>
@@ -131,12 +134,17 @@ __device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long lon
   });
 }
 
-// cells per thread per pass of the per-cell phases
+// cells per thread per pass of the per-cell phases: the face launch has few warps per SM to hide
+// memory latency, the other launch twice as many
 constexpr int kCellIlp = 4;
+constexpr int kRestIlp = 2;
+// CTAs of 128 threads per SM that the second launch of a stage is compiled to fit
+constexpr int kRestMinBlocks = 4;
 
+// stage 2's primitives (where flux correction changed stage 1's result) and the face sweeps
 template <int RC, int RS>
-__global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
-  // a barrier of an earlier stage gave up (the flag stays set until the host reads it): the
+__global__ void __launch_bounds__(128) k_batch_face(BatchDev B) {
+  // a barrier of an earlier launch gave up (the flag stays set until the host reads it): the
   // step is abandoned and the caller's state left as it was
   if (*(volatile unsigned long long*)(B.counters + 7)) return;
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -144,15 +152,14 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   const long long ncell = B.cell_pref[B.npatch];
   const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
   stamp(B, 0);
-  // the sweep phases' cursors start at zero; no block takes work from them before the first
-  // grid barrier, which block 0 passes only after this
+  // the sweep phases' cursors start at zero: the face phase's is taken only after the grid
+  // barrier below, which block 0 passes only after this, the edge phases' in the next launch
   if (blockIdx.x == 0 && threadIdx.x < 3) atomicExch(B.cursor + threadIdx.x, 0ull);
-  // per-patch flag counts of this stage start at zero (read after later barriers only)
+  // per-patch flag counts of this stage start at zero (read in the next launch only)
   unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
   for (long long i = t0; i < B.npatch; i += nth) pflags[i] = 0u;
-  // cons -> prim; the per-cell phases take kCellIlp cells per thread at a time, loads of all of
-  // them before any store (the persistent grid has few warps per SM to hide memory latency).
-  // Stage 1's primitives come from the CFL reduction, stage 2's from stage 1's update phase unless
+  // cons -> prim, kCellIlp cells per thread at a time, loads of all of them before any store.
+  // Stage 1's primitives come from the CFL reduction, stage 2's from stage 1's flag phase unless
   // flux correction changed its state (per patch: only patches where stage 1 flagged a cell are
   // redone).
   const bool prim_given = B.stage == 0 || *(volatile unsigned long long*)(B.counters + 0) == 0;
@@ -180,13 +187,21 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   if (!grid_sync(B)) return;
   stamp(B, 1);
   // face sweeps along each direction
-  {
-    const int dirs[3] = {0, 1, 2};
-    sweep_phase(B, B.cursor + 0, dirs, [&](const Dev& D, int j, const Line& ln, int m0, int m1) {
-      face_seg<RC, RS>(D, j, ln, m0, m1);
-    });
-  }
-  if (!grid_sync(B)) return;
+  const int dirs[3] = {0, 1, 2};
+  sweep_phase(B, B.cursor + 0, dirs, [&](const Dev& D, int j, const Line& ln, int m0, int m1) {
+    face_seg<RC, RS>(D, j, ln, m0, m1);
+  });
+}
+
+// the edge sweeps, the update, the validity flags and the first-order correction of the stage
+template <int RC>
+__global__ void __launch_bounds__(128, kRestMinBlocks) k_batch_rest(BatchDev B) {
+  if (*(volatile unsigned long long*)(B.counters + 7)) return;  // the face launch gave up
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ncell = B.cell_pref[B.npatch];
+  const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
+  unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
   stamp(B, 2);
   // a-face quantities to e-edges (lines along c = e + 2)
   {
@@ -210,12 +225,12 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
   // reads back instead of recomputing each cell's upper faces
   {
     int ku = k0;
-    for (long long base = t0; base < ncell; base += kCellIlp * nth) {
-      double w[kCellIlp][8];
-      const Dev* Dp[kCellIlp];
-      long long X[kCellIlp];
+    for (long long base = t0; base < ncell; base += kRestIlp * nth) {
+      double w[kRestIlp][8];
+      const Dev* Dp[kRestIlp];
+      long long X[kRestIlp];
 #pragma unroll
-      for (int g = 0; g < kCellIlp; ++g) {
+      for (int g = 0; g < kRestIlp; ++g) {
         const long long i = base + g * nth;
         Dp[g] = nullptr;
         if (i < ncell) {
@@ -226,21 +241,21 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
         }
       }
 #pragma unroll
-      for (int g = 0; g < kCellIlp; ++g)
+      for (int g = 0; g < kRestIlp; ++g)
         if (Dp[g]) store_update(*Dp[g], X[g], w[g]);
     }
   }
   if (!grid_sync(B)) return;
   // (every lane of a warp runs the same number of passes for the ballot)
   int kf = k0;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kCellIlp * nth) {
-    double u[kCellIlp][5], lo[kCellIlp][3], hi[kCellIlp][3], pw[kCellIlp][8];
-    int K[kCellIlp];
-    bool f[kCellIlp];
-    const Dev* Dp[kCellIlp];
-    long long X[kCellIlp];
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kRestIlp * nth) {
+    double u[kRestIlp][5], lo[kRestIlp][3], hi[kRestIlp][3], pw[kRestIlp][8];
+    int K[kRestIlp];
+    bool f[kRestIlp];
+    const Dev* Dp[kRestIlp];
+    long long X[kRestIlp];
 #pragma unroll
-    for (int g = 0; g < kCellIlp; ++g) {
+    for (int g = 0; g < kRestIlp; ++g) {
       const long long i = base + g * nth + threadIdx.x;
       Dp[g] = nullptr;
       if (i < ncell) {
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
     }
     unsigned cnt = 0;
 #pragma unroll
-    for (int g = 0; g < kCellIlp; ++g) {
+    for (int g = 0; g < kRestIlp; ++g) {
       f[g] = false;
       if (Dp[g]) {
         // stage 1 also forms the primitives of its result (stage 2's input), and reads the
@@ -269,10 +284,20 @@ __global__ void __launch_bounds__(128) k_batch_stage(BatchDev B) {
     }
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&B.counters[B.stage], (unsigned long long)cnt);
   }
-  if (!B.fofc) return;
-  if (!grid_sync(B)) return;
+}
+
+// first-order correction of the flagged patches' faces and edges and recompute of their touched
+// cells (a launch of its own at the face sweep's register budget: it solves several face
+// problems per cell; it returns at once when the stage flagged nothing)
+__global__ void __launch_bounds__(128) k_batch_fofc(BatchDev B) {
+  if (*(volatile unsigned long long*)(B.counters + 7)) return;  // an earlier launch gave up
   stamp(B, 5);
   if (*(volatile unsigned long long*)(B.counters + B.stage) == 0) return;  // uniform over the grid
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ncell = B.cell_pref[B.npatch];
+  const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
+  const unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
   // patches are independent boxes: only those with a flagged cell have anything to correct
   for (long long i = t0, k = k0; i < ncell; i += nth) {
     k = advance_pos(B.cell_pref, (int)k, i);
@@ -371,9 +396,19 @@ typedef void (*StageKernel)(BatchDev);
 template <int RC>
 static StageKernel pick_rs(int rs) {
   switch (rs) {
-    case RS_HLL: return k_batch_stage<RC, RS_HLL>;
-    case RS_HLLD: return k_batch_stage<RC, RS_HLLD>;
-    default: return k_batch_stage<RC, RS_LLF>;
+    case RS_HLL: return k_batch_face<RC, RS_HLL>;
+    case RS_HLLD: return k_batch_face<RC, RS_HLLD>;
+    default: return k_batch_face<RC, RS_LLF>;
+  }
+}
+// the second launch of a stage (edge, update, flag and correction phases)
+static StageKernel rest_kernel(int recon) {
+  switch (recon) {
+    case REC_PC: return k_batch_rest<REC_PC>;
+    case REC_PLM_MC: return k_batch_rest<REC_PLM_MC>;
+    case REC_PLM_MINMOD: return k_batch_rest<REC_PLM_MINMOD>;
+    case REC_PPM: return k_batch_rest<REC_PPM>;
+    default: return k_batch_rest<REC_PPM_EP>;
   }
 }
 static StageKernel stage_kernel(int recon, int rs) {
@@ -579,13 +614,19 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
                         cudaStream_t st) {
   const bool fofc = !(scheme & MHD_FOFC_OFF);
   const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf;
-  mhd::StageKernel k = mhd::stage_kernel(recon, rs);
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0);
+  mhd::StageKernel kf = mhd::stage_kernel(recon, rs), kr = mhd::rest_kernel(recon);
+  int per_sm = 0, per_sm_rest = 0;
+  int per_sm_fofc = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 128, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rest, kr, 128, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_fofc, (const void*)mhd::k_batch_fofc, 128, 0);
   if (e != cudaSuccess) return bcuda(b, e, "occupancy query");
-  if (per_sm < 1) return bfail(b, MHD_ERR_CUDA, "stage kernel cannot be resident");
+  if (per_sm < 1 || per_sm_rest < 1 || per_sm_fofc < 1)
+    return bfail(b, MHD_ERR_CUDA, "stage kernel cannot be resident");
   const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, per_sm) : per_sm;
-  const unsigned grid = (unsigned)(b->nsm * bps);
+  const unsigned grid_face = (unsigned)(b->nsm * bps), grid_rest = (unsigned)(b->nsm * per_sm_rest);
+  const unsigned grid_fofc = (unsigned)(b->nsm * per_sm_fofc);
   // counters 0..6 start each step at zero; counter 7 (a barrier gave up) is cleared only when
   // mhd_batch_last_dt or mhd_batch_stats reports it
   e = cudaMemsetAsync(b->counters, 0, 7 * sizeof(unsigned long long), st);
@@ -599,18 +640,21 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
   for (int stage = 0; stage < 2; ++stage) {
     mhd::BatchDev B = batch_dev(b, stage, fofc);
     void* args[] = {&B};
-    cudaLaunchConfig_t lc;
-    std::memset(&lc, 0, sizeof(lc));
-    lc.gridDim = dim3(grid);
-    lc.blockDim = dim3(128);
-    lc.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    e = cudaLaunchKernelExC(&lc, (const void*)k, args);
-    if (e != cudaSuccess) return bcuda(b, e, "cooperative stage launch");
+    for (int part = 0; part < (fofc ? 3 : 2); ++part) {
+      cudaLaunchConfig_t lc;
+      std::memset(&lc, 0, sizeof(lc));
+      lc.gridDim = dim3(part == 1 ? grid_rest : (part == 0 ? grid_face : grid_fofc));
+      lc.blockDim = dim3(128);
+      lc.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      lc.attrs = at;
+      lc.numAttrs = 1;
+      const void* k = part == 0 ? (const void*)kf : (part == 1 ? (const void*)kr : (const void*)mhd::k_batch_fofc);
+      e = cudaLaunchKernelExC(&lc, k, args);
+      if (e != cudaSuccess) return bcuda(b, e, "cooperative stage launch");
+    }
   }
   mhd::k_batch_copy_back<<<b->nsm * 8, 256, 0, st>>>(b->U1, s->cons, b->B1, s->b, b->ncell, b->counters + 7);
   e = cudaGetLastError();
