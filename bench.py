@@ -392,9 +392,8 @@ def _timed_steps(ctx, st, sch, eta, steps, stream, barrier, dist, dev, graph=Fal
 
 def run_c1(args, dev, stream, barrier, dist, world):
     """The 32^3 fast eigenmode along the box diagonal (rho0 = 1, p0 = 1/gamma, b0 oblique, amplitude
-    1e-6), PLM-MC + HLL + Q26 + LD04, CFL 0.3, 100 steps of mhd_step_cfl. At 32 K cells the library
-    runs the step as a batch of one patch (one persistent launch per stage); recorded in a CUDA
-    graph it takes the sweeps instead (the capture-safe path), which is timed beside it."""
+    1e-6), PLM-MC + HLL + Q26 + LD04, CFL 0.3, 100 steps of mhd_step_cfl, called eagerly and, timed
+    beside it, recorded once as a CUDA graph and replayed (no host launch cost)."""
     from paper_2609_10816_gb300 import inputs, mhd
 
     shape, steps = (32, 32, 32), 100
@@ -405,7 +404,7 @@ def run_c1(args, dev, stream, barrier, dist, world):
     for graph in (False, True):
         st = mhd.to_device(cons, b, dev)
         ms = _timed_steps(ctx, st, sch, 0.0, steps, stream, barrier, dist, dev, graph=graph)
-        out["c1_fast_wave_32cubed" + ("_sweeps_in_graph" if graph else "")] = whole_job_rate(32**3 * steps, world, ms)
+        out["c1_fast_wave_32cubed" + ("_in_graph" if graph else "")] = whole_job_rate(32**3 * steps, world, ms)
     md, mb = ctx.divb(st)
     ctx.close()
     r = out["c1_fast_wave_32cubed"] / world
@@ -659,8 +658,10 @@ def main():
     dom_ms, dom_launches = prof[dom]
     per_launch_s = dom_ms / 1e3 / dom_launches if dom_launches else float("nan")
     key = "turbulence"
+    # one face launch covers the x, y and z sweeps of a stage: 3 N faces
+    faces_per_launch = 3 * N
     if dom == "face":
-        flops_per_launch = FLOPS_PER_FACE[key] * N
+        flops_per_launch = FLOPS_PER_FACE[key] * faces_per_launch
     else:
         flops_per_launch = float("nan")
 
@@ -789,8 +790,9 @@ def main():
             "nominal_source": "152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (recipe SM count and maximum clock)",
             "algorithmic_flops_per_launch": flops_per_launch,
             "flops_per_unit": f"{FLOPS_PER_FACE[key]} per face (HLLD one-sided; {FLOPS_PER_FACE['turbulence_full_hlld']} "
-                              f"with both sides' star states), x {N} faces per launch",
-            "frac_full_hlld_count": (FLOPS_PER_FACE["turbulence_full_hlld"] * N / per_launch_s / 1e12
+                              f"with both sides' star states), x {faces_per_launch} faces per launch (the x, y "
+                              f"and z sweeps of one stage)",
+            "frac_full_hlld_count": (FLOPS_PER_FACE["turbulence_full_hlld"] * faces_per_launch / per_launch_s / 1e12
                                      / fp64_peak_tflops) if dom == "face" else None,
             "avg_launch_ms": per_launch_s * 1e3,
         },

@@ -104,14 +104,7 @@ mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double e
  * synchronisation (and a sequence of them can be recorded in a CUDA graph). cfl > 0 and eta >= 0
  * finite. Where mhd_max_dt would report MHD_ERR_NONFINITE, the step runs with dt = 0 (the state
  * is then unchanged wherever its fluxes are finite) and mhd_last_dt reports MHD_ERR_NONFINITE.
- * Asynchronous.
- * Small boxes (at most 64^3 cells, cubic cells, the Q26 EMF compute, the default validity criteria,
- * b0, b1, b2 contiguous in that order, profiling off and the stream not being captured) run as a
- * batch of one patch (see mhd_batch_step: persistent launches per stage, replayed as a CUDA
- * graph), with bitwise the same results: the sweeps cannot fill the GPU there. That path is taken
- * on the first call and whenever the state arrays, scheme, cfl and eta repeat the previous call's
- * (otherwise the sweeps run); it allocates its batch on first use and synchronises the stream when
- * it builds the batch's parameters and graph for new arguments. */
+ * Asynchronous. */
 mhd_status mhd_step_cfl(mhd_ctx *ctx, const mhd_state *state, double cfl, int scheme, double eta);
 
 /* The dt of the last mhd_step_cfl on this context (0 before any). Synchronous (reads two
@@ -130,9 +123,9 @@ mhd_status mhd_stats(mhd_ctx *ctx, long long *fofc_cells_stage1, long long *fofc
  * launches per stage). */
 enum {
   MHD_K_PRIM = 0,      /* cons -> prim */
-  MHD_K_FACE = 1,      /* reconstruction + Riemann sweeps, 3 launches per stage */
-  MHD_K_EDGE_BT = 2,   /* a-face quantities to edges along c, 3 launches per stage */
-  MHD_K_EDGE_LR = 3,   /* c-face quantities to edges along a + LD04 + eta j, 3 per stage */
+  MHD_K_FACE = 1,      /* reconstruction + Riemann sweeps, 1 launch per stage (all directions) */
+  MHD_K_EDGE_BT = 2,   /* a-face quantities to edges along c, 1 launch per stage (B25a: + 6) */
+  MHD_K_EDGE_LR = 3,   /* c-face quantities to edges along a + LD04 + eta j, 1 per stage */
   MHD_K_UPDATE = 4,    /* flux divergence and CT update */
   MHD_K_FLAG = 5,      /* validity flags */
   MHD_K_FOFC = 6,      /* first-order flux correction, 3 launches per stage (exit early if no flag) */

@@ -31,15 +31,6 @@ struct mhd_ctx {
   size_t ev_next;
   // adjoint scratch (allocated on the first mhd_step_adjoint call)
   double* adj;
-  // small boxes: mhd_step_cfl runs them as a batch of one patch (created on first use)
-  mhd_batch* small;
-  bool last_small;  // the last step went through `small` (its dt and flag counts are there)
-  // arguments of the previous mhd_step_cfl: the batch is used only when they repeat (it rebuilds
-  // its parameters and graph, with a synchronisation, whenever they change)
-  const double* prev_cons;
-  const double* prev_b0;
-  int prev_scheme;
-  double prev_cfl, prev_eta;
 };
 
 namespace {
@@ -117,12 +108,14 @@ void run_stage(mhd_ctx* c, const mhd::Dev& D, const Decoded& sc, PrimSource prim
     Timed t(c, MHD_K_PRIM, 1);
     mhd::launch_prim(D, st);
   }
-  for (int dir = 0; dir < 3; ++dir) {
-    Timed t(c, MHD_K_FACE, 1);
-    mhd::launch_face(D, dir, sc.recon, sc.rs, c->seg, st);
+  { Timed t(c, MHD_K_FACE, D.work ? 1 : 3); mhd::launch_faces(D, sc.recon, sc.rs, c->seg, st); }
+  {
+    // one launch per edge phase with work cursors (three without), B25a's six cell-to-face sweeps
+    const int n = D.work ? 1 : 3;
+    Timed t(c, MHD_K_EDGE_BT, sc.emf == mhd::EMF_B25A ? n + 6 : n);
+    mhd::launch_edges_bt(D, sc.recon, c->seg, st);
   }
-  { Timed t(c, MHD_K_EDGE_BT, sc.emf == mhd::EMF_B25A ? 9 : 3); mhd::launch_edges_bt(D, sc.recon, c->seg, st); }
-  { Timed t(c, MHD_K_EDGE_LR, 3); mhd::launch_edges_lr(D, sc.recon, c->seg, st); }
+  { Timed t(c, MHD_K_EDGE_LR, D.work ? 1 : 3); mhd::launch_edges_lr(D, sc.recon, c->seg, st); }
   { Timed t(c, MHD_K_UPDATE, 1); mhd::launch_update(D, st); }
   { Timed t(c, MHD_K_FLAG, 1); mhd::launch_flag(D, st); }
   if (sc.fofc) { Timed t(c, MHD_K_FOFC, 3); mhd::launch_fofc(D, st); }
@@ -177,12 +170,6 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   c->prof = false;
   c->ev_next = 0;
   c->adj = nullptr;
-  c->small = nullptr;
-  c->last_small = false;
-  c->prev_cons = nullptr;
-  c->prev_b0 = nullptr;
-  c->prev_scheme = -1;
-  c->prev_cfl = c->prev_eta = -1.0;
   mhd::Dev& D = c->base;
   std::memset(&D, 0, sizeof(D));
   D.n[0] = cfg->nx; D.n[1] = cfg->ny; D.n[2] = cfg->nz;
@@ -244,7 +231,6 @@ void mhd_destroy(mhd_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->adj) cudaFree(ctx->adj);
-  if (ctx->small) mhd_batch_destroy(ctx->small);
   cudaFree(ctx->scratch);
   delete ctx;
 }
@@ -284,7 +270,6 @@ static mhd_status advance(mhd_ctx* ctx, const mhd_state* state, mhd::Dev D, cons
                           bool prim_ready = false) {
   const long long N = D.N;
   mhd_status s;
-  ctx->last_small = false;
   D.eta = eta;
   D.resistive = eta != 0.0;
   D.emf = sc.emf;
@@ -343,25 +328,6 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
   return advance(ctx, state, D, sc, eta);
 }
 
-// Whether mhd_step_cfl runs this step as a batch of one patch: a box of at most
-// kSmallBoxCells cells (there the sweeps cannot fill the GPU, and one persistent launch per stage
-// with short segments is 2-3x faster at 32^3; from about 96^3 the sweeps are faster), with the
-// cubic cells, the EMF compute, the validity criteria and the contiguous face arrays the batched
-// step takes, and not while the stream is being captured (the batch synchronises when it builds its
-// parameters and graph); and only when the state arrays, scheme, cfl and eta repeat those of the
-// previous call or this is the first call (so alternating states or settings never rebuild the
-// batch's graph every step). The results are bitwise those of the sweeps.
-constexpr long long kSmallBoxCells = 64LL * 64 * 64;
-static bool small_box_route(mhd_ctx* ctx, const mhd_state* state, const Decoded& sc) {
-  const mhd::Dev& D = ctx->base;
-  if (D.N > kSmallBoxCells || ctx->prof || sc.emf != mhd::EMF_Q26 || sc.avg != 0) return false;
-  if (D.fofc_criteria != 3 || D.h[0] != D.h[1] || D.h[0] != D.h[2]) return false;
-  if (state->b1 != state->b0 + D.N || state->b2 != state->b1 + D.N) return false;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-  return true;
-}
-
 mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int scheme, double eta) {
   if (!ctx) return MHD_ERR_ARG;
   ctx->err.clear();
@@ -371,28 +337,6 @@ mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int sc
   Decoded sc;
   mhd_status s = decode(ctx, scheme, sc);
   if (s != MHD_OK) return s;
-  const bool repeat = ctx->prev_cons == nullptr ||
-                      (ctx->prev_cons == state->cons && ctx->prev_b0 == state->b0 && ctx->prev_scheme == scheme &&
-                       ctx->prev_cfl == cfl && ctx->prev_eta == eta);
-  ctx->prev_cons = state->cons;
-  ctx->prev_b0 = state->b0;
-  ctx->prev_scheme = scheme;
-  ctx->prev_cfl = cfl;
-  ctx->prev_eta = eta;
-  if (repeat && small_box_route(ctx, state, sc)) {
-    if (!ctx->small) {
-      const int dims[3] = {ctx->base.n[0], ctx->base.n[1], ctx->base.n[2]};
-      s = mhd_batch_create(dims, 1, ctx->base.h[0], ctx->base.gam, ctx->stream, &ctx->small);
-      if (s != MHD_OK) return fail(ctx, s, std::string("small-box batch: ") + mhd_batch_last_error(nullptr));
-      s = mhd_batch_set_schedule(ctx->small, 4, 0, 0, 1);
-      if (s != MHD_OK) return fail(ctx, s, std::string("small-box batch: ") + mhd_batch_last_error(ctx->small));
-    }
-    const mhd_batch_state bs = {state->cons, state->b0};
-    s = mhd_batch_step(ctx->small, &bs, cfl, scheme, eta);
-    if (s != MHD_OK) return fail(ctx, s, std::string("small-box batch: ") + mhd_batch_last_error(ctx->small));
-    ctx->last_small = true;
-    return MHD_OK;
-  }
   mhd::Dev D = ctx->base;
   cudaStream_t st = ctx->stream;
   s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, sizeof(unsigned long long), st), "cudaMemsetAsync");
@@ -415,11 +359,6 @@ mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt_out) {
   if (!ctx) return MHD_ERR_ARG;
   ctx->err.clear();
   if (!dt_out) return fail(ctx, MHD_ERR_ARG, "NULL argument");
-  if (ctx->last_small) {
-    const mhd_status s = mhd_batch_last_dt(ctx->small, dt_out);
-    if (s != MHD_OK) return fail(ctx, s, mhd_batch_last_error(ctx->small));
-    return MHD_OK;
-  }
   double h[5] = {0, 0, 0, 0, 0};
   mhd_status s = cuda_check(ctx, cudaMemcpyAsync(h, ctx->dtbuf, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream),
                             "cudaMemcpyAsync");
@@ -433,11 +372,6 @@ mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt_out) {
 
 mhd_status mhd_stats(mhd_ctx* ctx, long long* s1, long long* s2) {
   if (!ctx) return MHD_ERR_ARG;
-  if (ctx->last_small) {
-    const mhd_status s = mhd_batch_stats(ctx->small, s1, s2);
-    if (s != MHD_OK) return fail(ctx, s, mhd_batch_last_error(ctx->small));
-    return MHD_OK;
-  }
   unsigned long long h[2] = {0, 0};
   mhd_status s = cuda_check(ctx, cudaMemcpyAsync(h, ctx->base.counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream),
                             "cudaMemcpyAsync");
@@ -614,7 +548,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   };
   auto recompute = [&](const mhd::Dev& Ds) {  // P, alpha+-, u*, face and edge values of the stage input
     mhd::launch_prim(Ds, st);
-    for (int dir = 0; dir < 3; ++dir) mhd::launch_face(Ds, dir, sc.recon, sc.rs, ctx->seg, st);
+    mhd::launch_faces(Ds, sc.recon, sc.rs, ctx->seg, st);
     mhd::launch_edges_bt(Ds, sc.recon, ctx->seg, st);
     mhd::launch_edges_lr(Ds, sc.recon, ctx->seg, st);
   };

@@ -31,7 +31,8 @@ struct BatchDev {
   const Dev* patches;             // per-patch parameters of this stage, [npatch]
   const int* order;               // patch visited at schedule position k, [npatch]
   const long long* cell_pref;     // [npatch + 1] cells before schedule position k
-  const long long* sweep_pref;    // [3][npatch + 1] sweep segments along dir before position k
+  const long long* sweep_pref;    // [4][npatch + 1] sweep segments along dir (row 3: the edge sweeps'
+                                  // segments along x) before position k
   int npatch;
   int seg;
   int stage;
@@ -106,14 +107,17 @@ __device__ bool grid_sync(const BatchDev& B) {
 
 // One sweep phase: the sweeps along dirs[0..2] of every patch form one work list (sweep j's
 // segments after those of sweeps 0 .. j-1, patches in schedule order), taken 32 segments at a
-// time per warp from `cursor`; fn(D, j, line, m0, m1) runs each segment.
-template <class Fn>
+// time per warp from `cursor`; fn(D, j, line, m0, m1) runs each segment. In the edge phases
+// (EDGE) the lines along x are cut as the single-box edge sweeps cut them: short segments
+// numbered along the line, so that a warp walks whole lines (one thread per x-line would stream
+// a separate cache line per thread and array).
+template <bool EDGE = false, class Fn>
 __device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long long* cursor, const int* dirs, Fn fn) {
   const long long* pref[3];
   long long tot[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    pref[j] = B.sweep_pref + dirs[j] * (B.npatch + 1);
+    pref[j] = B.sweep_pref + ((EDGE && dirs[j] == 0) ? 3 : dirs[j]) * (B.npatch + 1);
     tot[j] = pref[j][B.npatch];
   }
   for_each_segment(cursor, tot[0] + tot[1] + tot[2], [&](long long t) {
@@ -128,9 +132,11 @@ __device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long lon
     }
     const int k = find_pos(pref[j], B.npatch, t);
     const Dev& D = B.patches[B.order[k]];
+    const bool xl = EDGE && dirs[j] == 0;
     Line ln;
     int m0, m1;
-    if (sweep_line_at(D, dirs[j], B.seg, t - pref[j][k], ln, m0, m1)) fn(D, j, ln, m0, m1);
+    if (sweep_line_at(D, dirs[j], xl ? edge_sweep_seg(D, 0, B.seg) : B.seg, t - pref[j][k], ln, m0, m1, xl))
+      fn(D, j, ln, m0, m1);
   });
 }
 
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(128, kRestMinBlocks) k_batch_rest(BatchDev B) 
   // a-face quantities to e-edges (lines along c = e + 2)
   {
     const int dirs[3] = {2, 0, 1};
-    sweep_phase(B, B.cursor + 1, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
+    sweep_phase<true>(B, B.cursor + 1, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
       edge_bt_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
     });
   }
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(128, kRestMinBlocks) k_batch_rest(BatchDev B) 
   // c-face quantities to e-edges (lines along a = e + 1) and the edge EMFs
   {
     const int dirs[3] = {1, 2, 0};
-    sweep_phase(B, B.cursor + 2, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
+    sweep_phase<true>(B, B.cursor + 2, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
       edge_lr_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
     });
   }
@@ -451,7 +457,7 @@ struct mhd_batch {
   mhd::Dev* pdev[2];              // per-patch parameters per stage
   int* order_dev;
   long long* cell_pref_dev;
-  long long* sweep_pref_dev;      // 3 * (npatch + 1)
+  long long* sweep_pref_dev;      // 4 * (npatch + 1)
   // schedule
   int seg, order_kind, blocks_per_sm, use_graph;
   long long spin_limit;
@@ -498,7 +504,7 @@ mhd_status upload_schedule(mhd_batch* b) {
       return b->off[x + 1] - b->off[x] > b->off[y + 1] - b->off[y];
     });
   }
-  std::vector<long long> cp(np + 1, 0), sp(3 * (np + 1), 0);
+  std::vector<long long> cp(np + 1, 0), sp(4 * (np + 1), 0);
   for (int k = 0; k < np; ++k) {
     const int p = order[k];
     const int* n = &b->dims[3 * p];
@@ -508,12 +514,15 @@ mhd_status upload_schedule(mhd_batch* b) {
       const long long segs = (n[d] + b->seg - 1) / b->seg;
       sp[d * (np + 1) + k + 1] = sp[d * (np + 1) + k] + (long long)n[t1] * n[t2] * segs;
     }
+    // the edge phases' segments along x: edge_sweep_seg's length, about nx / 32 points (4 to 16)
+    const int sx = std::min(16, std::max(4, (n[0] + 31) / 32));
+    sp[3 * (np + 1) + k + 1] = sp[3 * (np + 1) + k] + (long long)n[1] * n[2] * ((n[0] + sx - 1) / sx);
   }
   cudaError_t e = cudaMemcpyAsync(b->order_dev, order.data(), np * sizeof(int), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->cell_pref_dev, cp.data(), (np + 1) * sizeof(long long), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->sweep_pref_dev, sp.data(), 3 * (np + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(b->sweep_pref_dev, sp.data(), 4 * (np + 1) * sizeof(long long), cudaMemcpyHostToDevice,
                         b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return bcuda(b, e, "schedule upload");
@@ -715,7 +724,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->params_ok = false;
   const long long C = b->ncell;
   size_t bytes = (size_t)C * (5 + 3 + 47) * sizeof(double) + (size_t)C + 24 * 256 +
-                 2 * npatch * sizeof(mhd::Dev) + 3 * npatch * sizeof(int) + 4 * (npatch + 1) * sizeof(long long);
+                 2 * npatch * sizeof(mhd::Dev) + 3 * npatch * sizeof(int) + 5 * (npatch + 1) * sizeof(long long);
   cudaError_t e = cudaMalloc(&b->mem, bytes);
   if (e != cudaSuccess) {
     g_batch_create_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -738,7 +747,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->pdev[1] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
   b->order_dev = (int*)take(npatch * sizeof(int));
   b->cell_pref_dev = (long long*)take((npatch + 1) * sizeof(long long));
-  b->sweep_pref_dev = (long long*)take(3 * (npatch + 1) * sizeof(long long));
+  b->sweep_pref_dev = (long long*)take(4 * (npatch + 1) * sizeof(long long));
   b->flag = (unsigned char*)q;
   if ((size_t)(q - (char*)b->mem) + C > bytes) {  // layout check (padding consumed the slack)
     cudaFree(b->mem);

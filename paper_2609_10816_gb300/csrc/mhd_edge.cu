@@ -5,17 +5,10 @@
 
 namespace mhd {
 
+// one thread per segment (the form without work cursors: mhd_step_noalloc)
 template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_edge_bt(Dev D, int e, int seg) {
   const int dir = (e + 2) % 3;
-  if (D.work) {
-    for_each_segment(D.work + 3 + e, sweep_threads(D, dir, seg), [&](long long t) {
-      Line ln;
-      int m0, m1;
-      if (sweep_line_at(D, dir, seg, t, ln, m0, m1, dir == 0)) edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
-    });
-    return;
-  }
   Line ln;
   int m0, m1;
   if (!sweep_line(D, dir, seg, ln, m0, m1, dir == 0)) return;
@@ -34,54 +27,82 @@ __global__ void __launch_bounds__(128) k_b25_cell_to_face(Dev D, int e, int to_a
 template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_edge_lr(Dev D, int e, int seg) {
   const int dir = (e + 1) % 3;
-  if (D.work) {
-    for_each_segment(D.work + 6 + e, sweep_threads(D, dir, seg), [&](long long t) {
-      Line ln;
-      int m0, m1;
-      if (sweep_line_at(D, dir, seg, t, ln, m0, m1, dir == 0)) edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
-    });
-    return;
-  }
   Line ln;
   int m0, m1;
   if (!sweep_line(D, dir, seg, ln, m0, m1, dir == 0)) return;
   edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
 }
 
+// The three edge sweeps of one kind (LR: lines along a = e + 1, else along c = e + 2) as one
+// persistent launch: the segments of the e = 0, 1, 2 sweeps form one work list behind one cursor,
+// so that the grid drains one tail instead of three.
+template <int RC, int EMF, bool LR>
+__global__ void __launch_bounds__(128) k_edges(Dev D, int s0, int s1, int s2) {
+  const int sg[3] = {s0, s1, s2};
+  long long tot[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) tot[e] = sweep_threads(D, LR ? (e + 1) % 3 : (e + 2) % 3, sg[e]);
+  for_each_segment(D.work + (LR ? 6 : 3), tot[0] + tot[1] + tot[2], [&](long long t) {
+    int e = 0;
+    if (t >= tot[0]) {
+      t -= tot[0];
+      e = 1;
+      if (t >= tot[1]) {
+        t -= tot[1];
+        e = 2;
+      }
+    }
+    const int dir = LR ? (e + 1) % 3 : (e + 2) % 3;
+    Line ln;
+    int m0, m1;
+    if (sweep_line_at(D, dir, sg[e], t, ln, m0, m1, dir == 0)) {
+      if (LR) edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
+      else edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
+    }
+  });
+}
+
+template <int RC, int EMF, bool LR>
+static void launch_edges_t(const Dev& d, int seg, cudaStream_t st) {
+  const int bs = 128;
+  const long long res = resident_blocks((const void*)k_edges<RC, EMF, LR>, bs);
+  int sg[3];
+  long long tot = 0;
+  for (int e = 0; e < 3; ++e) {
+    const int dir = LR ? (e + 1) % 3 : (e + 2) % 3;
+    sg[e] = edge_sweep_seg(d, dir, seg);
+    if (dir != 0) sg[e] = fill_seg(d, dir, sg[e], res * bs);
+    tot += sweep_threads(d, dir, sg[e]);
+  }
+  const long long blocks = std::min((tot + bs - 1) / bs, res);
+  cudaMemsetAsync(d.work + (LR ? 6 : 3), 0, sizeof(unsigned long long), st);
+  k_edges<RC, EMF, LR><<<(unsigned)blocks, bs, 0, st>>>(d, sg[0], sg[1], sg[2]);
+}
+
 template <int RC, int EMF>
 static void launch_bt_t(const Dev& d, int seg, cudaStream_t st) {
+  if (d.work) {
+    launch_edges_t<RC, EMF, false>(d, seg, st);
+    return;
+  }
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int c = (e + 2) % 3;
-    int sg = edge_sweep_seg(d, c, seg);
-    long long blocks;
-    if (d.work) {
-      const long long res = resident_blocks((const void*)k_edge_bt<RC, EMF>, bs);
-      if (c != 0) sg = fill_seg(d, c, sg, res * bs);
-      blocks = std::min((sweep_threads(d, c, sg) + bs - 1) / bs, res);
-      cudaMemsetAsync(d.work + 3 + e, 0, sizeof(unsigned long long), st);
-    } else {
-      blocks = (sweep_threads(d, c, sg) + bs - 1) / bs;
-    }
-    k_edge_bt<RC, EMF><<<(unsigned)blocks, bs, 0, st>>>(d, e, sg);
+    const int sg = edge_sweep_seg(d, c, seg);
+    k_edge_bt<RC, EMF><<<(unsigned)((sweep_threads(d, c, sg) + bs - 1) / bs), bs, 0, st>>>(d, e, sg);
   }
 }
 template <int RC, int EMF>
 static void launch_lr_t(const Dev& d, int seg, cudaStream_t st) {
+  if (d.work) {
+    launch_edges_t<RC, EMF, true>(d, seg, st);
+    return;
+  }
   const int bs = 128;
   for (int e = 0; e < 3; ++e) {
     const int a = (e + 1) % 3;
-    int sg = edge_sweep_seg(d, a, seg);
-    long long blocks;
-    if (d.work) {
-      const long long res = resident_blocks((const void*)k_edge_lr<RC, EMF>, bs);
-      if (a != 0) sg = fill_seg(d, a, sg, res * bs);
-      blocks = std::min((sweep_threads(d, a, sg) + bs - 1) / bs, res);
-      cudaMemsetAsync(d.work + 6 + e, 0, sizeof(unsigned long long), st);
-    } else {
-      blocks = (sweep_threads(d, a, sg) + bs - 1) / bs;
-    }
-    k_edge_lr<RC, EMF><<<(unsigned)blocks, bs, 0, st>>>(d, e, sg);
+    const int sg = edge_sweep_seg(d, a, seg);
+    k_edge_lr<RC, EMF><<<(unsigned)((sweep_threads(d, a, sg) + bs - 1) / bs), bs, 0, st>>>(d, e, sg);
   }
 }
 template <int RC>

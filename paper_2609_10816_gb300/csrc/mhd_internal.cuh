@@ -105,6 +105,9 @@ void set_call_error(const char* msg);
 // launchers (each enqueues on `st`)
 void launch_prim(const Dev& d, cudaStream_t st);
 void launch_face(const Dev& d, int dir, int recon, int rs, int seg, cudaStream_t st);
+// the three face sweeps (one launch when d.work holds cursors, else one per direction); returns
+// the number of launches
+int launch_faces(const Dev& d, int recon, int rs, int seg, cudaStream_t st);
 void launch_edges_bt(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_edges_lr(const Dev& d, int recon, int seg, cudaStream_t st);
 void launch_update(const Dev& d, cudaStream_t st);
