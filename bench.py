@@ -42,9 +42,10 @@ FLOPS_PER_CELL_UPDATE = {"turbulence": 2746.0, "turbulence_full_hlld": 2852.6, "
                          "fast_wave": 2325.3, "harris": 2968.1}
 HBM_PEAK_GBS = 6759.6  # measured copy bandwidth of this GPU model (STREAM-style copy)
 ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B in + 64 B out
-# DRAM traffic of one face-sweep launch from an ncu capture (dram__bytes_read.sum +
+# DRAM traffic of one face-sweep launch (the x, y and z sweeps of a stage; mean of a stage-1 and a
+# stage-2 launch) from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 675.1e6, "cells": 160**3, "src": "b71c15425b46c7d1"}}
+TRAFFIC = {"face": {"bytes_per_launch": 2309.1e6, "cells": 160**3, "src": "43406666ee4fff87"}}
 
 
 # what the face sweep's machine code is compiled from: its kernel, the numerics and indexing
