@@ -104,7 +104,11 @@ mhd_status mhd_max_dt(mhd_ctx *ctx, const mhd_state *state, double cfl, double e
  * synchronisation (and a sequence of them can be recorded in a CUDA graph). cfl > 0 and eta >= 0
  * finite. Where mhd_max_dt would report MHD_ERR_NONFINITE, the step runs with dt = 0 (the state
  * is then unchanged wherever its fluxes are finite) and mhd_last_dt reports MHD_ERR_NONFINITE.
- * Asynchronous. */
+ * Asynchronous. On boxes of at most 128^3 cells, a call with the same state arrays, scheme, cfl
+ * and eta as the previous call (not while profiling, not while the stream is being captured)
+ * records the step's launches once as a CUDA graph on a private stream and replays it with one
+ * launch per call, for as long as the arguments repeat: the same kernels and results, without
+ * the host's launch cost. */
 mhd_status mhd_step_cfl(mhd_ctx *ctx, const mhd_state *state, double cfl, int scheme, double eta);
 
 /* The dt of the last mhd_step_cfl on this context (0 before any). Synchronous (reads two

@@ -31,6 +31,23 @@ struct mhd_ctx {
   size_t ev_next;
   // adjoint scratch (allocated on the first mhd_step_adjoint call)
   double* adj;
+  // mhd_step_cfl on small boxes: the launch sequence of a step recorded once as a CUDA graph (on
+  // the private stream `cap`) and replayed while the arguments repeat
+  struct StepKey {
+    const double *cons, *b0, *b1, *b2;
+    int scheme;
+    double cfl, eta;
+    bool operator==(const StepKey& o) const {
+      return cons == o.cons && b0 == o.b0 && b1 == o.b1 && b2 == o.b2 && scheme == o.scheme && cfl == o.cfl &&
+             eta == o.eta;
+    }
+  };
+  cudaStream_t cap;
+  cudaGraphExec_t graph;
+  bool graph_ok;
+  StepKey graph_key, prev_key;
+  bool prev_ok;
+  long long graph_launches[MHD_K_COUNT];
 };
 
 namespace {
@@ -165,6 +182,9 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   }
   mhd_ctx* c = new mhd_ctx();
   c->stream = (cudaStream_t)cuda_stream;
+  c->cap = nullptr;
+  c->graph_ok = false;
+  c->prev_ok = false;
   c->seg = 64;
   for (int k = 0; k < MHD_K_COUNT; ++k) c->launches[k] = 0;
   c->prof = false;
@@ -231,6 +251,8 @@ void mhd_destroy(mhd_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->adj) cudaFree(ctx->adj);
+  if (ctx->graph_ok) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
   cudaFree(ctx->scratch);
   delete ctx;
 }
@@ -328,18 +350,16 @@ mhd_status mhd_step(mhd_ctx* ctx, const mhd_state* state, double dt, int scheme,
   return advance(ctx, state, D, sc, eta);
 }
 
-mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int scheme, double eta) {
-  if (!ctx) return MHD_ERR_ARG;
-  ctx->err.clear();
-  if (!state_ok(state)) return fail(ctx, MHD_ERR_ARG, "state has a NULL array");
-  if (!(cfl > 0) || !(cfl < 1e300)) return fail(ctx, MHD_ERR_ARG, "cfl must be finite and > 0");
-  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
-  Decoded sc;
-  mhd_status s = decode(ctx, scheme, sc);
-  if (s != MHD_OK) return s;
+}  // extern "C"
+
+namespace {
+
+// the launches of one mhd_step_cfl on ctx->stream: CFL reduction, dt, both stages
+mhd_status enqueue_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, const Decoded& sc, double eta) {
   mhd::Dev D = ctx->base;
   cudaStream_t st = ctx->stream;
-  s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, sizeof(unsigned long long), st), "cudaMemsetAsync");
+  mhd_status s = cuda_check(ctx, cudaMemsetAsync(D.counters + 2, 0, sizeof(unsigned long long), st),
+                            "cudaMemsetAsync");
   if (s != MHD_OK) return s;
   mhd::Ptr3 B = {{state->b0, state->b1, state->b2}};
   const double hmin = std::fmin(D.h[0], std::fmin(D.h[1], D.h[2]));
@@ -353,6 +373,80 @@ mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int sc
   D.dt = 0.0;
   D.dthp = ctx->dtbuf + 1;
   return advance(ctx, state, D, sc, eta, true);
+}
+
+void drop_step_graph(mhd_ctx* ctx) {
+  if (ctx->graph_ok) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph_ok = false;
+}
+
+// Record one step's launches on the private stream as a graph (false, and nothing recorded, if
+// any part of it fails: the caller then runs the step eagerly).
+bool build_step_graph(mhd_ctx* ctx, const mhd_state* state, double cfl, const Decoded& sc, double eta,
+                      const mhd_ctx::StepKey& key) {
+  drop_step_graph(ctx);
+  if (!ctx->cap && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->cap = nullptr;
+    return false;
+  }
+  long long before[MHD_K_COUNT];
+  std::memcpy(before, ctx->launches, sizeof(before));
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+  mhd_status s = e == cudaSuccess ? enqueue_step_cfl(ctx, state, cfl, sc, eta) : MHD_ERR_CUDA;
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
+    if (e2 != cudaSuccess) s = MHD_ERR_CUDA;
+  }
+  ctx->stream = user;
+  // the launches one replay stands for; the recording itself launched nothing
+  for (int k = 0; k < MHD_K_COUNT; ++k) ctx->graph_launches[k] = ctx->launches[k] - before[k];
+  std::memcpy(ctx->launches, before, sizeof(before));
+  bool ok = s == MHD_OK && g && cudaGraphInstantiate(&ctx->graph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();  // a failed capture leaves nothing behind for the next launch to report
+  ctx->err.clear();
+  if (!ok) return false;
+  ctx->graph_ok = true;
+  ctx->graph_key = key;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Boxes of at most kGraphCells cells: the host's launch cost is a visible share of a step, so
+// when mhd_step_cfl is called again with the same arguments (state arrays, scheme, cfl, eta), not
+// while profiling or while the stream is being captured, the step's launch sequence is recorded
+// once as a CUDA graph and replayed by one launch per call (the same kernels, parameters and
+// results).
+constexpr long long kGraphCells = 128LL * 128 * 128;
+
+mhd_status mhd_step_cfl(mhd_ctx* ctx, const mhd_state* state, double cfl, int scheme, double eta) {
+  if (!ctx) return MHD_ERR_ARG;
+  ctx->err.clear();
+  if (!state_ok(state)) return fail(ctx, MHD_ERR_ARG, "state has a NULL array");
+  if (!(cfl > 0) || !(cfl < 1e300)) return fail(ctx, MHD_ERR_ARG, "cfl must be finite and > 0");
+  if (!(eta >= 0) || !(eta < 1e300)) return fail(ctx, MHD_ERR_ARG, "eta must be finite and >= 0");
+  Decoded sc;
+  mhd_status s = decode(ctx, scheme, sc);
+  if (s != MHD_OK) return s;
+  const mhd_ctx::StepKey key = {state->cons, state->b0, state->b1, state->b2, scheme, cfl, eta};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+  if (ctx->base.N <= kGraphCells && !ctx->prof && !capturing) {
+    const bool repeat = (ctx->graph_ok && ctx->graph_key == key) || (ctx->prev_ok && ctx->prev_key == key);
+    ctx->prev_key = key;
+    ctx->prev_ok = true;
+    if (repeat && ((ctx->graph_ok && ctx->graph_key == key) || build_step_graph(ctx, state, cfl, sc, eta, key))) {
+      for (int k = 0; k < MHD_K_COUNT; ++k) ctx->launches[k] += ctx->graph_launches[k];
+      return cuda_check(ctx, cudaGraphLaunch(ctx->graph, ctx->stream), "cudaGraphLaunch");
+    }
+  }
+  return enqueue_step_cfl(ctx, state, cfl, sc, eta);
 }
 
 mhd_status mhd_last_dt(mhd_ctx* ctx, double* dt_out) {

@@ -216,6 +216,28 @@ def test_step_cfl_equals_max_dt_and_step(gpu_lib, case):
     assert_parity(st.cons.cpu().numpy(), st.b.cpu().numpy(), co, bo, what=f"step_cfl {case}")
 
 
+def test_step_cfl_replays_its_own_graph(gpu_lib):
+    """Repeated mhd_step_cfl calls on a small box replay a recorded graph (profiling off): state, dt
+    and flag counts equal bitwise those of the eager steps (profiling on forces them), also when
+    cfl changes between calls (a new recording) and around a call with other arrays."""
+    shape = (18, 14, 10)
+    h = (0.05, 0.05, 0.05)
+    cons, b, _ = inputs.random_smooth(shape, seed=23, rough=0.05, h=h)
+    sch = mhd.scheme("ppm", "hlld", "q26")
+    eager, graphed = mhd.Context(shape, h), mhd.Context(shape, h)
+    eager.profile(True)
+    st_e, st_g, other = mhd.to_device(cons, b), mhd.to_device(cons, b), mhd.to_device(cons, b)
+    cfls = [0.3, 0.3, 0.3, 0.3, 0.25, 0.25, 0.25, 0.3, 0.3]
+    for k, cfl in enumerate(cfls):
+        if k == 6:
+            graphed.step_cfl(other, cfl, sch)  # other arrays in between (st_g's recording stays valid)
+        eager.step_cfl(st_e, cfl, sch)
+        graphed.step_cfl(st_g, cfl, sch)
+        assert eager.last_dt() == graphed.last_dt() and eager.stats() == graphed.stats(), k
+        torch.cuda.synchronize()
+        assert torch.equal(st_e.cons, st_g.cons) and torch.equal(st_e.b, st_g.b), k
+
+
 def test_step_cfl_sequence_in_a_cuda_graph(gpu_lib):
     """Four step_cfl calls recorded in one CUDA graph replay to the eager result bit for bit (the
     step needs no host round trip, so a sequence of steps can run as one graph launch)."""
