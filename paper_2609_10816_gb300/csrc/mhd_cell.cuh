@@ -50,8 +50,8 @@ __device__ __forceinline__ void prim_of(const Dev& D, const double* U, const dou
 // With S = a^2 + b^2/rho, every fast speed lies between sqrt(max(a^2, b^2/rho)) and sqrt(S) (the
 // discriminant (a^2 + b^2/rho)^2 - 4 a^2 b_d^2/rho is (a^2 - b^2/rho)^2 + 4 a^2 (b^2 - b_d^2)/rho),
 // so the three fast speeds are evaluated only when the upper bound, widened by 1e-12 against
-// rounding, reaches m: the running maximum is the same value, with two square roots for most
-// cells instead of six. A non-finite speed gives +inf.
+// rounding, reaches m: the running maximum is the same value, with no square root for most cells
+// of a cubic grid (one otherwise) instead of six. A non-finite speed gives +inf.
 __device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, const double* const* B, long long X,
                                                 double m, double* Pout = nullptr) {
   double w[8];
@@ -65,17 +65,27 @@ __device__ __forceinline__ double cfl_speed_max(const Dev& D, const double* U, c
 #pragma unroll
   for (int v = 0; v < 8; ++v) ok = ok && finite_d(w[v]);
   if (!ok) return __longlong_as_double(0x7ff0000000000000LL);
-  const double hmin = fmin(D.h[0], fmin(D.h[1], D.h[2]));
+  const double hmin = pmin(D.h[0], pmin(D.h[1], D.h[2]));  // h_d > 0: bit patterns order them
   const double rinv = rcp(w[0]);
   const double a2 = D.gam * w[4] * rinv;
   const double b2 = fma(w[5], w[5], fma(w[6], w[6], w[7] * w[7]));
   const double sum = fma(b2, rinv, a2);
-  const double cu = sqrt_(sum);
-  double hi = 0.0;
+  if (dbits(D.h[0]) == dbits(D.h[1]) && dbits(D.h[0]) == dbits(D.h[2])) {
+    // cubic cells (hmin / h_d is 1 up to an ulp): every speed is at most umax + sqrt(S) when
+    // p >= 0 and rho > 0, and umax + sqrt(S) < m (1 - 1e-12) is tested on squares, without the
+    // square root, S widened by 1e-12 against the rounding of the squares and the scale
+    const double umax = pmax(vabs(w[1]), pmax(vabs(w[2]), vabs(w[3])));
+    const double t = fma(m, -1e-12, m) - umax;
+    if (gt0(t) && gt0(w[0]) && ge0(w[4]) && finite_d(sum) && dbits(sum * (1.0 + 1e-12)) < dbits(t * t))
+      return m;
+  } else {
+    const double cu = sqrt_(sum);
+    double hi = 0.0;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) hi = pmax(hi, (vabs(w[1 + d]) + cu) * (hmin * D.hinv[d]));
-  hi *= 1.0 + 1e-12;
-  if (finite_d(hi) && dbits(hi) < dbits(m)) return m;
+    for (int d = 0; d < 3; ++d) hi = pmax(hi, (vabs(w[1 + d]) + cu) * (hmin * D.hinv[d]));
+    hi *= 1.0 + 1e-12;
+    if (finite_d(hi) && dbits(hi) < dbits(m)) return m;
+  }
   double s = 0.0;
   for (int d = 0; d < 3; ++d) {
     const double bn2 = w[5 + d] * w[5 + d];

@@ -157,6 +157,39 @@ def test_max_dt_and_divb(gpu_lib):
     assert abs(md - mdo) <= 1e-12 * mbo / min(info["h"])
 
 
+@pytest.mark.parametrize("case", ["turbulence", "bulk_flow", "fast_cell_last", "non_cubic"])
+def test_max_dt_early_exit_cases(gpu_lib, case):
+    """The CFL reduction's per-cell early exit (a bound on squares for cubic cells) never drops the
+    cell that sets dt: Mach-5 turbulence, a smooth state carried by a bulk flow far faster than its
+    sound and Alfven speeds, one fast cell at the end of the cell order, non-cubic cells; dt equals
+    the oracle's to 1e-14."""
+    if case == "turbulence":
+        shape = (24, 24, 24)
+        cons, b, info = inputs.turbulence(shape)
+    else:
+        shape = (24, 20, 16)
+        h = (0.05, 0.04, 0.03) if case == "non_cubic" else (0.05, 0.05, 0.05)
+        cons, b, info = inputs.random_smooth(shape, seed=29, rough=0.05, h=h)
+    cons = cons.copy()
+    if case == "bulk_flow":  # u_x += 1e3 (kinetic energy added accordingly)
+        rho = cons[0]
+        mx = cons[1] + 1e3 * rho
+        cons[4] = cons[4] + 0.5 * (mx**2 - cons[1] ** 2) / rho
+        cons[1] = mx
+    if case == "fast_cell_last":  # the last cell in memory order moves at 30x the others
+        rho = cons[0, -1, -1, -1]
+        mz = cons[3, -1, -1, -1] + 30.0 * rho
+        cons[4, -1, -1, -1] += 0.5 * (mz**2 - cons[3, -1, -1, -1] ** 2) / rho
+        cons[3, -1, -1, -1] = mz
+    cfg = oracle.Config(shape=shape, h=info["h"])
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    ref = oracle.max_dt(cfg, cons, b, 0.3)
+    assert abs(ctx.max_dt(st, 0.3) - ref) <= 1e-14 * ref
+    ctx.step_cfl(st, 0.3, mhd.scheme("plm_mc", "hll", "q26"))
+    assert abs(ctx.last_dt() - ref) <= 1e-14 * ref
+
+
 def test_step_with_device_cfl_equals_host_cfl(gpu_lib):
     """step_cfl (CFL reduction, dt and dt/h kept on the device) gives bit for bit the state and the
     dt of max_dt + step, over several steps, ideal and resistive; and the oracle's step agrees."""
