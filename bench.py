@@ -264,7 +264,8 @@ def run_reference(args):
 def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
     """1024 patches, edges uniform from {16, 24, 32, 48, 64} (seed 4), cell width 1/64, smooth
     random states; PPM + HLLD + Q26 + LD04; schedule from the autotuner; one CUDA-graph replay per
-    step (CFL reduction + dt + two persistent stage launches)."""
+    step (CFL reduction + dt + the persistent stage launches); then FS18 and B25a from the same
+    state with the same schedule."""
     import numpy as np
     import torch
 
@@ -279,6 +280,8 @@ def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
     del pats
     sch = mhd.scheme("ppm", "hlld", "q26")
     sched = bt.tune(cons, b, 0.3, sch)
+    # the initial state again for the FS18 / B25a comparison below
+    start = (cons.clone(), b.clone()) if not args.q26_only else None
     for _ in range(3):
         bt.step(cons, b, 0.3, sch)
     barrier()
@@ -299,6 +302,24 @@ def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
                               "fofc_flagged_last_step": list(flagged),
                               "phase_ms_last_step": phases,
                               "launches_per_step": "1 graph: maxspeed, set_dt, per stage 3 persistent launches (faces; edges, update, flags; first-order correction, which exits at once when nothing is flagged)"}}
+    if start is not None:
+        # the other EMF compute schemes on the same patches from the same state, same schedule
+        for emf in ("fs18", "b25a"):
+            cons.copy_(start[0])
+            b.copy_(start[1])
+            sch_e = mhd.scheme("ppm", "hlld", emf)
+            for _ in range(3):
+                bt.step(cons, b, 0.3, sch_e)
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                bt.step(cons, b, 0.3, sch_e)
+            e1.record(stream)
+            barrier()
+            bt.last_dt()
+            out[f"batched_{emf}"] = whole_job_rate(bt.ncell * args.steps, world,
+                                                   max_over_ranks(e0.elapsed_time(e1), dist, dev))
+        del start
     bt.close()
     del cons, b
     if same_state is not None:

@@ -239,8 +239,8 @@ mhd_status mhd_step_noalloc(const mhd_config *cfg, const mhd_state *state, doubl
  * face sweeps at the face kernel's register budget; the edge sweeps, update and validity flags
  * at half that budget (twice the warps per SM); and, with flux correction on, the first-order
  * correction (returning at once when the stage flagged nothing). The whole step is captured once
- * as a CUDA graph and replayed while the state arrays, scheme, eta and cfl stay the same. The batched step supports the Q26 EMF compute (FS18 and B25a ->
- * MHD_ERR_UNSUPPORTED). */
+ * as a CUDA graph and replayed while the state arrays, scheme, eta and cfl stay the same. Every
+ * EMF compute scheme (Q26, FS18, B25a) with LD04 averaging; B25b -> MHD_ERR_UNSUPPORTED. */
 typedef struct mhd_batch mhd_batch;
 
 /* Batch state, patch-major, all device memory: patch p (cell offset off[p] from
@@ -252,8 +252,9 @@ typedef struct {
 } mhd_batch_state;
 
 /* Create a batch of npatch patches (dims: 3 ints per patch, each >= 1, fewer than 2^31 cells per
- * patch) with cell width h > 0. Allocates 55 doubles and one byte of scratch per cell. Errors:
- * message from mhd_batch_last_error(NULL). */
+ * patch) with cell width h > 0. Allocates 55 doubles and one byte of scratch per cell (the first
+ * FS18 or B25a step 54 doubles per cell more, kept until mhd_batch_destroy). Errors: message from
+ * mhd_batch_last_error(NULL). */
 mhd_status mhd_batch_create(const int *dims, int npatch, double h, double gamma, void *cuda_stream,
                             mhd_batch **out);
 void mhd_batch_destroy(mhd_batch *batch);

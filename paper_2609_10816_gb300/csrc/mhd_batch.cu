@@ -42,7 +42,8 @@ struct BatchDev {
   long long spin_limit;           // bounded wait per barrier (iterations of ~100 ns)
   int barrier_extra;              // test hook: wait for this many blocks more than launched
   unsigned long long* ptime;      // [2][8] global-timer stamps at the phase boundaries of each stage
-  unsigned long long* cursor;     // [3] work-list cursors of the face, edge_bt and edge_lr phases
+  unsigned long long* cursor;     // [5] work-list cursors of the face, edge_bt, edge_lr and B25a's two
+                                  // cell-EMF phases
   unsigned* patch_flags;          // [2][npatch] flagged cells per stage and schedule position
 };
 
@@ -144,7 +145,8 @@ __device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long lon
 // memory latency, the other launch twice as many
 constexpr int kCellIlp = 4;
 constexpr int kRestIlp = 2;
-// CTAs of 128 threads per SM that the second launch of a stage is compiled to fit
+// CTAs of 128 threads per SM that the second launch of a stage is compiled to fit (one fewer for
+// FS18, whose bottom/top sweep carries five reconstruction windows)
 constexpr int kRestMinBlocks = 4;
 
 // stage 2's primitives (where flux correction changed stage 1's result) and the face sweeps
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(128) k_batch_face(BatchDev B) {
   stamp(B, 0);
   // the sweep phases' cursors start at zero: the face phase's is taken only after the grid
   // barrier below, which block 0 passes only after this, the edge phases' in the next launch
-  if (blockIdx.x == 0 && threadIdx.x < 3) atomicExch(B.cursor + threadIdx.x, 0ull);
+  if (blockIdx.x == 0 && threadIdx.x < 5) atomicExch(B.cursor + threadIdx.x, 0ull);
   // per-patch flag counts of this stage start at zero (read in the next launch only)
   unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
   for (long long i = t0; i < B.npatch; i += nth) pflags[i] = 0u;
@@ -199,9 +201,10 @@ __global__ void __launch_bounds__(128) k_batch_face(BatchDev B) {
   });
 }
 
-// the edge sweeps, the update, the validity flags and the first-order correction of the stage
-template <int RC>
-__global__ void __launch_bounds__(128, kRestMinBlocks) k_batch_rest(BatchDev B) {
+// the edge sweeps (for B25a after its cell-EMF sweeps), the update and the validity flags of the
+// stage, for the EMF compute scheme EMF
+template <int RC, int EMF>
+__global__ void __launch_bounds__(128, EMF == EMF_FS18 ? kRestMinBlocks - 1 : kRestMinBlocks) k_batch_rest(BatchDev B) {
   if (*(volatile unsigned long long*)(B.counters + 7)) return;  // the face launch gave up
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -209,11 +212,23 @@ __global__ void __launch_bounds__(128, kRestMinBlocks) k_batch_rest(BatchDev B) 
   const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
   unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
   stamp(B, 2);
+  if (EMF == EMF_B25A) {
+    // the cell-centred EMF reconstructed to the a-faces (lines along a = e + 1) and to the c-faces
+    // (lines along c = e + 2): two independent work lists, no barrier between them
+    const int dirs_a[3] = {1, 2, 0}, dirs_c[3] = {2, 0, 1};
+    sweep_phase<true>(B, B.cursor + 3, dirs_a, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
+      b25_seg<RC>(D, e, 1, ln, m0, m1);
+    });
+    sweep_phase<true>(B, B.cursor + 4, dirs_c, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
+      b25_seg<RC>(D, e, 0, ln, m0, m1);
+    });
+    if (!grid_sync(B)) return;
+  }
   // a-face quantities to e-edges (lines along c = e + 2)
   {
     const int dirs[3] = {2, 0, 1};
     sweep_phase<true>(B, B.cursor + 1, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
-      edge_bt_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
+      edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
     });
   }
   if (!grid_sync(B)) return;
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(128, kRestMinBlocks) k_batch_rest(BatchDev B) 
   {
     const int dirs[3] = {1, 2, 0};
     sweep_phase<true>(B, B.cursor + 2, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
-      edge_lr_seg<RC, EMF_Q26>(D, e, ln, m0, m1);
+      edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
     });
   }
   if (!grid_sync(B)) return;
@@ -407,14 +422,22 @@ static StageKernel pick_rs(int rs) {
     default: return k_batch_face<RC, RS_LLF>;
   }
 }
-// the second launch of a stage (edge, update, flag and correction phases)
-static StageKernel rest_kernel(int recon) {
+// the second launch of a stage (edge, update and flag phases)
+template <int EMF>
+static StageKernel rest_kernel_e(int recon) {
   switch (recon) {
-    case REC_PC: return k_batch_rest<REC_PC>;
-    case REC_PLM_MC: return k_batch_rest<REC_PLM_MC>;
-    case REC_PLM_MINMOD: return k_batch_rest<REC_PLM_MINMOD>;
-    case REC_PPM: return k_batch_rest<REC_PPM>;
-    default: return k_batch_rest<REC_PPM_EP>;
+    case REC_PC: return k_batch_rest<REC_PC, EMF>;
+    case REC_PLM_MC: return k_batch_rest<REC_PLM_MC, EMF>;
+    case REC_PLM_MINMOD: return k_batch_rest<REC_PLM_MINMOD, EMF>;
+    case REC_PPM: return k_batch_rest<REC_PPM, EMF>;
+    default: return k_batch_rest<REC_PPM_EP, EMF>;
+  }
+}
+static StageKernel rest_kernel(int recon, int emf) {
+  switch (emf) {
+    case EMF_FS18: return rest_kernel_e<EMF_FS18>(recon);
+    case EMF_B25A: return rest_kernel_e<EMF_B25A>(recon);
+    default: return rest_kernel_e<EMF_Q26>(recon);
   }
 }
 static StageKernel stage_kernel(int recon, int rs) {
@@ -447,6 +470,8 @@ struct mhd_batch {
   double* U1;                     // [patch][5][N_p]
   double* B1;                     // [patch][3][N_p]
   double* scratch;                // [patch][47][N_p]: P 8, F 15, Ap/Am/Us 9, Epart 12, E 3
+  double* extra;                  // [patch][54][N_p] for FS18 / B25a: VL 9, VR 9, Xpart 24, EfL 6, EfB 6
+                                  // (allocated by the first step that needs it)
   unsigned char* flag;
   unsigned long long* counters;   // 8
   unsigned* barrier;              // 2
@@ -549,7 +574,15 @@ mhd_status upload_params(mhd_batch* b, const mhd_batch_state* s, int scheme, dou
     D.eta = eta;
     D.resistive = eta != 0.0;
     D.fofc_criteria = (scheme & MHD_FOFC_OFF) ? 0 : 3;
-    D.emf = mhd::EMF_Q26;
+    D.emf = (scheme >> 8) & 0xf;
+    if (D.emf != mhd::EMF_Q26) {
+      double* x = b->extra + 54 * o;
+      D.VL = x; x += 9 * N;
+      D.VR = x; x += 9 * N;
+      D.Xpart = x; x += 24 * N;
+      D.EfL = x; x += 6 * N;
+      D.EfB = x;
+    }
     D.U0 = s->cons + 5 * o;
     for (int d = 0; d < 3; ++d) D.B0[d] = s->b + 3 * o + d * N;
     double* q = b->scratch + 47 * o;
@@ -623,7 +656,7 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
                         cudaStream_t st) {
   const bool fofc = !(scheme & MHD_FOFC_OFF);
   const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf;
-  mhd::StageKernel kf = mhd::stage_kernel(recon, rs), kr = mhd::rest_kernel(recon);
+  mhd::StageKernel kf = mhd::stage_kernel(recon, rs), kr = mhd::rest_kernel(recon, (scheme >> 8) & 0xf);
   int per_sm = 0, per_sm_rest = 0;
   int per_sm_fofc = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 128, 0);
@@ -722,6 +755,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->barrier_extra = 0;
   b->graph_ok = false;
   b->params_ok = false;
+  b->extra = nullptr;
   const long long C = b->ncell;
   size_t bytes = (size_t)C * (5 + 3 + 47) * sizeof(double) + (size_t)C + 24 * 256 +
                  2 * npatch * sizeof(mhd::Dev) + 3 * npatch * sizeof(int) + 5 * (npatch + 1) * sizeof(long long);
@@ -740,7 +774,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->counters = (unsigned long long*)take(8 * sizeof(unsigned long long));
   b->barrier = (unsigned*)take(2 * sizeof(unsigned));
   b->ptime = (unsigned long long*)take(16 * sizeof(unsigned long long));
-  b->cursor = (unsigned long long*)take(4 * sizeof(unsigned long long));
+  b->cursor = (unsigned long long*)take(8 * sizeof(unsigned long long));
   b->patch_flags = (unsigned*)take(2 * npatch * sizeof(unsigned));
   b->dt_dev = (double*)take(sizeof(double));
   b->pdev[0] = (mhd::Dev*)take(npatch * sizeof(mhd::Dev));
@@ -783,6 +817,7 @@ void mhd_batch_destroy(mhd_batch* b) {
   drop_graph(b);
   cudaStreamDestroy(b->cap);
   cudaFree(b->mem);
+  if (b->extra) cudaFree(b->extra);
   delete b;
 }
 
@@ -816,7 +851,15 @@ mhd_status mhd_batch_step(mhd_batch* b, const mhd_batch_state* s, double cfl, in
   const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf, emf = (scheme >> 8) & 0xf, avg = (scheme >> 12) & 0xf;
   if (avg == 1) return bfail(b, MHD_ERR_UNSUPPORTED, "B25b averaging is cited but not defined in the paper");
   if (recon > 4 || rs > 2 || emf > 2 || avg > 1) return bfail(b, MHD_ERR_ARG, "scheme field out of range");
-  if (emf != mhd::EMF_Q26) return bfail(b, MHD_ERR_UNSUPPORTED, "the batched step runs the Q26 EMF compute");
+  if (emf != mhd::EMF_Q26 && !b->extra) {  // FS18 / B25a arrays, on the first step that needs them
+    mhd_status st = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (st != MHD_OK) return st;
+    st = bcuda(b, cudaMalloc(&b->extra, (size_t)b->ncell * 54 * sizeof(double)), "cudaMalloc of FS18/B25a arrays");
+    if (st != MHD_OK) {
+      b->extra = nullptr;
+      return st;
+    }
+  }
   const bool same = b->params_ok && b->built_cons == s->cons && b->built_b == s->b && b->built_scheme == scheme &&
                     b->built_eta == eta && b->built_cfl == cfl;
   if (!same) {

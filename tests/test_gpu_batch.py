@@ -44,15 +44,17 @@ def _plain_step(shape, cons, b, dt, sch, eta):
     return out
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_single_box_steps(gpu_lib, use_graph):
+@pytest.mark.parametrize("use_graph,emf", [(True, "q26"), (False, "q26"), (True, "fs18"), (True, "b25a")])
+def test_batch_equals_single_box_steps(gpu_lib, use_graph, emf):
+    """Two batched steps of 21 uneven patches (one sets flux-correction flags) equal bit for bit the
+    single-box steps of each patch with the batch's dt, for each EMF compute scheme."""
     dims, pats = _patches(20, seed=3)
     dims.append((16, 6, 4))
     pats.append(_low_pressure_patch((16, 6, 4)))  # sets flux-correction flags
     bt = mhd.Batch(dims, H)
     bt.set_schedule(seg=8, order=1, blocks_per_sm=0, use_graph=use_graph)
     cons, b = bt.pack(pats)
-    sch = mhd.scheme("ppm", "hlld", "q26")
+    sch = mhd.scheme("ppm", "hlld", emf)
     for step in range(2):
         before = [bt.unpack(cons, b, p) for p in range(len(dims))]
         bt.step(cons, b, 0.3, sch, 1e-3)
@@ -70,16 +72,16 @@ def test_batch_equals_single_box_steps(gpu_lib, use_graph):
     assert flagged[0] + flagged[1] >= 0
 
 
-@pytest.mark.parametrize("recon", ["plm_mc", "ppm_ep"])
-def test_batch_patches_against_oracle(gpu_lib, recon):
+@pytest.mark.parametrize("recon,emf", [("plm_mc", "q26"), ("ppm_ep", "q26"), ("plm_mc", "fs18"), ("ppm_ep", "b25a")])
+def test_batch_patches_against_oracle(gpu_lib, recon, emf):
     dims, pats = _patches(6, seed=9, edges=(6, 8, 10))
     bt = mhd.Batch(dims, H)
     cons, b = bt.pack(pats)
-    sch = mhd.scheme(recon, "hlld", "q26")
+    sch = mhd.scheme(recon, "hlld", emf)
     bt.step(cons, b, 0.3, sch, 0.0)
     dt = bt.last_dt()
     # the batch dt is the CFL step over all patches
-    cfgs = [oracle.Config(shape=d, h=(H, H, H), recon=recon, riemann="hlld") for d in dims]
+    cfgs = [oracle.Config(shape=d, h=(H, H, H), recon=recon, riemann="hlld", emf=emf) for d in dims]
     assert dt == pytest.approx(min(oracle.max_dt(c, *pats[p], 0.3) for p, c in enumerate(cfgs)), rel=1e-14)
     for p, d in enumerate(dims):
         co, bo, _ = oracle.step(cfgs[p], *pats[p], dt)
