@@ -280,46 +280,49 @@ def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
     del pats
     sch = mhd.scheme("ppm", "hlld", "q26")
     sched = bt.tune(cons, b, 0.3, sch)
-    # the initial state again for the FS18 / B25a comparison below
-    start = (cons.clone(), b.clone()) if not args.q26_only else None
-    for _ in range(3):
-        bt.step(cons, b, 0.3, sch)
-    barrier()
+    # the initial state again for the comparisons below (the other launch form; FS18 / B25a)
+    start = (cons.clone(), b.clone())
+
+    def timed(scheme):
+        for _ in range(3):
+            bt.step(cons, b, 0.3, scheme)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            bt.step(cons, b, 0.3, scheme)
+        e1.record(stream)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev)
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        bt.step(cons, b, 0.3, sch)
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1)
+    ms = timed(sch)
     dt = bt.last_dt()  # also raises on a barrier timeout
     flagged = bt.stats()
     phases = {f"stage{st + 1}": {k: round(v, 3) for k, v in ph.items()} for st, ph in bt.phase_ms().items()}
-    ms = max_over_ranks(ms, dist, dev)
+    nl = sched["launches_per_stage"]
+    form = {1: "one persistent launch per stage", 3: "per stage 3 persistent launches (faces; edges, update, "
+            "flags; first-order correction, which exits at once when nothing is flagged)"}
     out = {"batched": whole_job_rate(bt.ncell * args.steps, world, ms),
            "batched_config": {"patches": len(dims), "cells_per_gpu": bt.ncell, "schedule": sched,
                               "ms_per_step": ms / args.steps, "last_dt": dt,
                               "fofc_flagged_last_step": list(flagged),
                               "phase_ms_last_step": phases,
-                              "launches_per_step": "1 graph: maxspeed, set_dt, per stage 3 persistent launches (faces; edges, update, flags; first-order correction, which exits at once when nothing is flagged)"}}
-    if start is not None:
+                              "launches_per_step": f"1 graph: maxspeed, set_dt, {form[nl]}"}}
+    # the launch form the tuner did not pick, same schedule otherwise
+    cons.copy_(start[0])
+    b.copy_(start[1])
+    bt.set_launches(4 - nl)
+    out[f"batched_{4 - nl}_launches_per_stage"] = whole_job_rate(bt.ncell * args.steps, world, timed(sch))
+    bt.set_launches(nl)
+    if not args.q26_only:
         # the other EMF compute schemes on the same patches from the same state, same schedule
         for emf in ("fs18", "b25a"):
             cons.copy_(start[0])
             b.copy_(start[1])
-            sch_e = mhd.scheme("ppm", "hlld", emf)
-            for _ in range(3):
-                bt.step(cons, b, 0.3, sch_e)
-            barrier()
-            e0.record(stream)
-            for _ in range(args.steps):
-                bt.step(cons, b, 0.3, sch_e)
-            e1.record(stream)
-            barrier()
+            ms_e = timed(mhd.scheme("ppm", "hlld", emf))
             bt.last_dt()
-            out[f"batched_{emf}"] = whole_job_rate(bt.ncell * args.steps, world,
-                                                   max_over_ranks(e0.elapsed_time(e1), dist, dev))
-        del start
+            out[f"batched_{emf}"] = whole_job_rate(bt.ncell * args.steps, world, ms_e)
+    del start
     bt.close()
     del cons, b
     if same_state is not None:
@@ -330,19 +333,18 @@ def run_batched(args, dev, stream, barrier, dist, world, same_state=None):
         bt = mhd.Batch([(n0, n0, n0)], h0, stream=stream)
         cons, b = bt.pack([(c0, b0)], dev)
         bt.set_schedule(seg=64, order=1, blocks_per_sm=0, use_graph=True)
-        for _ in range(3):
-            bt.step(cons, b, 0.3, sch)
-        barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
-            bt.step(cons, b, 0.3, sch)
-        e1.record(stream)
-        barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        bt.last_dt()
-        out[f"batched_1x{n0}cubed_same_state"] = whole_job_rate(n0**3 * args.steps, world, ms)
-        out["batched_config"]["same_state_phase_ms_last_step"] = {
-            f"stage{st + 1}": {k: round(v, 3) for k, v in ph.items()} for st, ph in bt.phase_ms().items()}
+        c_start, b_start = cons.clone(), b.clone()
+        for nl_s in (3, 1):  # three launches per stage, then one
+            cons.copy_(c_start)
+            b.copy_(b_start)
+            bt.set_launches(nl_s)
+            ms = timed(sch)
+            bt.last_dt()
+            key = f"batched_1x{n0}cubed_same_state" + ("" if nl_s == 3 else "_one_launch_per_stage")
+            out[key] = whole_job_rate(n0**3 * args.steps, world, ms)
+            out["batched_config"]["same_state_phase_ms_last_step" + ("" if nl_s == 3 else "_one_launch")] = {
+                f"stage{st + 1}": {k: round(v, 3) for k, v in ph.items()} for st, ph in bt.phase_ms().items()}
+        del c_start, b_start
         bt.close()
     return out
 

@@ -234,11 +234,12 @@ mhd_status mhd_step_noalloc(const mhd_config *cfg, const mhd_state *state, doubl
  * A batch is a list of independent triply periodic patches of sizes dims[3p..3p+2] = (nx, ny, nz)
  * and common cell width h (one refinement level of an AMR hierarchy, each patch its own periodic
  * box). One step advances every patch by the same dt = cfl h / (max over all cells of all patches
- * of the CFL signal speed, Eq. resistivity:cfl), computed on the device. Each RK stage runs as
- * persistent cooperative launches over all patches (grid-wide barriers with a bounded wait): the
- * face sweeps at the face kernel's register budget; the edge sweeps, update and validity flags
- * at half that budget (twice the warps per SM); and, with flux correction on, the first-order
- * correction (returning at once when the stage flagged nothing). The whole step is captured once
+ * of the CFL signal speed, Eq. resistivity:cfl), computed on the device. Each RK stage runs as one
+ * persistent cooperative launch over all patches (grid-wide barriers with a bounded wait between
+ * its phases), or as three (mhd_batch_set_launches): the face sweeps at the face kernel's register
+ * budget; the edge sweeps, update and validity flags at half that budget (twice the warps per
+ * SM); and, with flux correction on, the first-order correction (returning at once when the stage
+ * flagged nothing). The whole step is captured once
  * as a CUDA graph and replayed while the state arrays, scheme, eta and cfl stay the same. Every
  * EMF compute scheme (Q26, FS18, B25a) with LD04 averaging; B25b -> MHD_ERR_UNSUPPORTED. */
 typedef struct mhd_batch mhd_batch;
@@ -287,18 +288,25 @@ mhd_status mhd_batch_stats(mhd_batch *batch, long long *fofc_cells_stage1, long 
 mhd_status mhd_batch_phase_ms(mhd_batch *batch, double *ms);
 
 /* Schedule of the persistent stage launches: sweep segment length seg (points per thread), patch
- * order (0 as given, 1 largest first), CTAs per SM of the face-sweep launch (0 = as many as fit;
- * the other launches take as many as fit), and whether steps are captured and replayed as a
- * CUDA graph. */
+ * order (0 as given, 1 largest first), CTAs per SM of the stage's first launch (0 = as many as
+ * fit; with three launches per stage the others take as many as fit), and whether steps are
+ * captured and replayed as a CUDA graph. */
 mhd_status mhd_batch_set_schedule(mhd_batch *batch, int seg, int order, int blocks_per_sm, int use_graph);
 
-/* Autotuner: times one step for every candidate schedule (seg in {16, 32, 64, 128}, both orders,
- * 1 .. max CTAs per SM of the face-sweep launch) on a scratch copy of `state` (left unchanged; the copy is allocated and
- * freed here), keeps the fastest and returns it. The choice is remembered for the process, keyed
- * by the device, the scheme, whether eta is zero and the histogram of patch sizes: a later call
- * with the same key (on this batch or another) sets that schedule without timing anything. */
+/* Launches per RK stage: 1 (default) runs every phase of the stage in one persistent cooperative
+ * launch at the face sweep's register budget; 3 runs the face phase, then the edge, update and
+ * flag phases at half that budget (twice the warps per SM), then the first-order correction.
+ * Same results bit for bit. MHD_ERR_ARG for any other value. Synchronises the batch's stream. */
+mhd_status mhd_batch_set_launches(mhd_batch *batch, int launches_per_stage);
+
+/* Autotuner: times one step for every candidate schedule (1 or 3 launches per stage; seg in
+ * {16, 32, 64, 128}; both orders; 1 .. max CTAs per SM of the first launch) on a scratch copy of
+ * `state` (left unchanged; the copy is allocated and freed here), keeps the fastest and returns
+ * it (any output pointer may be NULL). The choice is remembered for the process, keyed by the
+ * device, the scheme, whether eta is zero and the histogram of patch sizes: a later call with the
+ * same key (on this batch or another) sets that schedule without timing anything. */
 mhd_status mhd_batch_tune(mhd_batch *batch, const mhd_batch_state *state, double cfl, int scheme, double eta,
-                          int *seg, int *order, int *blocks_per_sm);
+                          int *seg, int *order, int *blocks_per_sm, int *launches_per_stage);
 
 /* Test hook for the bounded barrier: every grid barrier waits for extra_blocks blocks more than
  * were launched and gives up after spin_limit polls (~100 ns each), so the next step ends with

@@ -1,15 +1,14 @@
-// mhd_batch.cu -- many uneven periodic patches advanced together (the batched form of the step).
+// mhd_batch.cu -- many uneven periodic patches advanced together (the batched form of the step):
+// the CFL reduction, dt and copy-back kernels, the first-order correction launch and the host side.
 //
-// Each stage of the step runs as two persistent cooperative launches whose blocks walk, phase
-// after phase, work lists that span every patch (cells for the per-cell phases, line segments of
-// the sweeps for the face and edge phases), separated by a grid-wide barrier of the library's own
-// with a bounded wait: the face phase (after stage 2's primitives where flux correction changed
-// stage 1's result) at the face sweep's register budget, then the edge, update, flag and
-// flux-correction phases in a kernel held to half that budget, so that they run with twice the
-// warps per SM. The CFL reduction and the time step stay on the device, so one step (reduction,
-// dt, stage 1, stage 2, copy back) is captured once as a CUDA graph and replayed. Patch order,
-// sweep segment length and the face launch's CTAs per SM form the schedule that mhd_batch_tune
-// picks by timing candidates.
+// Each RK stage runs as one persistent cooperative launch, or as three (face phase; edge, update
+// and flag phases at half the face phase's register budget; first-order correction), whose blocks
+// walk, phase after phase, work lists that span every patch (cells for the per-cell phases, line
+// segments of the sweeps for the face and edge phases), separated by a grid-wide barrier of the
+// library's own with a bounded wait (mhd_batch.cuh). The CFL reduction and the time step stay on
+// the device, so one step (reduction, dt, stage 1, stage 2, copy back) is captured once as a CUDA
+// graph and replayed. Launch form, patch order, sweep segment length and the first launch's CTAs
+// per SM form the schedule that mhd_batch_tune picks by timing candidates.
 #include <algorithm>
 #include <cstring>
 #include <tuple>
@@ -21,320 +20,12 @@
 #include <vector>
 
 #include "../../include/mhd.h"
-#include "mhd_cell.cuh"
-#include "mhd_edge.cuh"
-#include "mhd_face.cuh"
+#include "mhd_batch.cuh"
 
 namespace mhd {
 
-struct BatchDev {
-  const Dev* patches;             // per-patch parameters of this stage, [npatch]
-  const int* order;               // patch visited at schedule position k, [npatch]
-  const long long* cell_pref;     // [npatch + 1] cells before schedule position k
-  const long long* sweep_pref;    // [4][npatch + 1] sweep segments along dir (row 3: the edge sweeps'
-                                  // segments along x) before position k
-  int npatch;
-  int seg;
-  int stage;
-  int fofc;
-  unsigned* barrier;              // [0] arrivals, [1] generation
-  unsigned long long* counters;   // [0] stage-1 flags, [1] stage-2 flags, [2] max speed, [7] error
-  long long spin_limit;           // bounded wait per barrier (iterations of ~100 ns)
-  int barrier_extra;              // test hook: wait for this many blocks more than launched
-  unsigned long long* ptime;      // [2][8] global-timer stamps at the phase boundaries of each stage
-  unsigned long long* cursor;     // [5] work-list cursors of the face, edge_bt, edge_lr and B25a's two
-                                  // cell-EMF phases
-  unsigned* patch_flags;          // [2][npatch] flagged cells per stage and schedule position
-};
-
-// position k with pref[k] <= i < pref[k + 1]
-__device__ __forceinline__ int find_pos(const long long* pref, int n, long long i) {
-  int lo = 0, hi = n;  // invariant pref[lo] <= i < pref[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (pref[mid] <= i) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// schedule position of item i at or after k (a thread's items only grow, by less than a patch)
-__device__ __forceinline__ int advance_pos(const long long* pref, int k, long long i) {
-  while (pref[k + 1] <= i) ++k;
-  return k;
-}
-
-// block 0 stamps the global timer (ns) when it passes phase boundary j of this stage
-__device__ __forceinline__ void stamp(const BatchDev& B, int j) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    B.ptime[8 * B.stage + j] = t;
-  }
-}
-
-// Grid-wide barrier with a bounded wait: false (and the error flag set) if the other blocks did
-// not all arrive within the limit; the caller then leaves the kernel.
-__device__ bool grid_sync(const BatchDev& B) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned expected = gridDim.x + (unsigned)B.barrier_extra;
-    volatile unsigned* vgen = B.barrier + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(B.barrier, 1u);
-    int ok = 1;
-    if (arrived == expected - 1) {
-      atomicExch(B.barrier, 0u);
-      __threadfence();
-      atomicAdd(B.barrier + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (++spins > B.spin_limit || *(volatile unsigned long long*)(B.counters + 7)) {
-          ok = 0;
-          atomicExch(B.counters + 7, 1ull);
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// One sweep phase: the sweeps along dirs[0..2] of every patch form one work list (sweep j's
-// segments after those of sweeps 0 .. j-1, patches in schedule order), taken 32 segments at a
-// time per warp from `cursor`; fn(D, j, line, m0, m1) runs each segment. In the edge phases
-// (EDGE) the lines along x are cut as the single-box edge sweeps cut them: short segments
-// numbered along the line, so that a warp walks whole lines (one thread per x-line would stream
-// a separate cache line per thread and array).
-template <bool EDGE = false, class Fn>
-__device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long long* cursor, const int* dirs, Fn fn) {
-  const long long* pref[3];
-  long long tot[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    pref[j] = B.sweep_pref + ((EDGE && dirs[j] == 0) ? 3 : dirs[j]) * (B.npatch + 1);
-    tot[j] = pref[j][B.npatch];
-  }
-  for_each_segment(cursor, tot[0] + tot[1] + tot[2], [&](long long t) {
-    int j = 0;
-    if (t >= tot[0]) {
-      t -= tot[0];
-      j = 1;
-      if (t >= tot[1]) {
-        t -= tot[1];
-        j = 2;
-      }
-    }
-    const int k = find_pos(pref[j], B.npatch, t);
-    const Dev& D = B.patches[B.order[k]];
-    const bool xl = EDGE && dirs[j] == 0;
-    Line ln;
-    int m0, m1;
-    if (sweep_line_at(D, dirs[j], xl ? edge_sweep_seg(D, 0, B.seg) : B.seg, t - pref[j][k], ln, m0, m1, xl))
-      fn(D, j, ln, m0, m1);
-  });
-}
-
-// cells per thread per pass of the per-cell phases: the face launch has few warps per SM to hide
-// memory latency, the other launch twice as many
-constexpr int kCellIlp = 4;
-constexpr int kRestIlp = 2;
-// CTAs of 128 threads per SM that the second launch of a stage is compiled to fit (one fewer for
-// FS18, whose bottom/top sweep carries five reconstruction windows)
-constexpr int kRestMinBlocks = 4;
-
-// stage 2's primitives (where flux correction changed stage 1's result) and the face sweeps
-template <int RC, int RS>
-__global__ void __launch_bounds__(128) k_batch_face(BatchDev B) {
-  // a barrier of an earlier launch gave up (the flag stays set until the host reads it): the
-  // step is abandoned and the caller's state left as it was
-  if (*(volatile unsigned long long*)(B.counters + 7)) return;
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ncell = B.cell_pref[B.npatch];
-  const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
-  stamp(B, 0);
-  // the sweep phases' cursors start at zero: the face phase's is taken only after the grid
-  // barrier below, which block 0 passes only after this, the edge phases' in the next launch
-  if (blockIdx.x == 0 && threadIdx.x < 5) atomicExch(B.cursor + threadIdx.x, 0ull);
-  // per-patch flag counts of this stage start at zero (read in the next launch only)
-  unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
-  for (long long i = t0; i < B.npatch; i += nth) pflags[i] = 0u;
-  // cons -> prim, kCellIlp cells per thread at a time, loads of all of them before any store.
-  // Stage 1's primitives come from the CFL reduction, stage 2's from stage 1's flag phase unless
-  // flux correction changed its state (per patch: only patches where stage 1 flagged a cell are
-  // redone).
-  const bool prim_given = B.stage == 0 || *(volatile unsigned long long*)(B.counters + 0) == 0;
-  for (long long i0 = t0, k = k0; i0 < ncell && !prim_given; i0 += kCellIlp * nth) {
-    double w[kCellIlp][8];
-    const Dev* Dp[kCellIlp];
-    long long X[kCellIlp];
-#pragma unroll
-    for (int g = 0; g < kCellIlp; ++g) {
-      const long long i = i0 + g * nth;
-      Dp[g] = nullptr;
-      if (i < ncell) {
-        k = advance_pos(B.cell_pref, (int)k, i);
-        if (B.stage == 1 && B.patch_flags[k] == 0u) continue;  // stage 1 left this patch's primitives
-        Dp[g] = &B.patches[B.order[k]];
-        X[g] = i - B.cell_pref[k];
-        prim_of(*Dp[g], Dp[g]->Uin, Dp[g]->Bin, X[g], w[g]);
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < kCellIlp; ++g)
-      if (Dp[g])
-        for (int v = 0; v < 8; ++v) Dp[g]->P[v * Dp[g]->N + X[g]] = w[g][v];
-  }
-  if (!grid_sync(B)) return;
-  stamp(B, 1);
-  // face sweeps along each direction
-  const int dirs[3] = {0, 1, 2};
-  sweep_phase(B, B.cursor + 0, dirs, [&](const Dev& D, int j, const Line& ln, int m0, int m1) {
-    face_seg<RC, RS>(D, j, ln, m0, m1);
-  });
-}
-
-// the edge sweeps (for B25a after its cell-EMF sweeps), the update and the validity flags of the
-// stage, for the EMF compute scheme EMF
-template <int RC, int EMF>
-__global__ void __launch_bounds__(128, EMF == EMF_FS18 ? kRestMinBlocks - 1 : kRestMinBlocks) k_batch_rest(BatchDev B) {
-  if (*(volatile unsigned long long*)(B.counters + 7)) return;  // the face launch gave up
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ncell = B.cell_pref[B.npatch];
-  const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
-  unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
-  stamp(B, 2);
-  if (EMF == EMF_B25A) {
-    // the cell-centred EMF reconstructed to the a-faces (lines along a = e + 1) and to the c-faces
-    // (lines along c = e + 2): two independent work lists, no barrier between them
-    const int dirs_a[3] = {1, 2, 0}, dirs_c[3] = {2, 0, 1};
-    sweep_phase<true>(B, B.cursor + 3, dirs_a, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
-      b25_seg<RC>(D, e, 1, ln, m0, m1);
-    });
-    sweep_phase<true>(B, B.cursor + 4, dirs_c, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
-      b25_seg<RC>(D, e, 0, ln, m0, m1);
-    });
-    if (!grid_sync(B)) return;
-  }
-  // a-face quantities to e-edges (lines along c = e + 2)
-  {
-    const int dirs[3] = {2, 0, 1};
-    sweep_phase<true>(B, B.cursor + 1, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
-      edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
-    });
-  }
-  if (!grid_sync(B)) return;
-  stamp(B, 3);
-  // c-face quantities to e-edges (lines along a = e + 1) and the edge EMFs
-  {
-    const int dirs[3] = {1, 2, 0};
-    sweep_phase<true>(B, B.cursor + 2, dirs, [&](const Dev& D, int e, const Line& ln, int m0, int m1) {
-      edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
-    });
-  }
-  if (!grid_sync(B)) return;
-  stamp(B, 4);
-  // update, then (after a grid barrier) the validity flags of the new state, which the flag pass
-  // reads back instead of recomputing each cell's upper faces
-  {
-    int ku = k0;
-    for (long long base = t0; base < ncell; base += kRestIlp * nth) {
-      double w[kRestIlp][8];
-      const Dev* Dp[kRestIlp];
-      long long X[kRestIlp];
-#pragma unroll
-      for (int g = 0; g < kRestIlp; ++g) {
-        const long long i = base + g * nth;
-        Dp[g] = nullptr;
-        if (i < ncell) {
-          ku = advance_pos(B.cell_pref, ku, i);
-          Dp[g] = &B.patches[B.order[ku]];
-          X[g] = i - B.cell_pref[ku];
-          update_vals(*Dp[g], X[g], w[g]);
-        }
-      }
-#pragma unroll
-      for (int g = 0; g < kRestIlp; ++g)
-        if (Dp[g]) store_update(*Dp[g], X[g], w[g]);
-    }
-  }
-  if (!grid_sync(B)) return;
-  // (every lane of a warp runs the same number of passes for the ballot)
-  int kf = k0;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < ncell; base += kRestIlp * nth) {
-    double u[kRestIlp][5], lo[kRestIlp][3], hi[kRestIlp][3], pw[kRestIlp][8];
-    int K[kRestIlp];
-    bool f[kRestIlp];
-    const Dev* Dp[kRestIlp];
-    long long X[kRestIlp];
-#pragma unroll
-    for (int g = 0; g < kRestIlp; ++g) {
-      const long long i = base + g * nth + threadIdx.x;
-      Dp[g] = nullptr;
-      if (i < ncell) {
-        kf = advance_pos(B.cell_pref, kf, i);
-        Dp[g] = &B.patches[B.order[kf]];
-        X[g] = i - B.cell_pref[kf];
-        K[g] = kf;
-        load_cell(*Dp[g], Dp[g]->Uout, Dp[g]->Bout, X[g], u[g], lo[g], hi[g]);
-      }
-    }
-    unsigned cnt = 0;
-#pragma unroll
-    for (int g = 0; g < kRestIlp; ++g) {
-      f[g] = false;
-      if (Dp[g]) {
-        // stage 1 also forms the primitives of its result (stage 2's input), and reads the
-        // pressure of the validity test from them
-        f[g] = B.stage == 0 ? prim_invalid(*Dp[g], u[g], lo[g], hi[g], pw[g])
-                            : invalid_vals(*Dp[g], u[g], lo[g], hi[g]);
-        Dp[g]->flag[X[g]] = f[g] ? 1 : 0;
-        if (f[g]) atomicAdd(&pflags[K[g]], 1u);
-        if (B.stage == 0)  // the primitives of S^{n+1/2}, stage 2's input
-          for (int v = 0; v < 8; ++v) Dp[g]->P[v * Dp[g]->N + X[g]] = pw[g][v];
-      }
-      cnt += __popc(__ballot_sync(0xffffffffu, f[g]));
-    }
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&B.counters[B.stage], (unsigned long long)cnt);
-  }
-}
-
-// first-order correction of the flagged patches' faces and edges and recompute of their touched
-// cells (a launch of its own at the face sweep's register budget: it solves several face
-// problems per cell; it returns at once when the stage flagged nothing)
-__global__ void __launch_bounds__(128) k_batch_fofc(BatchDev B) {
-  if (*(volatile unsigned long long*)(B.counters + 7)) return;  // an earlier launch gave up
-  stamp(B, 5);
-  if (*(volatile unsigned long long*)(B.counters + B.stage) == 0) return;  // uniform over the grid
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ncell = B.cell_pref[B.npatch];
-  const int k0 = t0 < ncell ? find_pos(B.cell_pref, B.npatch, t0) : 0;
-  const unsigned* const pflags = B.patch_flags + (long long)B.stage * B.npatch;
-  // patches are independent boxes: only those with a flagged cell have anything to correct
-  for (long long i = t0, k = k0; i < ncell; i += nth) {
-    k = advance_pos(B.cell_pref, (int)k, i);
-    if (pflags[k] == 0u) continue;
-    const Dev& D = B.patches[B.order[k]];
-    fo_faces_cell(D, i - B.cell_pref[k]);
-    fo_edges_cell(D, i - B.cell_pref[k]);
-  }
-  if (!grid_sync(B)) return;
-  stamp(B, 6);
-  for (long long i = t0, k = k0; i < ncell; i += nth) {
-    k = advance_pos(B.cell_pref, (int)k, i);
-    if (pflags[k] == 0u) continue;
-    fo_recompute_cell(B.patches[B.order[k]], i - B.cell_pref[k]);
-  }
-}
+// the correction at the face sweep's register budget (it solves several face problems per cell)
+__global__ void __launch_bounds__(128) k_batch_fofc(BatchDev B) { fofc_part(B); }
 
 // max over all cells of all patches of the CFL signal speed (Sec. 2.4, cfl_speed_max), with the
 // running maximum shared across each warp after every pass
@@ -412,43 +103,19 @@ __global__ void __launch_bounds__(256) k_batch_copy_back(const double* __restric
   for (long long i = t0; i < nb; i += nth) b[i] = B1[i];
 }
 
-typedef void (*StageKernel)(BatchDev);
-
-template <int RC>
-static StageKernel pick_rs(int rs) {
-  switch (rs) {
-    case RS_HLL: return k_batch_face<RC, RS_HLL>;
-    case RS_HLLD: return k_batch_face<RC, RS_HLLD>;
-    default: return k_batch_face<RC, RS_LLF>;
-  }
-}
-// the second launch of a stage (edge, update and flag phases)
-template <int EMF>
-static StageKernel rest_kernel_e(int recon) {
+static StageKernel batch_kernel_of(int recon, int which, int rs, int emf) {
   switch (recon) {
-    case REC_PC: return k_batch_rest<REC_PC, EMF>;
-    case REC_PLM_MC: return k_batch_rest<REC_PLM_MC, EMF>;
-    case REC_PLM_MINMOD: return k_batch_rest<REC_PLM_MINMOD, EMF>;
-    case REC_PPM: return k_batch_rest<REC_PPM, EMF>;
-    default: return k_batch_rest<REC_PPM_EP, EMF>;
+    case REC_PC: return batch_kernel<REC_PC>(which, rs, emf);
+    case REC_PLM_MC: return batch_kernel<REC_PLM_MC>(which, rs, emf);
+    case REC_PLM_MINMOD: return batch_kernel<REC_PLM_MINMOD>(which, rs, emf);
+    case REC_PPM: return batch_kernel<REC_PPM>(which, rs, emf);
+    default: return batch_kernel<REC_PPM_EP>(which, rs, emf);
   }
 }
-static StageKernel rest_kernel(int recon, int emf) {
-  switch (emf) {
-    case EMF_FS18: return rest_kernel_e<EMF_FS18>(recon);
-    case EMF_B25A: return rest_kernel_e<EMF_B25A>(recon);
-    default: return rest_kernel_e<EMF_Q26>(recon);
-  }
-}
-static StageKernel stage_kernel(int recon, int rs) {
-  switch (recon) {
-    case REC_PC: return pick_rs<REC_PC>(rs);
-    case REC_PLM_MC: return pick_rs<REC_PLM_MC>(rs);
-    case REC_PLM_MINMOD: return pick_rs<REC_PLM_MINMOD>(rs);
-    case REC_PPM: return pick_rs<REC_PPM>(rs);
-    default: return pick_rs<REC_PPM_EP>(rs);
-  }
-}
+// the first launch of a stage: the one launch per stage (one) or the face launch of three
+static StageKernel stage_kernel(int recon, int rs, bool one) { return batch_kernel_of(recon, one ? 0 : 1, rs, 0); }
+// the second launch of three (edge, update and flag phases)
+static StageKernel rest_kernel(int recon, int emf) { return batch_kernel_of(recon, 2, 0, emf); }
 
 }  // namespace mhd
 
@@ -485,6 +152,7 @@ struct mhd_batch {
   long long* sweep_pref_dev;      // 4 * (npatch + 1)
   // schedule
   int seg, order_kind, blocks_per_sm, use_graph;
+  int launches_per_stage;         // 1: one persistent launch per stage; 3: face / rest / correction
   long long spin_limit;
   int barrier_extra;
   // what the current parameters / graph were built for
@@ -499,7 +167,7 @@ struct mhd_batch {
 
 // schedules chosen by mhd_batch_tune, keyed by device, scheme and patch-size histogram
 std::mutex g_tune_mu;
-std::map<std::string, std::array<int, 3>> g_tune_cache;
+std::map<std::string, std::array<int, 4>> g_tune_cache;
 
 namespace {
 
@@ -620,7 +288,7 @@ mhd_status upload_params(mhd_batch* b, const mhd_batch_state* s, int scheme, dou
   return bcuda(b, e, "parameter upload");
 }
 
-mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc) {
+mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc, int emf) {
   mhd::BatchDev B;
   B.patches = b->pdev[stage];
   B.order = b->order_dev;
@@ -630,6 +298,7 @@ mhd::BatchDev batch_dev(mhd_batch* b, int stage, bool fofc) {
   B.seg = b->seg;
   B.stage = stage;
   B.fofc = fofc ? 1 : 0;
+  B.emf = emf;
   B.barrier = b->barrier;
   B.counters = b->counters;
   B.spin_limit = b->spin_limit;
@@ -655,8 +324,9 @@ mhd_status report_timeout(mhd_batch* b) {
 mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta,
                         cudaStream_t st) {
   const bool fofc = !(scheme & MHD_FOFC_OFF);
-  const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf;
-  mhd::StageKernel kf = mhd::stage_kernel(recon, rs), kr = mhd::rest_kernel(recon, (scheme >> 8) & 0xf);
+  const int recon = scheme & 0xf, rs = (scheme >> 4) & 0xf, emf = (scheme >> 8) & 0xf;
+  const bool one = b->launches_per_stage == 1;
+  mhd::StageKernel kf = mhd::stage_kernel(recon, rs, one), kr = mhd::rest_kernel(recon, emf);
   int per_sm = 0, per_sm_rest = 0;
   int per_sm_fofc = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 128, 0);
@@ -675,14 +345,14 @@ mhd_status enqueue_step(mhd_batch* b, const mhd_batch_state* s, double cfl, int 
   if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 2 * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ptime, 0, 16 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
-  mhd::BatchDev B0 = batch_dev(b, 0, fofc);
+  mhd::BatchDev B0 = batch_dev(b, 0, fofc, emf);
   mhd::k_batch_maxspeed<<<b->nsm * 8, 256, 0, st>>>(B0);
   mhd::k_batch_set_dt<<<(b->npatch + 255) / 256, 256, 0, st>>>(
       b->pdev[0], b->pdev[1], b->npatch, b->counters + 2, cfl, eta, b->h, b->dt_dev, b->counters + 6);
   for (int stage = 0; stage < 2; ++stage) {
-    mhd::BatchDev B = batch_dev(b, stage, fofc);
+    mhd::BatchDev B = batch_dev(b, stage, fofc, emf);
     void* args[] = {&B};
-    for (int part = 0; part < (fofc ? 3 : 2); ++part) {
+    for (int part = 0; part < (one ? 1 : (fofc ? 3 : 2)); ++part) {
       cudaLaunchConfig_t lc;
       std::memset(&lc, 0, sizeof(lc));
       lc.gridDim = dim3(part == 1 ? grid_rest : (part == 0 ? grid_face : grid_fofc));
@@ -751,6 +421,7 @@ mhd_status mhd_batch_create(const int* dims, int npatch, double h, double gamma,
   b->order_kind = 1;
   b->blocks_per_sm = 0;
   b->use_graph = 1;
+  b->launches_per_stage = 1;
   b->spin_limit = 1LL << 25;  // ~3 s of waiting before a barrier gives up
   b->barrier_extra = 0;
   b->graph_ok = false;
@@ -938,8 +609,18 @@ mhd_status mhd_batch_phase_ms(mhd_batch* b, double* ms) {
   return MHD_OK;
 }
 
+mhd_status mhd_batch_set_launches(mhd_batch* b, int launches_per_stage) {
+  if (!b) return MHD_ERR_ARG;
+  if (launches_per_stage != 1 && launches_per_stage != 3) return bfail(b, MHD_ERR_ARG, "launches per stage: 1 or 3");
+  mhd_status s = bcuda(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+  if (s != MHD_OK) return s;
+  b->launches_per_stage = launches_per_stage;
+  drop_graph(b);
+  return MHD_OK;
+}
+
 mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, int scheme, double eta, int* seg_out,
-                          int* order_out, int* bps_out) {
+                          int* order_out, int* bps_out, int* launches_out) {
   if (!b || !s || !s->cons || !s->b) return MHD_ERR_ARG;
   // the choice depends on the device, the scheme and the patches' sizes (not on their order or
   // state): a batch with the same histogram of patch sizes reuses an earlier choice untimed
@@ -957,11 +638,13 @@ mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, in
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      const int c_seg = it->second[0], c_order = it->second[1], c_bps = it->second[2];
+      const int c_seg = it->second[0], c_order = it->second[1], c_bps = it->second[2], c_l = it->second[3];
       mhd_status st = mhd_batch_set_schedule(b, c_seg, c_order, c_bps, b->use_graph);
+      if (st == MHD_OK) st = mhd_batch_set_launches(b, c_l);
       if (seg_out) *seg_out = c_seg;
       if (order_out) *order_out = c_order;
       if (bps_out) *bps_out = c_bps;
+      if (launches_out) *launches_out = c_l;
       return st;
     }
   }
@@ -970,20 +653,25 @@ mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, in
   cudaError_t e = cudaMalloc(&cpy, 8 * b->ncell * sizeof(double));
   if (e != cudaSuccess) return bcuda(b, e, "cudaMalloc");
   mhd_batch_state t = {cpy, cpy + 5 * b->ncell};
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::stage_kernel(scheme & 0xf, (scheme >> 4) & 0xf), 128, 0);
+  int per_sm[2] = {0, 0};  // CTAs per SM of the first launch: one launch per stage, three
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], mhd::stage_kernel(scheme & 0xf, (scheme >> 4) & 0xf, true),
+                                                128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], mhd::stage_kernel(scheme & 0xf, (scheme >> 4) & 0xf, false),
+                                                128, 0);
   const int segs[] = {16, 32, 64, 128};
   float best = 1e30f;
-  int bs = 64, bo = 1, bb = 0;
+  int bs = 64, bo = 1, bb = 0, bl = 3;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   mhd_status st = MHD_OK;
   const int saved_graph = b->use_graph;
+  for (int form = 0; form < 2 && st == MHD_OK; ++form)
   for (int seg : segs)
     for (int order = 0; order < 2 && st == MHD_OK; ++order)
-      for (int bps = 1; bps <= std::max(1, per_sm) && st == MHD_OK; ++bps) {
+      for (int bps = 1; bps <= std::max(1, per_sm[form]) && st == MHD_OK; ++bps) {
         st = mhd_batch_set_schedule(b, seg, order, bps, 0);
+        if (st == MHD_OK) st = mhd_batch_set_launches(b, form == 0 ? 1 : 3);
         if (st != MHD_OK) break;
         float ms = 0.f;
         for (int rep = 0; rep < 2 && st == MHD_OK; ++rep) {  // first run warms up
@@ -1004,6 +692,7 @@ mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, in
           bs = seg;
           bo = order;
           bb = bps;
+          bl = form == 0 ? 1 : 3;
         }
       }
   cudaEventDestroy(e0);
@@ -1012,13 +701,15 @@ mhd_status mhd_batch_tune(mhd_batch* b, const mhd_batch_state* s, double cfl, in
   cudaFree(cpy);
   if (st != MHD_OK) return st;
   st = mhd_batch_set_schedule(b, bs, bo, bb, saved_graph);
+  if (st == MHD_OK) st = mhd_batch_set_launches(b, bl);
   if (st == MHD_OK) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = {bs, bo, bb};
+    g_tune_cache[key] = {bs, bo, bb, bl};
   }
   if (seg_out) *seg_out = bs;
   if (order_out) *order_out = bo;
   if (bps_out) *bps_out = bb;
+  if (launches_out) *launches_out = bl;
   return st;
 }
 

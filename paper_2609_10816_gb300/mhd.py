@@ -117,8 +117,10 @@ def lib():
     L.mhd_batch_phase_ms.restype = i
     L.mhd_batch_set_schedule.argtypes = [vp, i, i, i, i]
     L.mhd_batch_set_schedule.restype = i
-    L.mhd_batch_tune.argtypes = [vp, P(_BatchState), d, i, d, P(i), P(i), P(i)]
+    L.mhd_batch_tune.argtypes = [vp, P(_BatchState), d, i, d, P(i), P(i), P(i), P(i)]
     L.mhd_batch_tune.restype = i
+    L.mhd_batch_set_launches.argtypes = [vp, i]
+    L.mhd_batch_set_launches.restype = i
     L.mhd_batch_test_barrier.argtypes = [vp, i, ll]
     L.mhd_batch_test_barrier.restype = i
     L.mhd_batch_last_error.argtypes = [vp]
@@ -349,12 +351,17 @@ class Batch:
     def set_schedule(self, seg=64, order=1, blocks_per_sm=0, use_graph=True):
         self._err(lib().mhd_batch_set_schedule(self._h, int(seg), int(order), int(blocks_per_sm), 1 if use_graph else 0))
 
+    def set_launches(self, launches_per_stage: int):
+        """1: one persistent launch per RK stage (the default); 3: face / edge-update-flag /
+        first-order-correction launches."""
+        self._err(lib().mhd_batch_set_launches(self._h, int(launches_per_stage)))
+
     def tune(self, cons, b, cfl, scheme_bits, eta=0.0):
         s = self._st(cons, b)
-        seg, order, bps = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        seg, order, bps, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._err(lib().mhd_batch_tune(self._h, ctypes.byref(s), float(cfl), int(scheme_bits), float(eta),
-                                       ctypes.byref(seg), ctypes.byref(order), ctypes.byref(bps)))
-        return {"seg": seg.value, "order": order.value, "blocks_per_sm": bps.value}
+                                       ctypes.byref(seg), ctypes.byref(order), ctypes.byref(bps), ctypes.byref(nl)))
+        return {"seg": seg.value, "order": order.value, "blocks_per_sm": bps.value, "launches_per_stage": nl.value}
 
     def test_barrier(self, extra_blocks, spin_limit):
         self._err(lib().mhd_batch_test_barrier(self._h, int(extra_blocks), int(spin_limit)))

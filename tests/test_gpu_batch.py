@@ -44,15 +44,19 @@ def _plain_step(shape, cons, b, dt, sch, eta):
     return out
 
 
-@pytest.mark.parametrize("use_graph,emf", [(True, "q26"), (False, "q26"), (True, "fs18"), (True, "b25a")])
-def test_batch_equals_single_box_steps(gpu_lib, use_graph, emf):
+@pytest.mark.parametrize("use_graph,emf,launches", [(True, "q26", 1), (False, "q26", 1), (True, "q26", 3),
+                                                    (False, "q26", 3), (True, "fs18", 1), (True, "fs18", 3),
+                                                    (True, "b25a", 1), (True, "b25a", 3)])
+def test_batch_equals_single_box_steps(gpu_lib, use_graph, emf, launches):
     """Two batched steps of 21 uneven patches (one sets flux-correction flags) equal bit for bit the
-    single-box steps of each patch with the batch's dt, for each EMF compute scheme."""
+    single-box steps of each patch with the batch's dt, for each EMF compute scheme, with one and
+    with three persistent launches per stage."""
     dims, pats = _patches(20, seed=3)
     dims.append((16, 6, 4))
     pats.append(_low_pressure_patch((16, 6, 4)))  # sets flux-correction flags
     bt = mhd.Batch(dims, H)
     bt.set_schedule(seg=8, order=1, blocks_per_sm=0, use_graph=use_graph)
+    bt.set_launches(launches)
     cons, b = bt.pack(pats)
     sch = mhd.scheme("ppm", "hlld", emf)
     for step in range(2):
@@ -130,6 +134,7 @@ def test_batch_autotune_keeps_results(gpu_lib):
     choice = bt.tune(cons, b, 0.3, sch)
     t_first = time.perf_counter() - t0
     assert choice["seg"] in (16, 32, 64, 128) and choice["order"] in (0, 1) and choice["blocks_per_sm"] >= 1
+    assert choice["launches_per_stage"] in (1, 3)
     assert torch.equal(cons, ref_c) and torch.equal(b, ref_b)  # tuning leaves the state alone
     # the choice is remembered by patch-size histogram: another batch of the same sizes (in another
     # order) gets it without timing
@@ -140,9 +145,12 @@ def test_batch_autotune_keeps_results(gpu_lib):
     bt2.close()
     bt.step(cons, b, 0.3, sch)
     bt.set_schedule(seg=7, order=0, blocks_per_sm=1, use_graph=False)
+    bt.set_launches(4 - choice["launches_per_stage"])  # the other form
     bt.step(ref_c, ref_b, 0.3, sch)
     torch.cuda.synchronize()
     assert torch.equal(cons, ref_c) and torch.equal(b, ref_b)  # schedule changes nothing but time
+    with pytest.raises(mhd.MHDError):
+        bt.set_launches(2)
 
 
 def test_batch_barrier_wait_is_bounded(gpu_lib):
