@@ -744,32 +744,39 @@ def main():
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
-    barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    up.wait_event(f0)
-    for k in range(args.e2e_steps):
-        i = k % 2
-        s_k = sts[i]
-        if k >= 2:
-            up.wait_event(ev_out[i])  # buffer i's previous result has been read back
-        with torch.cuda.stream(up):
-            s_k.cons.copy_(cons_h, non_blocking=True)
-            s_k.b.copy_(b_h, non_blocking=True)
-        ev_in[i].record(up)
-        stream.wait_event(ev_in[i])
-        ctx.step_cfl(s_k, 0.3, sch)
-        ev_done[i].record(stream)
-        down.wait_event(ev_done[i])
-        with torch.cuda.stream(down):
-            outs[i][0].copy_(s_k.cons, non_blocking=True)
-            outs[i][1].copy_(s_k.b, non_blocking=True)
-        ev_out[i].record(down)
-    for i in range(min(2, args.e2e_steps)):
-        stream.wait_event(ev_out[i])
-    f1.record(stream)
-    barrier()
-    e2e_ms = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+
+    def e2e_run():
+        barrier()
+        f0.record(stream)
+        up.wait_event(f0)
+        for k in range(args.e2e_steps):
+            i = k % 2
+            s_k = sts[i]
+            if k >= 2:
+                up.wait_event(ev_out[i])  # buffer i's previous result has been read back
+            with torch.cuda.stream(up):
+                s_k.cons.copy_(cons_h, non_blocking=True)
+                s_k.b.copy_(b_h, non_blocking=True)
+            ev_in[i].record(up)
+            stream.wait_event(ev_in[i])
+            ctx.step_cfl(s_k, 0.3, sch)
+            ev_done[i].record(stream)
+            down.wait_event(ev_done[i])
+            with torch.cuda.stream(down):
+                outs[i][0].copy_(s_k.cons, non_blocking=True)
+                outs[i][1].copy_(s_k.b, non_blocking=True)
+            ev_out[i].record(down)
+        for i in range(min(2, args.e2e_steps)):
+            stream.wait_event(ev_out[i])
+        f1.record(stream)
+        barrier()
+        return max_over_ranks(f0.elapsed_time(f1), dist, dev)
+
+    # the copies share the host's memory with other jobs on the machine: the pipeline is timed
+    # three times and the median reported (all three beside it)
+    e2e_runs = sorted(e2e_run() for _ in range(3)) if args.e2e_steps > 0 else []
+    e2e_ms = e2e_runs[1] if e2e_runs else float("nan")
     e2e_value = whole_job_rate(N * args.e2e_steps, world, e2e_ms) if args.e2e_steps > 0 else None
     del sts[1]
 
@@ -846,6 +853,8 @@ def main():
             "h2d_bytes_per_step": int(cons_h.numel() * 8 + b_h.numel() * 8),
             "d2h_bytes_per_step": int(outs[0][0].numel() * 8 + outs[0][1].numel() * 8),
             "steps": args.e2e_steps,
+            "runs_ms": e2e_runs,
+            "timing": "median of 3 timed runs of the pipeline",
             "pipeline": "2 device states; upload of step k+1 and download of step k-1 overlap step k",
         },
         "gpu_launches": launches_timed,
