@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_2609_10816_gb300 import inputs
+from tests.util import relerr_pert
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 G = 5.0 / 3.0
@@ -429,14 +430,7 @@ def test_oblique_alfven_wave_second_order_ppm_hlld_fs18_b25a(emf):
 # ---------------------------------------------------------------------------------------
 # Convergence against closed-form waves (Sec. 3.1, Eq. error:relative)
 # ---------------------------------------------------------------------------------------
-def _relerr_pert(c0, b0, c1, b1, cbg, bbg):
-    """Eq. (error:relative) with the normalisation taken over the perturbation."""
-    num = den = 0.0
-    for s0, s1, sb in list(zip(c0, c1, cbg)) + list(zip(b0, b1, bbg)):
-        n = s0.size
-        num += (np.abs(s0 - s1).mean() * n) ** 2
-        den += (np.abs(s0 - sb).mean() * n) ** 2
-    return np.sqrt(num / den)
+_relerr_pert = relerr_pert  # Eq. (error:relative), normalised by the perturbation
 
 
 def _one_period(cfg, cons, b, T, cfl=0.3):

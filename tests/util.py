@@ -60,3 +60,14 @@ def parity_failures(cg, bg, co, bo, scales=None, l1_tol=L1_TOL, max_tol=MAX_TOL)
     l1 = state_errors(cg, bg, co, bo, scales)
     mx = state_errors(cg, bg, co, bo, scales, norm=rel_max)
     return {k: (l1[k], mx[k]) for k in l1 if not (l1[k] <= l1_tol and mx[k] <= max_tol)}
+
+
+def relerr_pert(c0, b0, c1, b1, cbg, bbg):
+    """Eq. (error:relative) between two states, normalised by the perturbation of the first from
+    the background state (cbg, bbg): the root of the summed squares of the per-field L1 norms."""
+    num = den = 0.0
+    for s0, s1, sb in list(zip(c0, c1, cbg)) + list(zip(b0, b1, bbg)):
+        n = s0.size
+        num += (np.abs(s0 - s1).mean() * n) ** 2
+        den += (np.abs(s0 - sb).mean() * n) ** 2
+    return (num / den) ** 0.5
