@@ -61,3 +61,24 @@ def test_plain_ppm_clips_where_ppm_ep_does_not(gpu_lib):
     print("PPM", pp, "PPM-EP 64^3", ep)
     assert pp[0] / pp[1] < 3.0, pp
     assert pp[1] > 10.0 * ep, (pp, ep)
+
+
+def test_turbulence_256cubed_conserves_and_keeps_divb_zero(gpu_lib):
+    """The headline workload (256^3 Mach-5 turbulence, PPM + HLLD + Q26 + LD04, flux correction on)
+    on the periodic box: five steps conserve the sums of mass, momentum and total energy to rounding
+    (the update is a flux divergence), and div b stays at machine zero (Sec. 2.1)."""
+    shape = (256, 256, 256)
+    cons, b, info = inputs.turbulence(shape)
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    sums0 = st.cons.sum(dim=(1, 2, 3))
+    scale = st.cons.abs().sum(dim=(1, 2, 3))
+    for _ in range(5):
+        ctx.step_cfl(st, 0.3, mhd.scheme("ppm", "hlld", "q26"))
+    sums1 = st.cons.sum(dim=(1, 2, 3))
+    drift = ((sums1 - sums0).abs() / scale).cpu().numpy()
+    md, mb = ctx.divb(st)
+    ctx.close()
+    print("relative drift of the sums", drift, "max|div b| dx / max|b|", md * info["h"][0] / mb)
+    assert (drift < 1e-13).all(), drift
+    assert md * info["h"][0] / mb < 1e-13
