@@ -219,8 +219,76 @@ __device__ __forceinline__ void q26_edge_vjp(const double* in, double lam, doubl
   g[11] = damc;
 }
 
+// Reverse sweep of Eq. (ld04) for any four corner EMFs e = (LB, RB, LT, RT): with
+// s_a = apa + ama, s_c = apc + amc, w = 1 / (s_a s_c), E = apa ama (bcR - bcL) / s_a
+// - apc amc (baT - baB) / s_c + (apc (apa eLB + ama eRB) + amc (apa eLT + ama eRT)) w; lam times
+// dE/de -> de, dE/d(baB, baT, bcL, bcR) -> db, dE/d(apa, ama, apc, amc) -> dal.
+__device__ __forceinline__ void ld04_vjp(double apa, double ama, double apc, double amc, const double* e, double baB,
+                                         double baT, double bcL, double bcR, double lam, double* de, double* db,
+                                         double* dal) {
+  const double sa = apa + ama, sc = apc + amc;
+  const double w = rcp(sa * sc);
+  const double isa = sc * w, isc = sa * w;
+  const double hB = fma(apa, e[0], ama * e[1]), hT = fma(apa, e[2], ama * e[3]);
+  const double up = fma(apc, hB, amc * hT) * w;
+  const double D1 = bcR - bcL, D2 = baT - baB;
+  const double lw = lam * w;
+  de[0] = lw * apc * apa;
+  de[1] = lw * apc * ama;
+  de[2] = lw * amc * apa;
+  de[3] = lw * amc * ama;
+  const double c1 = lam * apa * ama * isa, c2 = lam * apc * amc * isc;
+  db[0] = c2;   // baB
+  db[1] = -c2;  // baT
+  db[2] = -c1;  // bcL
+  db[3] = c1;   // bcR
+  dal[0] = lam * (D1 * ama * ama * isa * isa + fma(apc, e[0], amc * e[2]) * w - up * isa);
+  dal[1] = lam * (D1 * apa * apa * isa * isa + fma(apc, e[1], amc * e[3]) * w - up * isa);
+  dal[2] = lam * (-D2 * amc * amc * isc * isc + hB * w - up * isc);
+  dal[3] = lam * (-D2 * apc * apc * isc * isc + hT * w - up * isc);
+}
+
+// Reverse sweep of the FS18 corners (Eqs. fs18-average, fs18) and their LD04 average. in: baB, baT,
+// bcL, bcR, the a-then-c partials xp[0..7] (u_a L:B,T, u_a R:B,T, u_c L:B,T, u_c R:B,T), the
+// c-then-a partials (u_a B:L,R, u_a T:L,R, u_c B:L,R, u_c T:L,R), then apa, ama, apc, amc (24
+// values); g (24) receives lam times the derivative in each.
+__device__ __forceinline__ void fs18_edge_vjp(const double* in, double lam, double* g) {
+  const double baB = in[0], baT = in[1], bcL = in[2], bcR = in[3];
+  const double* xp = in + 4;
+  const double* lr = in + 12;
+  double ua[4], uc[4], e[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {  // corner q = sI + 2 sII: LB, RB, LT, RT
+    const int sI = q & 1, sII = q >> 1;
+    ua[q] = halve(xp[2 * sI + sII] + lr[2 * sII + sI]);
+    uc[q] = halve(xp[4 + 2 * sI + sII] + lr[4 + 2 * sII + sI]);
+    e[q] = fma(-ua[q], sI ? bcR : bcL, uc[q] * (sII ? baT : baB));
+  }
+  double de[4], db[4];
+  ld04_vjp(in[20], in[21], in[22], in[23], e, baB, baT, bcL, bcR, lam, de, db, g + 20);
+#pragma unroll
+  for (int k = 0; k < 20; ++k) g[k] = 0.0;
+  g[0] = db[0];
+  g[1] = db[1];
+  g[2] = db[2];
+  g[3] = db[3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int sI = q & 1, sII = q >> 1;
+    const double bc = sI ? bcR : bcL, ba = sII ? baT : baB;
+    const double dua = -de[q] * bc, duc = de[q] * ba;
+    g[sI ? 3 : 2] -= de[q] * ua[q];
+    g[sII ? 1 : 0] += de[q] * uc[q];
+    // each velocity is the mean of its two reconstruction orders
+    g[4 + 2 * sI + sII] += 0.5 * dua;
+    g[12 + 2 * sII + sI] += 0.5 * dua;
+    g[8 + 2 * sI + sII] += 0.5 * duc;
+    g[16 + 2 * sII + sI] += 0.5 * duc;
+  }
+}
+
 // ---- edges: adjoint of E_e from the 8 reconstructed edge values, the edge speeds, eta j ----
-template <int RC>
+template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
   const Dev& D = A.D;
   const long long X = aid();
@@ -228,21 +296,38 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
   double etaacc = 0.0;
   for (int e = 0; e < 3 && X < N; ++e) {  // no early return: the whole warp sums d/d(eta) below
     const int a = (e + 1) % 3, c = (e + 2) % 3;
+    constexpr int NE = EMF == EMF_FS18 ? 20 : 8;  // adjoint slots per edge
     const double lam = A.lE[e * N + X];
     if (lam == 0.0) {
-      for (int k = 0; k < 8; ++k) A.lEdge[(8LL * e + k) * N + X] = 0.0;
+      for (int k = 0; k < NE; ++k) A.lEdge[(NE * e + k) * N + X] = 0.0;
       continue;
     }
     const long long Xc = shift(D, X, c, -1), Xa = shift(D, X, a, -1);
-    // the eight reconstructed edge values as the forward edge sweeps formed them: b_a, u_a* bottom
-    // and top (Epart), b_c, u_c* left and right (EdgeC)
-    double in[12];
+    // the reconstructed edge values as the forward edge sweeps formed them. Q26: b_a, u_a* bottom
+    // and top (Epart), b_c, u_c* left and right (EdgeC). FS18: b_a bottom and top (Epart), b_c
+    // left and right, the a-then-c partials (Xpart) and the c-then-a ones (EdgeC).
+    constexpr int NI = EMF == EMF_FS18 ? 24 : 12;
+    double in[NI];
     const double* pa = D.Epart + 4LL * e * N;
-    const double* pc = D.EdgeC + 4LL * e * N;
+    if (EMF == EMF_FS18) {
+      const double* pc = D.EdgeC + 10LL * e * N;
+      const double* xp = D.Xpart + 8LL * e * N;
+      in[0] = pa[X];
+      in[1] = pa[N + X];
+      in[2] = pc[X];
+      in[3] = pc[N + X];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      in[k] = pa[k * N + X];
-      in[4 + k] = pc[k * N + X];
+      for (int k = 0; k < 8; ++k) {
+        in[4 + k] = xp[k * N + X];
+        in[12 + k] = pc[(2 + k) * N + X];
+      }
+    } else {
+      const double* pc = D.EdgeC + 4LL * e * N;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        in[k] = pa[k * N + X];
+        in[4 + k] = pc[k * N + X];
+      }
     }
     const double* Apa = D.Ap + a * N;
     const double* Ama = D.Am + a * N;
@@ -251,17 +336,18 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
     // Eq. (alpha-edge): the max keeps its first argument on ties (pmax)
     const bool wa_p = dbits(Apa[Xc]) >= dbits(Apa[X]), wa_m = dbits(Ama[Xc]) >= dbits(Ama[X]);
     const bool wc_p = dbits(Apc[Xa]) >= dbits(Apc[X]), wc_m = dbits(Amc[Xa]) >= dbits(Amc[X]);
-    in[8] = wa_p ? Apa[Xc] : Apa[X];
-    in[9] = wa_m ? Ama[Xc] : Ama[X];
-    in[10] = wc_p ? Apc[Xa] : Apc[X];
-    in[11] = wc_m ? Amc[Xa] : Amc[X];
-    double g[12];
-    q26_edge_vjp(in, lam, g);
-    for (int k = 0; k < 8; ++k) A.lEdge[(8LL * e + k) * N + X] = g[k];
-    atomicAdd(&A.lAp[a * N + (wa_p ? Xc : X)], g[8]);
-    atomicAdd(&A.lAm[a * N + (wa_m ? Xc : X)], g[9]);
-    atomicAdd(&A.lAp[c * N + (wc_p ? Xa : X)], g[10]);
-    atomicAdd(&A.lAm[c * N + (wc_m ? Xa : X)], g[11]);
+    in[NI - 4] = wa_p ? Apa[Xc] : Apa[X];
+    in[NI - 3] = wa_m ? Ama[Xc] : Ama[X];
+    in[NI - 2] = wc_p ? Apc[Xa] : Apc[X];
+    in[NI - 1] = wc_m ? Amc[Xa] : Amc[X];
+    double g[NI];
+    if (EMF == EMF_FS18) fs18_edge_vjp(in, lam, g);
+    else q26_edge_vjp(in, lam, g);
+    for (int k = 0; k < NE; ++k) A.lEdge[(NE * e + k) * N + X] = g[k];
+    atomicAdd(&A.lAp[a * N + (wa_p ? Xc : X)], g[NI - 4]);
+    atomicAdd(&A.lAm[a * N + (wa_m ? Xc : X)], g[NI - 3]);
+    atomicAdd(&A.lAp[c * N + (wc_p ? Xa : X)], g[NI - 2]);
+    atomicAdd(&A.lAm[c * N + (wc_m ? Xa : X)], g[NI - 1]);
     if (D.resistive) {  // E += eta j, j = (b_c[X] - b_c[X-a]) / h_a - (b_a[X] - b_a[X-c]) / h_c
       const double* Ba = D.Bin[a];
       const double* Bc = D.Bin[c];
@@ -282,24 +368,43 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
 // e = d + 2 (bottom/top slots 0/1 for b, 2/3 for u*), and along t2 = d + 2 as the "c" array of
 // e-edges with e = d + 1 (left/right slots 4/5 for b, 6/7 for u*). Point m's lower value is the
 // top/right value at edge m; its upper value is the bottom/left value at edge m + t.
-template <int RC>
+// FS18's velocity sources on the d-faces, as rows of the face states (LR): reconstructed along c of
+// the e-edges with d = a (u_a L, u_a R, u_c L, u_c R: the normal and the first tangential
+// component) and along a of the e-edges with d = c (u_a B, u_a T, u_c B, u_c T: the second
+// tangential and the normal component)
+__device__ constexpr int kFs18RowBt[4] = {1, 8, 2, 9};
+__device__ constexpr int kFs18RowLr[4] = {3, 10, 1, 8};
+
+template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
   const Dev& D = A.D;
   const long long X = aid();
   if (X >= D.N) return;
   const long long N = D.N;
+  constexpr int NE = EMF == EMF_FS18 ? 20 : 8;
   for (int d = 0; d < 3; ++d) {
     const int t1 = (d + 1) % 3, e1 = (d + 2) % 3;  // d is "a" of e1, reconstructed along c(e1) = t1
     const int t2 = (d + 2) % 3, e2 = (d + 1) % 3;  // d is "c" of e2, reconstructed along a(e2) = t2
-    const double* L1 = A.lEdge + 8LL * e1 * N;
-    const double* L2 = A.lEdge + 8LL * e2 * N;
+    const double* L1 = A.lEdge + (long long)NE * e1 * N;
+    const double* L2 = A.lEdge + (long long)NE * e2 * N;
     const long long X1 = shift(D, X, t1, 1), X2 = shift(D, X, t2, 1);
     // point X's lower value is the top (right) value at edge X, its upper value the bottom (left)
     // value at edge X + t
-    rec_scatter<RC>(D, D.Bin[d], X, t1, L1[1 * N + X], L1[0 * N + X1], A.lB + d * N);
-    rec_scatter<RC>(D, D.Bin[d], X, t2, L2[5 * N + X], L2[4 * N + X2], A.lB + d * N);
-    rec_scatter<RC>(D, D.Us + d * N, X, t1, L1[3 * N + X], L1[2 * N + X1], A.lUs + d * N);
-    rec_scatter<RC>(D, D.Us + d * N, X, t2, L2[7 * N + X], L2[6 * N + X2], A.lUs + d * N);
+    if (EMF == EMF_FS18) {
+      rec_scatter<RC>(D, D.Bin[d], X, t1, L1[1 * N + X], L1[0 * N + X1], A.lB + d * N);
+      rec_scatter<RC>(D, D.Bin[d], X, t2, L2[3 * N + X], L2[2 * N + X2], A.lB + d * N);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long long rb = (14LL * d + kFs18RowBt[k]) * N, rl = (14LL * d + kFs18RowLr[k]) * N;
+        rec_scatter<RC>(D, D.LR + rb, X, t1, L1[(5 + 2 * k) * N + X], L1[(4 + 2 * k) * N + X1], A.lLR + rb);
+        rec_scatter<RC>(D, D.LR + rl, X, t2, L2[(13 + 2 * k) * N + X], L2[(12 + 2 * k) * N + X2], A.lLR + rl);
+      }
+    } else {
+      rec_scatter<RC>(D, D.Bin[d], X, t1, L1[1 * N + X], L1[0 * N + X1], A.lB + d * N);
+      rec_scatter<RC>(D, D.Bin[d], X, t2, L2[5 * N + X], L2[4 * N + X2], A.lB + d * N);
+      rec_scatter<RC>(D, D.Us + d * N, X, t1, L1[3 * N + X], L1[2 * N + X1], A.lUs + d * N);
+      rec_scatter<RC>(D, D.Us + d * N, X, t2, L2[7 * N + X], L2[6 * N + X2], A.lUs + d * N);
+    }
   }
 }
 
@@ -395,11 +500,27 @@ __device__ __forceinline__ RecSrc face_src(const AdjDev& A, int s, int v) {
   const double* lLR = A.lLR + 14LL * s * N;
   return {A.D.P + slot * N, lLR + (7 + v) * N, lLR + v * N, A.lP + slot * N};
 }
-// edge values (k_adj_edge_rec): b_d and u_d^* reconstructed along s, for the face arrays d = s - 1
+// edge values (k_adj_edge_rec): the arrays reconstructed along s, for the face arrays d = s - 1
 // (s is their "c" direction, e-edges e = s + 1: bottom / top values) and d = s + 1 (s is their "a"
-// direction, e-edges e = s + 2: left / right values)
+// direction, e-edges e = s + 2: left / right values). Q26: b_d and u_d^* of each (4 sources);
+// FS18: b_d and the four velocity states of each (10 sources).
+template <int EMF>
 __device__ __forceinline__ RecSrc edge_src(const AdjDev& A, int s, int v) {
   const long long N = A.D.N;
+  if (EMF == EMF_FS18) {
+    const bool bt = v < 5;
+    const int d = bt ? (s + 2) % 3 : (s + 1) % 3;
+    const int e = bt ? (s + 1) % 3 : (s + 2) % 3;
+    const int k = bt ? v : v - 5;  // 0: b_d; 1-4: the velocity states
+    const double* L = A.lEdge + 20LL * e * N;
+    if (k == 0) {
+      const int lo = bt ? 1 : 3;
+      return {A.D.Bin[d], L + lo * N, L + (lo - 1) * N, A.lB + d * N};
+    }
+    const long long row = (14LL * d + (bt ? kFs18RowBt[k - 1] : kFs18RowLr[k - 1])) * N;
+    const int lo = (bt ? 5 : 13) + 2 * (k - 1);
+    return {A.D.LR + row, L + lo * N, L + (lo - 1) * N, A.lLR + row};
+  }
   const bool bt = v < 2;
   const int d = bt ? (s + 2) % 3 : (s + 1) % 3;
   const int e = bt ? (s + 1) % 3 : (s + 2) % 3;
@@ -410,18 +531,18 @@ __device__ __forceinline__ RecSrc edge_src(const AdjDev& A, int s, int v) {
 }
 
 // Reverse PPM sweeps along s over all sources of one kind: thread = (source, line segment).
-template <bool FACE>
+template <bool FACE, int EMF = EMF_Q26>
 __global__ void __launch_bounds__(128) k_adj_rec_sweep(AdjDev A, int s, int seg) {
   const Dev& D = A.D;
   const long long nsw = sweep_threads(D, s, seg);
   const long long tid = aid();
-  const int nsrc = FACE ? 7 : 4;
+  const int nsrc = FACE ? 7 : (EMF == EMF_FS18 ? 10 : 4);
   if (tid >= nsw * nsrc) return;
   const int v = (int)(tid / nsw);
   Line ln;
   int m0, m1;
   if (!sweep_line_at(D, s, seg, tid - v * nsw, ln, m0, m1, s == 0)) return;
-  const RecSrc r = FACE ? face_src(A, s, v) : edge_src(A, s, v);
+  const RecSrc r = FACE ? face_src(A, s, v) : edge_src<EMF>(A, s, v);
   RevPPM w;
   double v5[5];
 #pragma unroll
@@ -504,7 +625,7 @@ __global__ void __launch_bounds__(128) k_adj_faces(AdjDev A, int dir) {
   riemann_grad_rev<RS>(WL, WR, bn, D.gam, D.gm1inv, lf, A.lAp[dir * N + f], A.lAm[dir * N + f],
                        A.lUs[dir * N + f], g);
 #pragma unroll
-  for (int i = 0; i < 14; ++i) A.lLR[(14LL * dir + i) * N + f] = g[i];
+  for (int i = 0; i < 14; ++i) A.lLR[(14LL * dir + i) * N + f] += g[i];
   atomicAdd(&A.lB[dir * N + f], g[14]);
 }
 
@@ -855,8 +976,8 @@ __global__ void __launch_bounds__(128) k_adj_fo(AdjDev A, const unsigned char* f
         if (lam == 0.0) continue;
         const int a = (e + 1) % 3, c = (e + 2) % 3;
         const long long Xa = shift(D, X, a, -1), Xc = shift(D, X, c, -1), Xac = shift(D, Xa, c, -1);
-        // the first-order edge EMF (Q26 corners of piecewise-constant values, LD04 with the LLF
-        // speeds) as fo_edges_cell forms it: the four faces' alpha and u*, recomputed
+        // the first-order edge EMF (corners of piecewise-constant values, LD04 with the LLF speeds)
+        // as fo_edges_cell forms it: the four faces' alpha and u*, recomputed
         double f[5], apaB, apaT, apcL, apcR, uaB, uaT, ucL, ucR;
         fo_face(D, a, Xac, Xc, Xc, f, apaB, uaB);
         fo_face(D, a, Xa, X, X, f, apaT, uaT);
@@ -864,20 +985,54 @@ __global__ void __launch_bounds__(128) k_adj_fo(AdjDev A, const unsigned char* f
         fo_face(D, c, Xc, X, X, f, apcR, ucR);
         const bool pickB = dbits(apaB) >= dbits(apaT), pickL = dbits(apcL) >= dbits(apcR);  // pmax
         const double apa = pickB ? apaB : apaT, apc = pickL ? apcL : apcR;
-        const double in[12] = {D.B0[a][Xc], D.B0[a][X], uaB, uaT, D.B0[c][Xa], D.B0[c][X], ucL, ucR,
-                               apa, apa, apc, apc};
-        double g[12];
-        q26_edge_vjp(in, lam, g);
-        const double dapa = g[8] + g[9], dapc = g[10] + g[11];
+        const double baB = D.B0[a][Xc], baT = D.B0[a][X], bcL = D.B0[c][Xa], bcR = D.B0[c][X];
+        double dba[2], dbc[2], dapa, dapc, dua[2] = {0.0, 0.0}, duc[2] = {0.0, 0.0};
+        if (D.emf == EMF_FS18) {
+          // piecewise-constant FS18: corner q takes the velocity of the cell in that corner
+          // (LB = X-a-c, RB = X-c, LT = X-a, RT = X) and the face fields of the edge
+          const long long cellQ[4] = {Xac, Xc, Xa, X};
+          double ua[4], uc[4], ri[4], e4[4];
+          for (int q = 0; q < 4; ++q) {
+            const long long Q = cellQ[q];
+            ri[q] = rcp(D.U0[Q]);
+            ua[q] = D.U0[(1 + a) * N + Q] * ri[q];
+            uc[q] = D.U0[(1 + c) * N + Q] * ri[q];
+            e4[q] = fma(-ua[q], (q & 1) ? bcR : bcL, uc[q] * ((q >> 1) ? baT : baB));
+          }
+          double de[4], db[4], dal[4];
+          ld04_vjp(apa, apa, apc, apc, e4, baB, baT, bcL, bcR, lam, de, db, dal);
+          dba[0] = db[0]; dba[1] = db[1]; dbc[0] = db[2]; dbc[1] = db[3];
+          dapa = dal[0] + dal[1];
+          dapc = dal[2] + dal[3];
+          for (int q = 0; q < 4; ++q) {
+            const long long Q = cellQ[q];
+            const double bcs = (q & 1) ? bcR : bcL, bas = (q >> 1) ? baT : baB;
+            const double dva = -de[q] * bcs, dvc = de[q] * bas;
+            dbc[q & 1] -= de[q] * ua[q];
+            dba[q >> 1] += de[q] * uc[q];
+            // u = m / rho
+            atomicAdd(&A.lU[(1 + a) * N + Q], dva * ri[q]);
+            atomicAdd(&A.lU[(1 + c) * N + Q], dvc * ri[q]);
+            atomicAdd(&A.lU[Q], -fma(dva, ua[q], dvc * uc[q]) * ri[q]);
+          }
+        } else {
+          const double in[12] = {baB, baT, uaB, uaT, bcL, bcR, ucL, ucR, apa, apa, apc, apc};
+          double g[12];
+          q26_edge_vjp(in, lam, g);
+          dapa = g[8] + g[9];
+          dapc = g[10] + g[11];
+          dba[0] = g[0]; dba[1] = g[1]; dbc[0] = g[4]; dbc[1] = g[5];
+          dua[0] = g[2]; dua[1] = g[3]; duc[0] = g[6]; duc[1] = g[7];
+        }
         const double z[5] = {0, 0, 0, 0, 0};
-        fo_face_vjp(A, a, Xac, Xc, z, pickB ? dapa : 0.0, g[2]);
-        fo_face_vjp(A, a, Xa, X, z, pickB ? 0.0 : dapa, g[3]);
-        fo_face_vjp(A, c, Xac, Xa, z, pickL ? dapc : 0.0, g[6]);
-        fo_face_vjp(A, c, Xc, X, z, pickL ? 0.0 : dapc, g[7]);
-        atomicAdd(&A.lB[a * N + Xc], g[0]);
-        atomicAdd(&A.lB[a * N + X], g[1]);
-        atomicAdd(&A.lB[c * N + Xa], g[4]);
-        atomicAdd(&A.lB[c * N + X], g[5]);
+        fo_face_vjp(A, a, Xac, Xc, z, pickB ? dapa : 0.0, dua[0]);
+        fo_face_vjp(A, a, Xa, X, z, pickB ? 0.0 : dapa, dua[1]);
+        fo_face_vjp(A, c, Xac, Xa, z, pickL ? dapc : 0.0, duc[0]);
+        fo_face_vjp(A, c, Xc, X, z, pickL ? 0.0 : dapc, duc[1]);
+        atomicAdd(&A.lB[a * N + Xc], dba[0]);
+        atomicAdd(&A.lB[a * N + X], dba[1]);
+        atomicAdd(&A.lB[c * N + Xa], dbc[0]);
+        atomicAdd(&A.lB[c * N + X], dbc[1]);
         if (D.resistive) {  // + eta j from S^n
           const double j = (D.B0[c][X] - D.B0[c][Xa]) * D.hinv[a] - (D.B0[a][X] - D.B0[a][Xc]) * D.hinv[c];
           etaacc += lam * j;
@@ -906,21 +1061,31 @@ void launch_adj_fo(const AdjDev& A, const unsigned char* fl1, const unsigned cha
 
 // reverse sweeps of the PPM reconstructions along each direction (one launch per direction, so
 // that every output element has one writer per launch); kind FACE or edge values
-template <bool FACE>
+template <bool FACE, int EMF = EMF_Q26>
 static void rec_sweeps(const AdjDev& A, cudaStream_t st) {
   for (int s = 0; s < 3; ++s) {
     const int seg = 32;
-    const long long n = sweep_threads(A.D, s, seg) * (FACE ? 7 : 4);
-    k_adj_rec_sweep<FACE><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, s, seg);
+    const long long n = sweep_threads(A.D, s, seg) * (FACE ? 7 : (EMF == EMF_FS18 ? 10 : 4));
+    k_adj_rec_sweep<FACE, EMF><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, s, seg);
   }
+}
+
+template <int RC, int EMF>
+static void adj_edges_t(const AdjDev& A, cudaStream_t st) {
+  const unsigned nb = (unsigned)((A.D.N + 127) / 128);
+  k_adj_edges<RC, EMF><<<nb, 128, 0, st>>>(A);
+  if (RC == REC_PPM) rec_sweeps<false, EMF>(A, st);
+  else k_adj_edge_rec<RC, EMF><<<nb, 128, 0, st>>>(A);
 }
 
 template <int RC>
 static void adj_flux_r(const AdjDev& A, int rs, cudaStream_t st) {
   const unsigned nb = (unsigned)((A.D.N + 127) / 128);
-  k_adj_edges<RC><<<nb, 128, 0, st>>>(A);
-  if (RC == REC_PPM) rec_sweeps<false>(A, st);
-  else k_adj_edge_rec<RC><<<nb, 128, 0, st>>>(A);
+  // the face-state adjoints accumulate (FS18's edge reconstructions of the face velocity states
+  // add to them, then the face solve's reverse sweep)
+  cudaMemsetAsync(A.lLR, 0, 42 * A.D.N * sizeof(double), st);
+  if (A.D.emf == EMF_FS18) adj_edges_t<RC, EMF_FS18>(A, st);
+  else adj_edges_t<RC, EMF_Q26>(A, st);
   for (int dir = 0; dir < 3; ++dir) {
     if (rs == RS_HLL) k_adj_faces<RC, RS_HLL><<<nb, 128, 0, st>>>(A, dir);
     else if (rs == RS_HLLD) k_adj_faces<RC, RS_HLLD><<<nb, 128, 0, st>>>(A, dir);

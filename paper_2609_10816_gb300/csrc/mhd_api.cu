@@ -546,7 +546,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   Decoded sc;
   mhd_status s = decode(ctx, scheme, sc);
   if (s != MHD_OK) return s;
-  if (sc.emf != mhd::EMF_Q26) return fail(ctx, MHD_ERR_UNSUPPORTED, "the adjoint covers the Q26 EMF compute");
+  if (sc.emf == mhd::EMF_B25A) return fail(ctx, MHD_ERR_UNSUPPORTED, "the adjoint covers the Q26 and FS18 EMF compute");
   const long long N = ctx->base.N;
   cudaStream_t st = ctx->stream;
   // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
@@ -554,7 +554,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   // stage inputs 2 x 42, and their reconstructed edge values 12 + 2 x 12; for flux correction
   // D^T lam and the stage-1 flux adjoint 2 x 18, the stage-2 proposal 8 and the stage-1 flags
   // (doubles per cell) + eta
-  const size_t nd = 306;
+  const size_t nd = 402;
   if (!ctx->adj) {
     s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + (N + 7) / 8 + 8) * sizeof(double)),
                    "cudaMalloc of adjoint scratch");
@@ -567,7 +567,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* lAp = take(3);
   double* lAm = take(3);
   double* lUs = take(3);
-  double* lEdge = take(24);
+  double* lEdge = take(60);  // Q26 uses 24, FS18 60
   double* lLR = take(42);
   double* lP = take(8);
   double* lU1 = take(5);
@@ -581,8 +581,9 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* LR0 = take(42);
   double* LR1 = take(42);
   double* Epart0 = take(12);
-  double* EdgeC0 = take(12);
-  double* EdgeC1 = take(12);
+  double* EdgeC0 = take(30);  // Q26 uses 12, FS18 30
+  double* EdgeC1 = take(30);
+  double* Xpart0 = take(24);  // FS18: stage 1's a-then-c corner partials
   double* gF = take(15);  // g = D^T lam
   double* gE = take(3);
   double* kF = take(15);  // k: the adjoint of the stage-1 fluxes and EMFs
@@ -625,6 +626,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   D0.Us = Apm0 + 6 * N;
   D0.LR = LR0;  // the forward face and edge values, which the stage-1 adjoint reads
   D0.Epart = Epart0;
+  D0.Xpart = Xpart0;
   D0.EdgeC = EdgeC0;
   run_stage(ctx, D0, sc);
   // the stage-1 flags (none without flux correction: the flag pass then marks only cells that are

@@ -239,6 +239,14 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
       eRB = fma(-ua[1], bcR, uc[1] * baB);
       eLT = fma(-ua[2], bcL, uc[2] * baT);
       eRT = fma(-ua[3], bcR, uc[3] * baT);
+      if (D.EdgeC) {  // the left/right values, for the adjoint (b_c, then lo/hi of the 4 states)
+        double* ec = D.EdgeC + 10LL * e * N;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ec[(2 * v) * N + X] = lo[v];
+          ec[(2 * v + 1) * N + X] = hi[v];
+        }
+      }
     } else {
       // Eq. (b25a-average): a-then-c partials (eps L:B,T, eps R:B,T); c-then-a lo/hi[1] = B:(L,R),
       // [2] = T:(L,R)

@@ -56,8 +56,9 @@ struct Dev {
                   // stage's input, whose prim pass then runs only if flux correction changed it)
   double* LR;     // when set, the face sweep also stores its reconstructed left (7) and right (7)
                   // face states here, [3][14][N] (for the adjoint)
-  double* EdgeC;  // when set, the c-face edge sweep (Q26) also stores its reconstructed b_c and
-                  // u_c* left / right values here, [3][4][N] (for the adjoint)
+  double* EdgeC;  // when set, the c-face edge sweep also stores its reconstructed left / right
+                  // values here (for the adjoint): Q26 b_c and u_c*, [3][4][N]; FS18 b_c and the
+                  // four c-face velocity states, [3][10][N]
   unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
   // work-list cursors of the dynamically scheduled sweeps ([dir] face, [3 + e] edge_bt,
   // [6 + e] edge_lr), zeroed before every stage; NULL: one segment per thread, no cursor
@@ -76,8 +77,10 @@ struct AdjDev {
   double* lAp;          // [3][N] adjoint of alpha+ on faces
   double* lAm;          // [3][N] adjoint of alpha-
   double* lUs;          // [3][N] adjoint of the Q26 face velocity
-  double* lEdge;        // [3][8][N] adjoint of baB, baT, uaB, uaT, bcL, bcR, ucL, ucR per e-edge
-  double* lLR;          // [3][14][N] adjoint of the left (7) and right (7) face states
+  double* lEdge;        // adjoint of the reconstructed edge values per e-edge: Q26 [3][8][N] baB, baT,
+                        // uaB, uaT, bcL, bcR, ucL, ucR; FS18 [3][20][N] baB, baT, bcL, bcR, the 8
+                        // a-then-c velocity partials, the 8 c-then-a ones
+  double* lLR;          // [3][14][N] adjoint of the left (7) and right (7) face states (accumulated)
   double* lP;           // [8][N] adjoint of the primitives
   double* lU;           // [5][N] output: adjoint of the conserved variables (accumulated)
   double* lB;           // [3][N] output: adjoint of the face field (accumulated, atomics)

@@ -15,13 +15,17 @@ from paper_2609_10816_gb300 import adjoint, inputs, mhd
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("recon,rs", [("ppm", "hlld"), ("plm_mc", "hll"), ("plm_minmod", "llf"), ("pc", "hlld"),
-                                     ("ppm_ep", "hlld")])
+@pytest.mark.parametrize("recon,rs,emf", [("ppm", "hlld", "q26"), ("plm_mc", "hll", "q26"), ("plm_minmod", "llf", "q26"),
+                                         ("pc", "hlld", "q26"), ("ppm_ep", "hlld", "q26"), ("ppm", "hlld", "fs18"),
+                                         ("plm_mc", "hlld", "fs18"), ("ppm_ep", "hll", "fs18"), ("pc", "llf", "fs18")])
 @pytest.mark.parametrize("eta", [0.0, 3e-3])
 @pytest.mark.parametrize("shape", [(10, 8, 6), (7, 4, 2)])  # the second: windows wrap onto themselves
-def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta, shape):
+def test_one_step_adjoint_identity(gpu_lib, recon, rs, emf, eta, shape):
+    """<lam, J v> from the oracle's dual numbers equals <J^T lam, v> from the adjoint step (the
+    line sweeps of the PPM reverse and the point-wise reverse of the other reconstructions), for
+    the Q26 and FS18 EMF compute schemes."""
     cons, b, info = inputs.random_smooth(shape, seed=21, rough=0.02)
-    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf="q26", eta=eta)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf=emf, eta=eta)
     dt = oracle.max_dt(cfg, cons, b, 0.3)
     rng = np.random.default_rng(1)
     lc, lb = rng.normal(size=cons.shape), rng.normal(size=b.shape)
@@ -31,11 +35,11 @@ def test_one_step_adjoint_identity(gpu_lib, recon, rs, eta, shape):
     ctx = mhd.Context(shape, info["h"])
     st = mhd.to_device(cons, b)
     lam = mhd.to_device(lc, lb)
-    deta = ctx.step_adjoint(st, lam, dt, mhd.scheme(recon, rs, "q26"), eta)
+    deta = ctx.step_adjoint(st, lam, dt, mhd.scheme(recon, rs, emf), eta)
     torch.cuda.synchronize()
     rc, rb = lam.cons.cpu().numpy(), lam.b.cpu().numpy()
     rhs = (rc * vc).sum() + (rb * vb).sum() + deta * veta
-    print(f"ADJ {recon} {rs} eta={eta}: lhs {lhs:.15e} rhs {rhs:.15e} rel {abs(lhs - rhs) / abs(lhs):.2e}")
+    print(f"ADJ {recon} {rs} {emf} eta={eta}: lhs {lhs:.15e} rhs {rhs:.15e} rel {abs(lhs - rhs) / abs(lhs):.2e}")
     assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs((rc * vc).sum()) + abs((rb * vb).sum()) + 1e-300), (lhs, rhs)
     # the state is not modified by the adjoint
     assert np.array_equal(st.cons.cpu().numpy(), cons) and np.array_equal(st.b.cpu().numpy(), b)
@@ -61,8 +65,8 @@ def _shock_state(shape, seed, amp, p0):
 # (shape, seed, velocity amplitude, pressure, CFL, reconstruction): a few cells flagged after
 # stage 1; half the box flagged after stage 1 and a few cells after stage 2; a few cells after
 # each stage with PLM
-FOFC_CASES = [((10, 8, 6), 1, 0.3, 1e-2, 0.4, "ppm"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm"),
-              ((10, 8, 6), 4, 0.6, 1e-2, 0.6, "plm_mc")]
+FOFC_CASES = [((10, 8, 6), 1, 0.3, 1e-2, 0.4, "ppm", "q26"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm", "q26"),
+              ((10, 8, 6), 4, 0.6, 1e-2, 0.6, "plm_mc", "q26"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm", "fs18")]
 
 
 @pytest.mark.parametrize("case", range(len(FOFC_CASES)))
@@ -71,13 +75,13 @@ def test_flux_corrected_step_adjoint_identity(gpu_lib, case, eta):
     """Steps in which flux correction (Sec. 2.5) replaces fluxes with first-order ones, in stage 1
     and in stage 2: <lam, J v> from the oracle's dual numbers (the same flagged cells, taken from
     the values) equals <J^T lam, v> from the adjoint, to ~1e-10 relative."""
-    shape, seed, amp, p0, cfl, recon = FOFC_CASES[case]
+    shape, seed, amp, p0, cfl, recon, emf = FOFC_CASES[case]
     cons, b, info = _shock_state(shape, seed, amp, p0)
-    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann="hlld", emf="q26", eta=eta)
+    cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann="hlld", emf=emf, eta=eta)
     dt = oracle.max_dt(cfg, cons, b, cfl)
     _, _, cnt = oracle.step(cfg, cons, b, dt)
     assert cnt[0] > 0 and (case == 0 or cnt[1] > 0), cnt
-    sch = mhd.scheme(recon, "hlld", "q26")
+    sch = mhd.scheme(recon, "hlld", emf)
     ctx = mhd.Context(shape, info["h"])
     st = mhd.to_device(cons, b)
     ctx.step(mhd.to_device(cons, b), dt, sch, eta)
@@ -210,3 +214,17 @@ def test_reverse_sweep_of_face_solve_matches_dual_numbers(gpu_lib, rs):
     assert err20 <= 1e-6, kinds20
     for k in ("equal", "bn_zero", "large"):
         assert kinds20[k] <= 1e-12, (k, kinds20)
+
+
+def test_adjoint_refuses_b25a(gpu_lib):
+    """B25a's adjoint is not built: the call says so and leaves lam unchanged."""
+    shape = (8, 6, 4)
+    cons, b, info = inputs.random_smooth(shape, seed=5, rough=0.02)
+    ctx = mhd.Context(shape, info["h"])
+    st = mhd.to_device(cons, b)
+    lc, lb = np.ones_like(cons), np.ones_like(b)
+    lam = mhd.to_device(lc, lb)
+    with pytest.raises(mhd.MHDError):
+        ctx.step_adjoint(st, lam, 1e-3, mhd.scheme("ppm", "hlld", "b25a"), 0.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(lam.cons.cpu().numpy(), lc) and np.array_equal(lam.b.cpu().numpy(), lb)
