@@ -77,8 +77,8 @@ typedef struct mhd_ctx mhd_ctx; /* opaque: owns the scratch of one patch size an
 
 /* Create a context for one patch size. `cuda_stream` is a cudaStream_t (NULL = legacy default
  * stream); all work of the context is enqueued on it. Allocates the step's scratch
- * (112 doubles and one byte per cell, the FS18 / B25a intermediates included) with cudaMalloc on
- * the current device; the first mhd_step_adjoint adds 402 doubles per cell. *out is NULL on
+ * (109 doubles and one byte per cell, the FS18 / B25a intermediates included) with cudaMalloc on
+ * the current device; the first mhd_step_adjoint adds 414 doubles per cell. *out is NULL on
  * error. */
 mhd_status mhd_create(const mhd_config *cfg, void *cuda_stream, mhd_ctx **out);
 
@@ -156,9 +156,9 @@ mhd_status mhd_profile_read(mhd_ctx *ctx, double *total_ms, long long *launches,
  * stages are recomputed inside, up to the stage-2 flags). Flux correction (Sec. 2.5) is
  * differentiated with the cells it flagged held fixed: the first-order fluxes and EMFs of S^n on
  * the masked faces and edges get their share of the adjoint, the high-order ones the rest. The
- * paper has no counterpart; it makes the step usable inside gradient-based workflows. Covers the
- * Q26 and FS18 EMF compute schemes (B25a -> MHD_ERR_UNSUPPORTED); the first call allocates 402
- * doubles per cell of adjoint scratch. Synchronous when dL_deta is not NULL. */
+ * paper has no counterpart; it makes the step usable inside gradient-based workflows. Covers every
+ * EMF compute scheme (Q26, FS18, B25a); the first call allocates 414 doubles per cell of adjoint
+ * scratch. Synchronous when dL_deta is not NULL. */
 mhd_status mhd_step_adjoint(mhd_ctx *ctx, const mhd_state *state, const mhd_state *lam, double dt, int scheme,
                             double eta, double *dL_deta);
 

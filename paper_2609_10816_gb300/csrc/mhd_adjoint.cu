@@ -287,6 +287,29 @@ __device__ __forceinline__ void fs18_edge_vjp(const double* in, double lam, doub
   }
 }
 
+// Reverse sweep of the B25a corners (Eq. b25a-average: the mean of the two reconstruction orders
+// of the cell EMF) and their LD04 average. in: baB, baT, bcL, bcR, the a-then-c partials (eps
+// L:B,T, eps R:B,T), the c-then-a partials (eps B:L,R, eps T:L,R), then apa, ama, apc, amc (16
+// values); g (16) receives lam times the derivative in each.
+__device__ __forceinline__ void b25a_edge_vjp(const double* in, double lam, double* g) {
+  const double* xp = in + 4;
+  const double* lr = in + 8;
+  double e[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int sI = q & 1, sII = q >> 1;
+    e[q] = halve(xp[2 * sI + sII] + lr[2 * sII + sI]);
+  }
+  double de[4];
+  ld04_vjp(in[12], in[13], in[14], in[15], e, in[0], in[1], in[2], in[3], lam, de, g, g + 12);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int sI = q & 1, sII = q >> 1;
+    g[4 + 2 * sI + sII] = 0.5 * de[q];
+    g[8 + 2 * sII + sI] = 0.5 * de[q];
+  }
+}
+
 // ---- edges: adjoint of E_e from the 8 reconstructed edge values, the edge speeds, eta j ----
 template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
@@ -296,7 +319,7 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
   double etaacc = 0.0;
   for (int e = 0; e < 3 && X < N; ++e) {  // no early return: the whole warp sums d/d(eta) below
     const int a = (e + 1) % 3, c = (e + 2) % 3;
-    constexpr int NE = EMF == EMF_FS18 ? 20 : 8;  // adjoint slots per edge
+    constexpr int NE = EMF == EMF_FS18 ? 20 : (EMF == EMF_B25A ? 12 : 8);  // adjoint slots per edge
     const double lam = A.lE[e * N + X];
     if (lam == 0.0) {
       for (int k = 0; k < NE; ++k) A.lEdge[(NE * e + k) * N + X] = 0.0;
@@ -306,10 +329,22 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
     // the reconstructed edge values as the forward edge sweeps formed them. Q26: b_a, u_a* bottom
     // and top (Epart), b_c, u_c* left and right (EdgeC). FS18: b_a bottom and top (Epart), b_c
     // left and right, the a-then-c partials (Xpart) and the c-then-a ones (EdgeC).
-    constexpr int NI = EMF == EMF_FS18 ? 24 : 12;
+    constexpr int NI = EMF == EMF_FS18 ? 24 : (EMF == EMF_B25A ? 16 : 12);
     double in[NI];
     const double* pa = D.Epart + 4LL * e * N;
-    if (EMF == EMF_FS18) {
+    if (EMF == EMF_B25A) {  // b_a B/T, b_c L/R, the a-then-c EMF partials (Xpart), the c-then-a ones
+      const double* pc = D.EdgeC + 10LL * e * N;
+      const double* xp = D.Xpart + 8LL * e * N;
+      in[0] = pa[X];
+      in[1] = pa[N + X];
+      in[2] = pc[X];
+      in[3] = pc[N + X];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        in[4 + k] = xp[k * N + X];
+        in[8 + k] = pc[(2 + k) * N + X];
+      }
+    } else if (EMF == EMF_FS18) {
       const double* pc = D.EdgeC + 10LL * e * N;
       const double* xp = D.Xpart + 8LL * e * N;
       in[0] = pa[X];
@@ -342,6 +377,7 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
     in[NI - 1] = wc_m ? Amc[Xa] : Amc[X];
     double g[NI];
     if (EMF == EMF_FS18) fs18_edge_vjp(in, lam, g);
+    else if (EMF == EMF_B25A) b25a_edge_vjp(in, lam, g);
     else q26_edge_vjp(in, lam, g);
     for (int k = 0; k < NE; ++k) A.lEdge[(NE * e + k) * N + X] = g[k];
     atomicAdd(&A.lAp[a * N + (wa_p ? Xc : X)], g[NI - 4]);
@@ -381,7 +417,7 @@ __global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
   const long long X = aid();
   if (X >= D.N) return;
   const long long N = D.N;
-  constexpr int NE = EMF == EMF_FS18 ? 20 : 8;
+  constexpr int NE = EMF == EMF_FS18 ? 20 : (EMF == EMF_B25A ? 12 : 8);
   for (int d = 0; d < 3; ++d) {
     const int t1 = (d + 1) % 3, e1 = (d + 2) % 3;  // d is "a" of e1, reconstructed along c(e1) = t1
     const int t2 = (d + 2) % 3, e2 = (d + 1) % 3;  // d is "c" of e2, reconstructed along a(e2) = t2
@@ -390,7 +426,16 @@ __global__ void __launch_bounds__(128) k_adj_edge_rec(AdjDev A) {
     const long long X1 = shift(D, X, t1, 1), X2 = shift(D, X, t2, 1);
     // point X's lower value is the top (right) value at edge X, its upper value the bottom (left)
     // value at edge X + t
-    if (EMF == EMF_FS18) {
+    if (EMF == EMF_B25A) {  // b_d, and the e-EMF face values EfL (d = a of e1) and EfB (d = c of e2)
+      rec_scatter<RC>(D, D.Bin[d], X, t1, L1[1 * N + X], L1[0 * N + X1], A.lB + d * N);
+      rec_scatter<RC>(D, D.Bin[d], X, t2, L2[3 * N + X], L2[2 * N + X2], A.lB + d * N);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const long long r1 = (2LL * e1 + k) * N, r2 = (2LL * e2 + k) * N;
+        rec_scatter<RC>(D, D.EfL + r1, X, t1, L1[(5 + 2 * k) * N + X], L1[(4 + 2 * k) * N + X1], A.lEf + r1);
+        rec_scatter<RC>(D, D.EfB + r2, X, t2, L2[(9 + 2 * k) * N + X], L2[(8 + 2 * k) * N + X2], A.lEf + 6 * N + r2);
+      }
+    } else if (EMF == EMF_FS18) {
       rec_scatter<RC>(D, D.Bin[d], X, t1, L1[1 * N + X], L1[0 * N + X1], A.lB + d * N);
       rec_scatter<RC>(D, D.Bin[d], X, t2, L2[3 * N + X], L2[2 * N + X2], A.lB + d * N);
 #pragma unroll
@@ -507,6 +552,20 @@ __device__ __forceinline__ RecSrc face_src(const AdjDev& A, int s, int v) {
 template <int EMF>
 __device__ __forceinline__ RecSrc edge_src(const AdjDev& A, int s, int v) {
   const long long N = A.D.N;
+  if (EMF == EMF_B25A) {  // b_d and the e-EMF values EfL (bottom/top) or EfB (left/right)
+    const bool bt = v < 3;
+    const int d = bt ? (s + 2) % 3 : (s + 1) % 3;
+    const int e = bt ? (s + 1) % 3 : (s + 2) % 3;
+    const int k = bt ? v : v - 3;
+    const double* L = A.lEdge + 12LL * e * N;
+    if (k == 0) {
+      const int lo = bt ? 1 : 3;
+      return {A.D.Bin[d], L + lo * N, L + (lo - 1) * N, A.lB + d * N};
+    }
+    const long long row = (2LL * e + k - 1) * N;
+    const int lo = (bt ? 5 : 9) + 2 * (k - 1);
+    return {(bt ? A.D.EfL : A.D.EfB) + row, L + lo * N, L + (lo - 1) * N, A.lEf + (bt ? 0 : 6 * N) + row};
+  }
   if (EMF == EMF_FS18) {
     const bool bt = v < 5;
     const int d = bt ? (s + 2) % 3 : (s + 1) % 3;
@@ -530,19 +589,35 @@ __device__ __forceinline__ RecSrc edge_src(const AdjDev& A, int s, int v) {
   return {vel ? A.D.Us + d * N : A.D.Bin[d], L + lo * N, L + hi * N, (vel ? A.lUs : A.lB) + d * N};
 }
 
-// Reverse PPM sweeps along s over all sources of one kind: thread = (source, line segment).
-template <bool FACE, int EMF = EMF_Q26>
+// B25a's cell EMF eps_e reconstructed along s to faces (Eqs. b25a-b-avg, b25a-emf-centre): along
+// a for e = s - 1 (the EfL values, left / right), along c for e = s + 1 (the EfB values)
+__device__ __forceinline__ RecSrc eps_src(const AdjDev& A, int s, int v) {
+  const long long N = A.D.N;
+  const int e = v == 0 ? (s + 2) % 3 : (s + 1) % 3;
+  const double* lf = A.lEf + (v == 0 ? 0 : 6 * N) + 2LL * e * N;
+  // point Y's lower value is the right value at face Y, its upper value the left value at Y + s
+  return {A.eps + e * N, lf + N, lf, A.leps + e * N};
+}
+
+template <int KIND, int EMF>
+__device__ __forceinline__ int rec_sources() {
+  return KIND == 1 ? 7 : (KIND == 2 ? 2 : (EMF == EMF_FS18 ? 10 : (EMF == EMF_B25A ? 6 : 4)));
+}
+
+// Reverse PPM sweeps along s over all sources of one kind (0 edge values, 1 face states, 2 B25a's
+// cell EMF): thread = (source, line segment).
+template <int KIND, int EMF = EMF_Q26>
 __global__ void __launch_bounds__(128) k_adj_rec_sweep(AdjDev A, int s, int seg) {
   const Dev& D = A.D;
   const long long nsw = sweep_threads(D, s, seg);
   const long long tid = aid();
-  const int nsrc = FACE ? 7 : (EMF == EMF_FS18 ? 10 : 4);
+  const int nsrc = rec_sources<KIND, EMF>();
   if (tid >= nsw * nsrc) return;
   const int v = (int)(tid / nsw);
   Line ln;
   int m0, m1;
   if (!sweep_line_at(D, s, seg, tid - v * nsw, ln, m0, m1, s == 0)) return;
-  const RecSrc r = FACE ? face_src(A, s, v) : edge_src<EMF>(A, s, v);
+  const RecSrc r = KIND == 1 ? face_src(A, s, v) : (KIND == 2 ? eps_src(A, s, v) : edge_src<EMF>(A, s, v));
   RevPPM w;
   double v5[5];
 #pragma unroll
@@ -987,17 +1062,21 @@ __global__ void __launch_bounds__(128) k_adj_fo(AdjDev A, const unsigned char* f
         const double apa = pickB ? apaB : apaT, apc = pickL ? apcL : apcR;
         const double baB = D.B0[a][Xc], baT = D.B0[a][X], bcL = D.B0[c][Xa], bcR = D.B0[c][X];
         double dba[2], dbc[2], dapa, dapc, dua[2] = {0.0, 0.0}, duc[2] = {0.0, 0.0};
-        if (D.emf == EMF_FS18) {
-          // piecewise-constant FS18: corner q takes the velocity of the cell in that corner
-          // (LB = X-a-c, RB = X-c, LT = X-a, RT = X) and the face fields of the edge
+        if (D.emf != EMF_Q26) {
+          // piecewise-constant FS18 / B25a: corner q takes the velocity of the cell in that corner
+          // (LB = X-a-c, RB = X-c, LT = X-a, RT = X), and FS18 the face fields of the edge, B25a
+          // the cell's field (the mean of its two faces)
+          const bool b25 = D.emf == EMF_B25A;
           const long long cellQ[4] = {Xac, Xc, Xa, X};
-          double ua[4], uc[4], ri[4], e4[4];
+          double ua[4], uc[4], ri[4], e4[4], bas[4], bcs[4];
           for (int q = 0; q < 4; ++q) {
             const long long Q = cellQ[q];
             ri[q] = rcp(D.U0[Q]);
             ua[q] = D.U0[(1 + a) * N + Q] * ri[q];
             uc[q] = D.U0[(1 + c) * N + Q] * ri[q];
-            e4[q] = fma(-ua[q], (q & 1) ? bcR : bcL, uc[q] * ((q >> 1) ? baT : baB));
+            bcs[q] = b25 ? halve(D.B0[c][Q] + D.B0[c][shift(D, Q, c, 1)]) : ((q & 1) ? bcR : bcL);
+            bas[q] = b25 ? halve(D.B0[a][Q] + D.B0[a][shift(D, Q, a, 1)]) : ((q >> 1) ? baT : baB);
+            e4[q] = fma(-ua[q], bcs[q], uc[q] * bas[q]);
           }
           double de[4], db[4], dal[4];
           ld04_vjp(apa, apa, apc, apc, e4, baB, baT, bcL, bcR, lam, de, db, dal);
@@ -1006,10 +1085,17 @@ __global__ void __launch_bounds__(128) k_adj_fo(AdjDev A, const unsigned char* f
           dapc = dal[2] + dal[3];
           for (int q = 0; q < 4; ++q) {
             const long long Q = cellQ[q];
-            const double bcs = (q & 1) ? bcR : bcL, bas = (q >> 1) ? baT : baB;
-            const double dva = -de[q] * bcs, dvc = de[q] * bas;
-            dbc[q & 1] -= de[q] * ua[q];
-            dba[q >> 1] += de[q] * uc[q];
+            const double dva = -de[q] * bcs[q], dvc = de[q] * bas[q];
+            if (b25) {  // the cell field b_k = (B_k[Q] + B_k[Q + k]) / 2
+              const double hc = -0.5 * de[q] * ua[q], ha = 0.5 * de[q] * uc[q];
+              atomicAdd(&A.lB[c * N + Q], hc);
+              atomicAdd(&A.lB[c * N + shift(D, Q, c, 1)], hc);
+              atomicAdd(&A.lB[a * N + Q], ha);
+              atomicAdd(&A.lB[a * N + shift(D, Q, a, 1)], ha);
+            } else {
+              dbc[q & 1] -= de[q] * ua[q];
+              dba[q >> 1] += de[q] * uc[q];
+            }
             // u = m / rho
             atomicAdd(&A.lU[(1 + a) * N + Q], dva * ri[q]);
             atomicAdd(&A.lU[(1 + c) * N + Q], dvc * ri[q]);
@@ -1061,21 +1147,76 @@ void launch_adj_fo(const AdjDev& A, const unsigned char* fl1, const unsigned cha
 
 // reverse sweeps of the PPM reconstructions along each direction (one launch per direction, so
 // that every output element has one writer per launch); kind FACE or edge values
-template <bool FACE, int EMF = EMF_Q26>
+template <int KIND, int EMF = EMF_Q26>
 static void rec_sweeps(const AdjDev& A, cudaStream_t st) {
+  const int nsrc = KIND == 1 ? 7 : (KIND == 2 ? 2 : (EMF == EMF_FS18 ? 10 : (EMF == EMF_B25A ? 6 : 4)));
   for (int s = 0; s < 3; ++s) {
     const int seg = 32;
-    const long long n = sweep_threads(A.D, s, seg) * (FACE ? 7 : (EMF == EMF_FS18 ? 10 : 4));
-    k_adj_rec_sweep<FACE, EMF><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, s, seg);
+    const long long n = sweep_threads(A.D, s, seg) * nsrc;
+    k_adj_rec_sweep<KIND, EMF><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, s, seg);
+  }
+}
+
+// B25a: the cell EMF of the stage input, eps_e = -u_a b_c + u_c b_a from its primitives (as the
+// forward cell-to-face sweeps form it)
+__global__ void __launch_bounds__(256) k_adj_eps_prep(AdjDev A) {
+  const long long X = aid();
+  const Dev& D = A.D;
+  if (X >= D.N) return;
+  const long long N = D.N;
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, c = (e + 2) % 3;
+    A.eps[e * N + X] = fma(-D.P[(1 + a) * N + X], D.P[(5 + c) * N + X], D.P[(1 + c) * N + X] * D.P[(5 + a) * N + X]);
+  }
+}
+// point-wise reverse of the cell-EMF reconstructions (PC, PLM, PPM-EP)
+template <int RC>
+__global__ void __launch_bounds__(128) k_adj_eps_rec(AdjDev A) {
+  const Dev& D = A.D;
+  const long long X = aid();
+  if (X >= D.N) return;
+  const long long N = D.N;
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, c = (e + 2) % 3;
+    const double* lfL = A.lEf + 2LL * e * N;
+    const double* lfB = A.lEf + 6 * N + 2LL * e * N;
+    rec_scatter<RC>(D, A.eps + e * N, X, a, lfL[N + X], lfL[shift(D, X, a, 1)], A.leps + e * N);
+    rec_scatter<RC>(D, A.eps + e * N, X, c, lfB[N + X], lfB[shift(D, X, c, 1)], A.leps + e * N);
+  }
+}
+// the cell EMF's adjoint into the primitives' (one thread per cell, no other writer meanwhile)
+__global__ void __launch_bounds__(256) k_adj_eps_to_prim(AdjDev A) {
+  const long long X = aid();
+  const Dev& D = A.D;
+  if (X >= D.N) return;
+  const long long N = D.N;
+  for (int e = 0; e < 3; ++e) {
+    const int a = (e + 1) % 3, c = (e + 2) % 3;
+    const double l = A.leps[e * N + X];
+    if (l == 0.0) continue;
+    A.lP[(1 + a) * N + X] -= l * D.P[(5 + c) * N + X];
+    A.lP[(5 + c) * N + X] -= l * D.P[(1 + a) * N + X];
+    A.lP[(1 + c) * N + X] += l * D.P[(5 + a) * N + X];
+    A.lP[(5 + a) * N + X] += l * D.P[(1 + c) * N + X];
   }
 }
 
 template <int RC, int EMF>
 static void adj_edges_t(const AdjDev& A, cudaStream_t st) {
-  const unsigned nb = (unsigned)((A.D.N + 127) / 128);
+  const unsigned nb = (unsigned)((A.D.N + 127) / 128), nb256 = (unsigned)((A.D.N + 255) / 256);
+  if (EMF == EMF_B25A) {
+    cudaMemsetAsync(A.lEf, 0, 12 * A.D.N * sizeof(double), st);
+    cudaMemsetAsync(A.leps, 0, 3 * A.D.N * sizeof(double), st);
+    k_adj_eps_prep<<<nb256, 256, 0, st>>>(A);
+  }
   k_adj_edges<RC, EMF><<<nb, 128, 0, st>>>(A);
-  if (RC == REC_PPM) rec_sweeps<false, EMF>(A, st);
+  if (RC == REC_PPM) rec_sweeps<0, EMF>(A, st);
   else k_adj_edge_rec<RC, EMF><<<nb, 128, 0, st>>>(A);
+  if (EMF == EMF_B25A) {  // the face EMF values back to the cell EMF, then to the primitives
+    if (RC == REC_PPM) rec_sweeps<2>(A, st);
+    else k_adj_eps_rec<RC><<<nb, 128, 0, st>>>(A);
+    k_adj_eps_to_prim<<<nb256, 256, 0, st>>>(A);
+  }
 }
 
 template <int RC>
@@ -1085,6 +1226,7 @@ static void adj_flux_r(const AdjDev& A, int rs, cudaStream_t st) {
   // add to them, then the face solve's reverse sweep)
   cudaMemsetAsync(A.lLR, 0, 42 * A.D.N * sizeof(double), st);
   if (A.D.emf == EMF_FS18) adj_edges_t<RC, EMF_FS18>(A, st);
+  else if (A.D.emf == EMF_B25A) adj_edges_t<RC, EMF_B25A>(A, st);
   else adj_edges_t<RC, EMF_Q26>(A, st);
   for (int dir = 0; dir < 3; ++dir) {
     if (rs == RS_HLL) k_adj_faces<RC, RS_HLL><<<nb, 128, 0, st>>>(A, dir);
@@ -1092,7 +1234,7 @@ static void adj_flux_r(const AdjDev& A, int rs, cudaStream_t st) {
     else k_adj_faces<RC, RS_LLF><<<nb, 128, 0, st>>>(A, dir);
     if (A.D.resistive) k_adj_joule<<<nb, 128, 0, st>>>(A, dir);
   }
-  if (RC == REC_PPM) rec_sweeps<true>(A, st);
+  if (RC == REC_PPM) rec_sweeps<1>(A, st);
   else k_adj_face_rec<RC><<<nb, 128, 0, st>>>(A);
   k_adj_prim<<<nb, 128, 0, st>>>(A);
 }

@@ -201,8 +201,8 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   D.gm1inv = 1.0 / (cfg->gamma - 1.0);
   D.fofc_criteria = cfg->fofc_criteria ? cfg->fofc_criteria : 3;
   // scratch, in doubles per cell: U1 5, B1 3, P 8, F 15, Ap/Am/Us 9, Epart 12, E 3,
-  // VL/VR 18, Xpart 24, Ec 3, EfL 6, EfB 6  -> 112; + flags (1 byte) + counters
-  const size_t nd = 112;
+  // VL/VR 18, Xpart 24, EfL 6, EfB 6  -> 109; + flags (1 byte) + counters
+  const size_t nd = 109;
   const size_t bytes = nd * sizeof(double) * (size_t)N + (size_t)N + 256 + 64 + 128;
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
@@ -227,7 +227,6 @@ mhd_status mhd_create(const mhd_config* cfg, void* cuda_stream, mhd_ctx** out) {
   D.VL = take(9);
   D.VR = take(9);
   D.Xpart = take(24);
-  D.Ec = take(3);
   D.EfL = take(6);
   D.EfB = take(6);
   D.counters = (unsigned long long*)q;  // 8 counters, then the sweeps' work cursors
@@ -546,15 +545,14 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   Decoded sc;
   mhd_status s = decode(ctx, scheme, sc);
   if (s != MHD_OK) return s;
-  if (sc.emf == mhd::EMF_B25A) return fail(ctx, MHD_ERR_UNSUPPORTED, "the adjoint covers the Q26 and FS18 EMF compute");
   const long long N = ctx->base.N;
   cudaStream_t st = ctx->stream;
   // adjoint scratch: lF 15, lE 3, lAp/lAm/lUs 9, lEdge 24, lLR 42, lP 8, lU1 5, lB1 3, lU0 5,
   // lB0 3, lam2 8, the stage-1 input's P 8 and alpha+- / u* 9, the forward face states of both
-  // stage inputs 2 x 42, and their reconstructed edge values 12 + 2 x 12; for flux correction
-  // D^T lam and the stage-1 flux adjoint 2 x 18, the stage-2 proposal 8 and the stage-1 flags
-  // (doubles per cell) + eta
-  const size_t nd = 402;
+  // stage inputs 2 x 42, and their reconstructed edge values 12 + 2 x 30 + 24, B25a's face EMF
+  // values of the stage-1 input 12; for flux correction D^T lam and the stage-1 flux adjoint
+  // 2 x 18, the stage-2 proposal 8 and the stage-1 flags (doubles per cell) + eta
+  const size_t nd = 414;
   if (!ctx->adj) {
     s = cuda_check(ctx, cudaMalloc(&ctx->adj, (nd * N + (N + 7) / 8 + 8) * sizeof(double)),
                    "cudaMalloc of adjoint scratch");
@@ -567,7 +565,7 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* lAp = take(3);
   double* lAm = take(3);
   double* lUs = take(3);
-  double* lEdge = take(60);  // Q26 uses 24, FS18 60
+  double* lEdge = take(60);  // Q26 uses 24, FS18 60, B25a 36 (+ 18 for its face and cell EMF adjoints)
   double* lLR = take(42);
   double* lP = take(8);
   double* lU1 = take(5);
@@ -583,7 +581,8 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   double* Epart0 = take(12);
   double* EdgeC0 = take(30);  // Q26 uses 12, FS18 30
   double* EdgeC1 = take(30);
-  double* Xpart0 = take(24);  // FS18: stage 1's a-then-c corner partials
+  double* Xpart0 = take(24);  // FS18 / B25a: stage 1's a-then-c corner partials
+  double* Ef0 = take(12);     // B25a: stage 1's face EMF values (EfL, then EfB)
   double* gF = take(15);  // g = D^T lam
   double* gE = take(3);
   double* kF = take(15);  // k: the adjoint of the stage-1 fluxes and EMFs
@@ -627,6 +626,8 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
   D0.LR = LR0;  // the forward face and edge values, which the stage-1 adjoint reads
   D0.Epart = Epart0;
   D0.Xpart = Xpart0;
+  D0.EfL = Ef0;
+  D0.EfB = Ef0 + 6 * N;
   D0.EdgeC = EdgeC0;
   run_stage(ctx, D0, sc);
   // the stage-1 flags (none without flux correction: the flag pass then marks only cells that are
@@ -640,6 +641,8 @@ mhd_status mhd_step_adjoint(mhd_ctx* ctx, const mhd_state* state, const mhd_stat
     A.D = Ds;
     A.lF = lF; A.lE = lE; A.lAp = lAp; A.lAm = lAm; A.lUs = lUs; A.lEdge = lEdge; A.lLR = lLR; A.lP = lP;
     A.lU = lU; A.lB = lB; A.lEta = lEta;
+    // B25a: the face EMF adjoints, the cell EMF and its adjoint in lEdge's last 24 rows
+    A.lEf = lEdge + 36 * N; A.eps = lEdge + 48 * N; A.leps = lEdge + 51 * N;
     return A;
   };
   auto recompute = [&](const mhd::Dev& Ds) {  // P, alpha+-, u*, face and edge values of the stage input

@@ -262,6 +262,14 @@ __device__ __forceinline__ void edge_lr_seg(const Dev& D, int e, const Line& ln,
       eRB = ec[1];
       eLT = ec[2];
       eRT = ec[3];
+      if (D.EdgeC) {  // the left/right values, for the adjoint (b_c, then lo/hi of the 2 EMF values)
+        double* es = D.EdgeC + 10LL * e * N;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          es[(2 * v) * N + X] = lo[v];
+          es[(2 * v + 1) * N + X] = hi[v];
+        }
+      }
     }
     if (EMF != EMF_Q26) emf = ld04(apa, ama, apc, amc, eLB, eRB, eLT, eRT, baB, baT, bcL, bcR);
     if (D.resistive) {

@@ -48,7 +48,6 @@ struct Dev {
   double* VL;     // [3][3][N] FS18: left velocity states on d-faces, component k
   double* VR;     // [3][3][N]
   double* Xpart;  // [3][8][N] FS18/B25a per e-edge corner partials of the a-faces sweep
-  double* Ec;     // [3][N] B25a cell-centred EMF of the stage input
   double* EfL;    // [3][2][N] B25a e-EMF on a-faces (L/R) for order (a then c)
   double* EfB;    // [3][2][N] B25a e-EMF on c-faces (B/T) for order (c then a)
   unsigned char* flag;         // [N]
@@ -58,7 +57,8 @@ struct Dev {
                   // face states here, [3][14][N] (for the adjoint)
   double* EdgeC;  // when set, the c-face edge sweep also stores its reconstructed left / right
                   // values here (for the adjoint): Q26 b_c and u_c*, [3][4][N]; FS18 b_c and the
-                  // four c-face velocity states, [3][10][N]
+                  // four c-face velocity states, [3][10][N]; B25a b_c and the two c-face EMF
+                  // values, in the first 6 of [3][10][N]
   unsigned long long* counters;  // [0] stage-1 flagged cells, [1] stage-2, [2..3] reductions
   // work-list cursors of the dynamically scheduled sweeps ([dir] face, [3 + e] edge_bt,
   // [6 + e] edge_lr), zeroed before every stage; NULL: one segment per thread, no cursor
@@ -79,7 +79,11 @@ struct AdjDev {
   double* lUs;          // [3][N] adjoint of the Q26 face velocity
   double* lEdge;        // adjoint of the reconstructed edge values per e-edge: Q26 [3][8][N] baB, baT,
                         // uaB, uaT, bcL, bcR, ucL, ucR; FS18 [3][20][N] baB, baT, bcL, bcR, the 8
-                        // a-then-c velocity partials, the 8 c-then-a ones
+                        // a-then-c velocity partials, the 8 c-then-a ones; B25a [3][12][N] baB, baT,
+                        // bcL, bcR, the 4 a-then-c EMF partials, the 4 c-then-a ones
+  double* lEf;          // B25a: [2][3][2][N] adjoint of the face EMF values (EfL, then EfB)
+  double* eps;          // B25a: [3][N] the cell-centred EMF of the stage input (formed here)
+  double* leps;         // B25a: [3][N] its adjoint
   double* lLR;          // [3][14][N] adjoint of the left (7) and right (7) face states (accumulated)
   double* lP;           // [8][N] adjoint of the primitives
   double* lU;           // [5][N] output: adjoint of the conserved variables (accumulated)

@@ -17,13 +17,15 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("recon,rs,emf", [("ppm", "hlld", "q26"), ("plm_mc", "hll", "q26"), ("plm_minmod", "llf", "q26"),
                                          ("pc", "hlld", "q26"), ("ppm_ep", "hlld", "q26"), ("ppm", "hlld", "fs18"),
-                                         ("plm_mc", "hlld", "fs18"), ("ppm_ep", "hll", "fs18"), ("pc", "llf", "fs18")])
+                                         ("plm_mc", "hlld", "fs18"), ("ppm_ep", "hll", "fs18"), ("pc", "llf", "fs18"),
+                                         ("ppm", "hlld", "b25a"), ("plm_mc", "hll", "b25a"), ("ppm_ep", "hlld", "b25a"),
+                                         ("pc", "llf", "b25a")])
 @pytest.mark.parametrize("eta", [0.0, 3e-3])
 @pytest.mark.parametrize("shape", [(10, 8, 6), (7, 4, 2)])  # the second: windows wrap onto themselves
 def test_one_step_adjoint_identity(gpu_lib, recon, rs, emf, eta, shape):
     """<lam, J v> from the oracle's dual numbers equals <J^T lam, v> from the adjoint step (the
     line sweeps of the PPM reverse and the point-wise reverse of the other reconstructions), for
-    the Q26 and FS18 EMF compute schemes."""
+    the Q26, FS18 and B25a EMF compute schemes."""
     cons, b, info = inputs.random_smooth(shape, seed=21, rough=0.02)
     cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf=emf, eta=eta)
     dt = oracle.max_dt(cfg, cons, b, 0.3)
@@ -62,11 +64,13 @@ def _shock_state(shape, seed, amp, p0):
     return inputs.assemble(rho, u, p, b), b, info
 
 
-# (shape, seed, velocity amplitude, pressure, CFL, reconstruction): a few cells flagged after
-# stage 1; half the box flagged after stage 1 and a few cells after stage 2; a few cells after
-# each stage with PLM
+# (shape, seed, velocity amplitude, pressure, CFL, reconstruction, EMF compute): a few cells
+# flagged after stage 1; half the box flagged after stage 1 and a few cells after stage 2; a few
+# cells after each stage with PLM; the second again with FS18 and B25a, and PLM with B25a
+# (their first-order corners take the cell velocities, and B25a's the cell fields)
 FOFC_CASES = [((10, 8, 6), 1, 0.3, 1e-2, 0.4, "ppm", "q26"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm", "q26"),
-              ((10, 8, 6), 4, 0.6, 1e-2, 0.6, "plm_mc", "q26"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm", "fs18")]
+              ((10, 8, 6), 4, 0.6, 1e-2, 0.6, "plm_mc", "q26"), ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm", "fs18"),
+              ((10, 8, 6), 4, 3.0, 1e-3, 0.3, "ppm", "b25a"), ((10, 8, 6), 3, 1.0, 1e-2, 0.6, "plm_mc", "b25a")]
 
 
 @pytest.mark.parametrize("case", range(len(FOFC_CASES)))
@@ -214,17 +218,3 @@ def test_reverse_sweep_of_face_solve_matches_dual_numbers(gpu_lib, rs):
     assert err20 <= 1e-6, kinds20
     for k in ("equal", "bn_zero", "large"):
         assert kinds20[k] <= 1e-12, (k, kinds20)
-
-
-def test_adjoint_refuses_b25a(gpu_lib):
-    """B25a's adjoint is not built: the call says so and leaves lam unchanged."""
-    shape = (8, 6, 4)
-    cons, b, info = inputs.random_smooth(shape, seed=5, rough=0.02)
-    ctx = mhd.Context(shape, info["h"])
-    st = mhd.to_device(cons, b)
-    lc, lb = np.ones_like(cons), np.ones_like(b)
-    lam = mhd.to_device(lc, lb)
-    with pytest.raises(mhd.MHDError):
-        ctx.step_adjoint(st, lam, 1e-3, mhd.scheme("ppm", "hlld", "b25a"), 0.0)
-    torch.cuda.synchronize()
-    assert np.array_equal(lam.cons.cpu().numpy(), lc) and np.array_equal(lam.b.cpu().numpy(), lb)
