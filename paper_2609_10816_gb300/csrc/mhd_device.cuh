@@ -585,37 +585,38 @@ __device__ __forceinline__ FaceStateT<T> pick(bool left, const FaceStateT<T>& a,
   return r;
 }
 
-// Miyoshi & Kusano (2005) HLLD without the Minoshima fixes. The face x/t = 0 lies on the side of
-// the contact given by sgn(S_M); only that side's star state is formed, and the other side's star
+// Miyoshi & Kusano (2005) HLLD without the Minoshima fixes. Outside the fan (S_L > 0 or S_R < 0)
+// the flux is that side's physical flux; inside it the face x/t = 0 lies on the side of the
+// contact given by sgn(S_M), and only that side's star state is formed, and the other side's star
 // state and the double-star state (MK05 Eqs. 49-63) only when the face lies inside that side's
-// rotational wave. Same values as forming all four states and selecting.
+// rotational wave. Same values as forming all four states and selecting. The side is chosen before
+// the one physical flux vector a face needs is formed, so that the lanes of a warp on either side
+// of the fan or inside it form it together.
 template <class T>
 __device__ __forceinline__ void hlld(const FaceStateT<T>& sl, const FaceStateT<T>& sr, T bn, double gm1inv,
-                                     PhysFluxT<T>& L, PhysFluxT<T>& R, T SL, T SR, T* F) {
-  // the flux vectors are formed only for the side(s) the face needs
-  if (gt0(SL)) {
-    phys_flux(sl, bn, gm1inv, L);
-    for (int v = 0; v < 5; ++v) F[v] = L.F[v];
-    return;
+                                     const PhysFluxT<T>& L, const PhysFluxT<T>& R, T SL, T SR, T* F) {
+  const bool supL = gt0(SL);
+  const bool fan = !supL && !lt0(SR);
+  T mL = 0.0, mR = 0.0, SM = 0.0, ptS = 0.0;
+  if (fan) {
+    mL = (SL - sl.u) * sl.rho;  // mass fluxes through the outer waves
+    mR = (SR - sr.u) * sr.rho;
+    const T dinv = rcp(mR - mL);
+    SM = ((mR * sr.u - mL * sl.u) + (L.pt - R.pt)) * dinv;  // MK05 Eq. 38
+    ptS = (mR * L.pt - mL * R.pt + mL * mR * (sr.u - sl.u)) * dinv;  // MK05 Eq. 41
   }
-  if (lt0(SR)) {
-    phys_flux(sr, bn, gm1inv, R);
-    for (int v = 0; v < 5; ++v) F[v] = R.F[v];
-    return;
-  }
-  const T sluL = SL - sl.u, sruR = SR - sr.u;
-  const T mL = sluL * sl.rho, mR = sruR * sr.rho;  // mass fluxes through the outer waves
-  const T dinv = rcp(mR - mL);
-  const T SM = ((mR * sr.u - mL * sl.u) + (L.pt - R.pt)) * dinv;  // MK05 Eq. 38
-  const T ptS = (mR * L.pt - mL * R.pt + mL * mR * (sr.u - sl.u)) * dinv;  // MK05 Eq. 41
-  const T bn2 = bn * bn;
-  const T abn = vabs(bn);
-  const bool left = ge0(SM);
+  const bool left = fan ? ge0(SM) : supL;
   const FaceStateT<T> q = pick(left, sl, sr);
   PhysFluxT<T> P;
   P.b2 = left ? L.b2 : R.b2;
   P.pt = left ? L.pt : R.pt;
   phys_flux(q, bn, gm1inv, P);
+  if (!fan) {
+    for (int v = 0; v < 5; ++v) F[v] = P.F[v];
+    return;
+  }
+  const T bn2 = bn * bn;
+  const T abn = vabs(bn);
   const T S = left ? SL : SR;
   StarT<T> a;
   star_state(q, P, S, SM, ptS, bn, bn2, a);
@@ -690,7 +691,7 @@ __device__ __forceinline__ void riemann(const FaceStateT<T>& sl, const FaceState
   const bool zero = is_zero(sum);
   const T inv = zero ? 0.0 : rcp(sum);
   if (RS == RS_HLLD) {
-    hlld(sl, sr, bn, gm1inv, L, R, SL, SR, F);
+    hlld(sl, sr, bn, gm1inv, L, R, SL, SR, F);  // (reads L, R's pt and b2 only)
   } else {
     phys_flux(sl, bn, gm1inv, L);
     phys_flux(sr, bn, gm1inv, R);
