@@ -656,6 +656,8 @@ def main():
     # what a binary64 multiply on the integer pipe adds (not used by the step's kernels)
     fp64_probe.update({k: mhd.fp64_rate(k, 1 << 13, stream) for k in ("int_mul", "dfma_int_mul",
                                                                       "dfma_int_mul_2x128")})
+    # DFMA on 16 and 8 lanes of each warp: what FP64 work in a divergent branch costs
+    fp64_probe.update({k: mhd.fp64_rate(k, 1 << 13, stream) for k in ("dfma_16_lanes", "dfma_8_lanes")})
     fp64_peak_tflops = 2.0 * fp64_probe["dfma"] / 1e12
 
     # ---- device-resident timed region ------------------------------------------------------

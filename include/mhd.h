@@ -186,9 +186,11 @@ mhd_status mhd_math_check(mhd_ctx *ctx, long long n, double *max_rel_err);
  * thread-lane). Kinds 4-6 measure a binary64 multiply done on the integer pipe (bit for bit the
  * FP64 multiply; mhd_math_check verifies it) that the step's kernels do not use: 4 eight chains
  * of it, 5 four chains of it beside four DFMA chains, 6 the same mix at 2 blocks of 128 threads
- * per SM (the face sweep's occupancy); *ops_per_s counts the operations of all chains.
+ * per SM (the face sweep's occupancy); *ops_per_s counts the operations of all chains. Kinds 7
+ * and 8 run the DFMA chains on 16 and 8 lanes of every warp (the other lanes exit at once) and
+ * count the active lanes' operations only: the cost of FP64 work in a divergent branch.
  * Synchronous; allocates 8 bytes of device memory for the duration of the call.
- * MHD_ERR_ARG for a kind outside 0-6 or iters outside [1, 2^30]. */
+ * MHD_ERR_ARG for a kind outside 0-8 or iters outside [1, 2^30]. */
 mhd_status mhd_fp64_rate(int kind, long long iters, void *cuda_stream, double *ops_per_s);
 
 /* Self-check of the adjoint's reverse sweep through the face solve (the Riemann solver of

@@ -8,7 +8,9 @@
 // times them with CUDA events on the context's stream. The chains stay bounded (x <- a x + b with
 // 0 < a < 1), and their sum is stored so that nothing is optimised away. Kinds 4-6 run chains of
 // the integer-pipe multiply (mhd_softmul.cuh), alone and mixed with DFMA chains, at the probe's
-// occupancy and at the face sweep's (2 blocks of 128 threads per SM).
+// occupancy and at the face sweep's (2 blocks of 128 threads per SM). Kinds 7 and 8 run the DFMA
+// chains on 16 and 8 lanes of every warp (the others exit at once): whether the pipe's throughput
+// in lane operations falls with the active lanes tells what a divergent branch of FP64 work costs.
 #include <cstring>
 
 #include "../../include/mhd.h"
@@ -20,9 +22,11 @@ namespace mhd {
 constexpr int kChains = 8;
 
 // KIND 0-3: kChains chains of DFMA, DADD, DMUL or FP32 FFMA; KIND 4: NI chains of the
-// integer-pipe multiply and NF chains of DFMA
+// integer-pipe multiply and NF chains of DFMA; KIND 5: kChains chains of DFMA on the first NF
+// lanes of each warp
 template <int KIND, int NF = 0, int NI = 0>
 __global__ void __launch_bounds__(256) k_rate(long long iters, double a, double b, double* out) {
+  if (KIND == 5 && (int)(threadIdx.x & 31) >= NF) return;
   double x[kChains], z[NI > 0 ? NI : 1];
   float y[kChains];
 #pragma unroll
@@ -42,7 +46,7 @@ __global__ void __launch_bounds__(256) k_rate(long long iters, double a, double 
     } else {
 #pragma unroll
       for (int c = 0; c < kChains; ++c) {
-        if (KIND == 0) x[c] = fma(x[c], a, b);      // DFMA
+        if (KIND == 0 || KIND == 5) x[c] = fma(x[c], a, b);  // DFMA
         else if (KIND == 1) x[c] = x[c] + b;          // DADD
         else if (KIND == 2) x[c] = x[c] * a;          // DMUL
         else y[c] = fmaf(y[c], af, bf);               // FFMA (FP32, for comparison)
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(256) k_rate(long long iters, double a, double 
 }  // namespace mhd
 
 extern "C" mhd_status mhd_fp64_rate(int kind, long long iters, void* cuda_stream, double* ops_per_s) {
-  if (kind < 0 || kind > 6 || iters < 1 || iters > (1LL << 30) || !ops_per_s) return MHD_ERR_ARG;
+  if (kind < 0 || kind > 8 || iters < 1 || iters > (1LL << 30) || !ops_per_s) return MHD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
@@ -90,6 +94,8 @@ extern "C" mhd_status mhd_fp64_rate(int kind, long long iters, void* cuda_stream
       case 2: mhd::k_rate<2><<<grid, threads, 0, st>>>(n, a, b, out); break;
       case 3: mhd::k_rate<3><<<grid, threads, 0, st>>>(n, a, b, out); break;
       case 4: mhd::k_rate<4, 0, 8><<<grid, threads, 0, st>>>(n, a, b, out); break;
+      case 7: mhd::k_rate<5, 16><<<grid, threads, 0, st>>>(n, a, b, out); break;
+      case 8: mhd::k_rate<5, 8><<<grid, threads, 0, st>>>(n, a, b, out); break;
       default: mhd::k_rate<4, 4, 4><<<grid, threads, 0, st>>>(n, a, b, out); break;
     }
   };
@@ -105,6 +111,8 @@ extern "C" mhd_status mhd_fp64_rate(int kind, long long iters, void* cuda_stream
   cudaEventDestroy(e1);
   cudaFree(out);
   if (e != cudaSuccess || !(ms > 0.f)) return MHD_ERR_CUDA;
-  *ops_per_s = (double)grid * (double)threads * (double)chains * (double)iters / (ms * 1e-3);
+  // operations of the active lanes only
+  const double lanes = kind == 7 ? 0.5 : (kind == 8 ? 0.25 : 1.0);
+  *ops_per_s = (double)grid * (double)threads * lanes * (double)chains * (double)iters / (ms * 1e-3);
   return MHD_OK;
 }

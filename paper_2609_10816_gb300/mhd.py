@@ -130,7 +130,7 @@ def lib():
 
 
 FP64_RATE_KINDS = {"dfma": 0, "dadd": 1, "dmul": 2, "ffma": 3, "int_mul": 4, "dfma_int_mul": 5,
-                   "dfma_int_mul_2x128": 6}
+                   "dfma_int_mul_2x128": 6, "dfma_16_lanes": 7, "dfma_8_lanes": 8}
 
 
 def fp64_rate(kind: str = "dfma", iters: int = 1 << 14, stream: torch.cuda.Stream | None = None) -> float:

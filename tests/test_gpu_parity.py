@@ -345,13 +345,17 @@ def test_fp64_rate_probe(gpu_lib):
                                                                         "dfma_int_mul_2x128")}
     print("integer-pipe multiply", {k: f"{v:.2f}/SM/clk" for k, v in mixed.items()})
     assert all(0.2 <= v <= 8.0 for v in mixed.values()), mixed
+    # DFMA on 16 and 8 lanes per warp: the active lanes' operations at no more than the full rate
+    part = {k: mhd.fp64_rate(k, 1 << 12) / rates["dfma"] for k in ("dfma_16_lanes", "dfma_8_lanes")}
+    print("DFMA on part of the warp, of the full-warp rate", {k: f"{v:.3f}" for k, v in part.items()})
+    assert all(0.05 <= v <= 1.2 for v in part.values()), part
     with pytest.raises(mhd.MHDError):
         mhd.fp64_rate("dfma", 0)
     with pytest.raises(mhd.MHDError):
         lib = mhd.lib()
         import ctypes
         out = ctypes.c_double()
-        rc = lib.mhd_fp64_rate(7, 1 << 10, None, ctypes.byref(out))
+        rc = lib.mhd_fp64_rate(9, 1 << 10, None, ctypes.byref(out))
         if rc != mhd.OK:
-            raise mhd.MHDError(rc, "kind 7")
+            raise mhd.MHDError(rc, "kind 9")
 
