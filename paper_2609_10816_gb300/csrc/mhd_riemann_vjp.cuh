@@ -192,203 +192,207 @@ __device__ __forceinline__ void add_side(bool left, FaceState& dl, FaceState& dr
 }
 
 // Reverse sweep of hlld(): dF in; accumulates into dsl, dsr, dbn, the adjoints of the two sides'
-// b2 / pt (dLb2, dLpt, dRb2, dRpt) and of SL, SR.
+// b2 / pt (dLb2, dLpt, dRb2, dRpt) and of SL, SR. As in hlld, the side is chosen first, so that
+// the one physical flux vector and its reverse are formed by every lane together (outside the fan
+// the flux is that vector; inside it the star states' reverse comes first).
 __device__ __forceinline__ void hlld_rev(const FaceState& sl, const FaceState& sr, double bn, double gm1inv,
                                          const PhysFlux& Lsp, const PhysFlux& Rsp, double SL, double SR,
                                          const double* dF, FaceState& dsl, FaceState& dsr, double& dbn,
                                          double& dLb2, double& dLpt, double& dRb2, double& dRpt, double& dSL,
                                          double& dSR) {
-  const double zero5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (gt0(SL) || lt0(SR)) {  // the face lies outside the fan: F = the flux of one side
-    const bool lside = gt0(SL);
-    PhysFlux P = lside ? Lsp : Rsp;
-    phys_flux(lside ? sl : sr, bn, gm1inv, P);
-    FaceState d = {0, 0, 0, 0, 0, 0, 0};
-    double db2 = 0.0, dpt = 0.0;
-    phys_flux_rev(lside ? sl : sr, bn, gm1inv, P, zero5, dF, 0.0, d, dbn, db2, dpt);
-    add_side(lside, dsl, dsr, d);
-    (lside ? dLb2 : dRb2) += db2;
-    (lside ? dLpt : dRpt) += dpt;
-    return;
-  }
   // ---- forward values (as in hlld) ----
-  const double sluL = SL - sl.u, sruR = SR - sr.u;
-  const double mL = sluL * sl.rho, mR = sruR * sr.rho;
-  const double dinv = rcp(mR - mL);
-  const double nSM = (mR * sr.u - mL * sl.u) + (Lsp.pt - Rsp.pt);
-  const double SM = nSM * dinv;
-  const double nPT = mR * Lsp.pt - mL * Rsp.pt + mL * mR * (sr.u - sl.u);
-  const double ptS = nPT * dinv;
-  const double bn2 = bn * bn;
-  const double abn = vabs(bn);
-  const bool left = ge0(SM);
+  const bool supL = gt0(SL);
+  const bool fan = !supL && !lt0(SR);
+  double sluL = 0.0, sruR = 0.0, mL = 0.0, mR = 0.0, dinv = 0.0, nSM = 0.0, SM = 0.0, nPT = 0.0, ptS = 0.0;
+  if (fan) {
+    sluL = SL - sl.u;
+    sruR = SR - sr.u;
+    mL = sluL * sl.rho;
+    mR = sruR * sr.rho;
+    dinv = rcp(mR - mL);
+    nSM = (mR * sr.u - mL * sl.u) + (Lsp.pt - Rsp.pt);
+    SM = nSM * dinv;
+    nPT = mR * Lsp.pt - mL * Rsp.pt + mL * mR * (sr.u - sl.u);
+    ptS = nPT * dinv;
+  }
+  const bool left = fan ? ge0(SM) : supL;
   const FaceState q = pick(left, sl, sr);
   PhysFlux P;
   P.b2 = left ? Lsp.b2 : Rsp.b2;
   P.pt = left ? Lsp.pt : Rsp.pt;
   phys_flux(q, bn, gm1inv, P);
-  const double S = left ? SL : SR;
-  StarT<double> a;
-  star_state(q, P, S, SM, ptS, bn, bn2, a);
-  const double isqa = rsqrt_(a.rs);
-  const double Ss = left ? SM - abn * isqa : SM + abn * isqa;
-  const double Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
-  const bool dstar = hlld_in_rotational(left, SM, a.rs, bn2);
-
-  // ---- reverse ----
-  double dFs[5], dUsa[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int v = 0; v < 5; ++v) dFs[v] = dF[v];
-  double dSM = 0.0, dptS = 0.0, dbn2 = 0.0, dS = 0.0, dSs = 0.0, disqa = 0.0;
-  StarAdj da = {0, 0, 0, 0, 0, 0};
-  FaceState dq = {0, 0, 0, 0, 0, 0, 0};
-  double dPe = 0.0, dPpt = 0.0;
-  if (dstar) {
-    const FaceState qo = pick(!left, sl, sr);
-    const double So = left ? SR : SL;
-    StarT<double> b;
-    star_state<double, false>(qo, P, So, SM, ptS, bn, bn2, b);
-    const double isqb = rsqrt_(b.rs);
-    const StarT<double>& sL = left ? a : b;
-    const StarT<double>& sR = left ? b : a;
-    const double iL = left ? isqa : isqb, iR = left ? isqb : isqa;
-    const double sqL = sL.rs * iL, sqR = sR.rs * iR;
-    const double sb = sgnd(bn);
-    const double inv = rcp(sqL + sqR);
-    const double nv = fma(sqL, sL.vs, fma(sqR, sR.vs, (sR.bys - sL.bys) * sb));
-    const double nw = fma(sqL, sL.ws, fma(sqR, sR.ws, (sR.bzs - sL.bzs) * sb));
-    const double sLR = sqL * sqR;
-    const double nby = fma(sqL, sR.bys, fma(sqR, sL.bys, sLR * (sR.vs - sL.vs) * sb));
-    const double nbz = fma(sqL, sR.bzs, fma(sqR, sL.bzs, sLR * (sR.ws - sL.ws) * sb));
-    const double vss = nv * inv, wss = nw * inv, byss = nby * inv, bzss = nbz * inv;
-    const double vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
-    const double sq = left ? sqL : sqR;
-    const double sgn_side = left ? -1.0 : 1.0;
-    const double vbs = fma(SM, bn, fma(a.vs, a.bys, a.ws * a.bzs));
-    double Uss[5];
-    Uss[0] = a.rs;
-    Uss[1] = a.rs * SM;
-    Uss[2] = a.rs * vss;
-    Uss[3] = a.rs * wss;
-    Uss[4] = fma(sgn_side * sq, (vbs - vbss) * sb, a.es);
-    // F = Ss (Uss - Usa) + Fs
-    double dUss[5];
-    for (int v = 0; v < 5; ++v) {
-      dSs += dF[v] * (Uss[v] - Usa[v]);
-      dUss[v] = Ss * dF[v];
-      dUsa[v] -= Ss * dF[v];
-    }
-    // Uss
-    da.rs += dUss[0] + dUss[1] * SM + dUss[2] * vss + dUss[3] * wss;
-    dSM += dUss[1] * a.rs;
-    double dvss = dUss[2] * a.rs, dwss = dUss[3] * a.rs;
-    da.es += dUss[4];
-    const double dsq = dUss[4] * sgn_side * (vbs - vbss) * sb;
-    const double dvbs = dUss[4] * sgn_side * sq * sb, dvbss = -dvbs;
-    // vbs = SM bn + a.vs a.bys + a.ws a.bzs
-    dSM += dvbs * bn;
-    dbn += dvbs * SM;
-    da.vs += dvbs * a.bys;
-    da.bys += dvbs * a.vs;
-    da.ws += dvbs * a.bzs;
-    da.bzs += dvbs * a.ws;
-    // vbss = SM bn + vss byss + wss bzss
-    dSM += dvbss * bn;
-    dbn += dvbss * SM;
-    dvss += dvbss * byss;
-    const double dbyss = dvbss * vss;
-    dwss += dvbss * bzss;
-    const double dbzss = dvbss * wss;
-    // the four double-star values: X = nX inv
-    const double dnv = dvss * inv, dnw = dwss * inv, dnby = dbyss * inv, dnbz = dbzss * inv;
-    const double dinv2 = dvss * nv + dwss * nw + dbyss * nby + dbzss * nbz;
-    StarAdj dL = {0, 0, 0, 0, 0, 0}, dR = {0, 0, 0, 0, 0, 0};
-    double dsqL = 0.0, dsqR = 0.0, dsLR = 0.0;
-    if (left) dsqL += dsq; else dsqR += dsq;
-    // nv = sqL vsL + sqR vsR + (bysR - bysL) sb
-    dsqL += dnv * sL.vs;
-    dL.vs += dnv * sqL;
-    dsqR += dnv * sR.vs;
-    dR.vs += dnv * sqR;
-    dR.bys += dnv * sb;
-    dL.bys -= dnv * sb;
-    // nw
-    dsqL += dnw * sL.ws;
-    dL.ws += dnw * sqL;
-    dsqR += dnw * sR.ws;
-    dR.ws += dnw * sqR;
-    dR.bzs += dnw * sb;
-    dL.bzs -= dnw * sb;
-    // nby = sqL bysR + sqR bysL + sLR (vsR - vsL) sb
-    dsqL += dnby * sR.bys;
-    dR.bys += dnby * sqL;
-    dsqR += dnby * sL.bys;
-    dL.bys += dnby * sqR;
-    dsLR += dnby * (sR.vs - sL.vs) * sb;
-    dR.vs += dnby * sLR * sb;
-    dL.vs -= dnby * sLR * sb;
-    // nbz
-    dsqL += dnbz * sR.bzs;
-    dR.bzs += dnbz * sqL;
-    dsqR += dnbz * sL.bzs;
-    dL.bzs += dnbz * sqR;
-    dsLR += dnbz * (sR.ws - sL.ws) * sb;
-    dR.ws += dnbz * sLR * sb;
-    dL.ws -= dnbz * sLR * sb;
-    // sLR = sqL sqR; inv = 1/(sqL + sqR)
-    dsqL += dsLR * sqR;
-    dsqR += dsLR * sqL;
-    const double dsum = -dinv2 * inv * inv;
-    dsqL += dsum;
-    dsqR += dsum;
-    // sq = rs i, i = rsqrt(rs)
-    double diL = dsqL * sL.rs, diR = dsqR * sR.rs;
-    dL.rs += dsqL * iL;
-    dR.rs += dsqR * iR;
-    // back to sides a (this side) and b (the other)
-    StarAdj& dA_ = left ? dL : dR;
-    StarAdj& dB_ = left ? dR : dL;
-    const double diA = left ? diL : diR, diB = left ? diR : diL;
-    da.rs += dA_.rs;
-    da.vs += dA_.vs;
-    da.ws += dA_.ws;
-    da.bys += dA_.bys;
-    da.bzs += dA_.bzs;
-    disqa += diA;
-    StarAdj db = dB_;
-    db.es = 0.0;
-    db.rs += diB * (-0.5 * isqb * isqb * isqb);
-    // b = star_state(qo, ., So, SM, ptS, bn, bn2) without its energy (db.es = 0, so neither the
-    // side's flux vectors nor its pt enter)
-    FaceState dqo = {0, 0, 0, 0, 0, 0, 0};
-    double dPoe = 0.0, dPopt = 0.0, dSo = 0.0;
-    star_state_rev(qo, P, So, SM, ptS, bn, bn2, b, db, dqo, dPoe, dPopt, dSo, dSM, dptS, dbn, dbn2);
-    add_side(!left, dsl, dsr, dqo);
-    if (left) dSR += dSo; else dSL += dSo;
-  }
-  // Ss = SM -/+ |bn| isqa
-  dSM += dSs;
-  if (left) { dbn -= dSs * isqa * sgnd(bn); disqa -= dSs * abn; }
-  else { dbn += dSs * isqa * sgnd(bn); disqa += dSs * abn; }
-  // Fs = S (Usa - P.U) + P.F
-  double dPU[5];
+  // the adjoints of the flux vector's inputs: outside the fan F = P.F
+  double dFs[5], dPU[5];
   for (int v = 0; v < 5; ++v) {
-    dS += dFs[v] * (Usa[v] - P.U[v]);
-    dUsa[v] += S * dFs[v];
-    dPU[v] = -S * dFs[v];
+    dFs[v] = dF[v];
+    dPU[v] = 0.0;
   }
-  // Usa = (rs, rs SM, rs vs, rs ws, es)
-  da.rs += dUsa[0] + dUsa[1] * SM + dUsa[2] * a.vs + dUsa[3] * a.ws;
-  dSM += dUsa[1] * a.rs;
-  da.vs += dUsa[2] * a.rs;
-  da.ws += dUsa[3] * a.rs;
-  da.es += dUsa[4];
-  // isqa = rsqrt(a.rs)
-  da.rs += disqa * (-0.5 * isqa * isqa * isqa);
-  star_state_rev(q, P, S, SM, ptS, bn, bn2, a, da, dq, dPe, dPpt, dS, dSM, dptS, dbn, dbn2);
+  FaceState dq = {0, 0, 0, 0, 0, 0, 0};
+  double dPe = 0.0, dPpt = 0.0, dSM = 0.0, dptS = 0.0, dbn2 = 0.0, dS = 0.0;
+  if (fan) {
+    const double bn2 = bn * bn;
+    const double abn = vabs(bn);
+    const double S = left ? SL : SR;
+    StarT<double> a;
+    star_state(q, P, S, SM, ptS, bn, bn2, a);
+    const double isqa = rsqrt_(a.rs);
+    const double Ss = left ? SM - abn * isqa : SM + abn * isqa;
+    const double Usa[5] = {a.rs, a.rs * SM, a.rs * a.vs, a.rs * a.ws, a.es};
+    const bool dstar = hlld_in_rotational(left, SM, a.rs, bn2);
+
+    // ---- reverse ----
+    double dUsa[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double dSs = 0.0, disqa = 0.0;
+    StarAdj da = {0, 0, 0, 0, 0, 0};
+    if (dstar) {
+      const FaceState qo = pick(!left, sl, sr);
+      const double So = left ? SR : SL;
+      StarT<double> b;
+      star_state<double, false>(qo, P, So, SM, ptS, bn, bn2, b);
+      const double isqb = rsqrt_(b.rs);
+      const StarT<double>& sL = left ? a : b;
+      const StarT<double>& sR = left ? b : a;
+      const double iL = left ? isqa : isqb, iR = left ? isqb : isqa;
+      const double sqL = sL.rs * iL, sqR = sR.rs * iR;
+      const double sb = sgnd(bn);
+      const double inv = rcp(sqL + sqR);
+      const double nv = fma(sqL, sL.vs, fma(sqR, sR.vs, (sR.bys - sL.bys) * sb));
+      const double nw = fma(sqL, sL.ws, fma(sqR, sR.ws, (sR.bzs - sL.bzs) * sb));
+      const double sLR = sqL * sqR;
+      const double nby = fma(sqL, sR.bys, fma(sqR, sL.bys, sLR * (sR.vs - sL.vs) * sb));
+      const double nbz = fma(sqL, sR.bzs, fma(sqR, sL.bzs, sLR * (sR.ws - sL.ws) * sb));
+      const double vss = nv * inv, wss = nw * inv, byss = nby * inv, bzss = nbz * inv;
+      const double vbss = fma(SM, bn, fma(vss, byss, wss * bzss));
+      const double sq = left ? sqL : sqR;
+      const double sgn_side = left ? -1.0 : 1.0;
+      const double vbs = fma(SM, bn, fma(a.vs, a.bys, a.ws * a.bzs));
+      double Uss[5];
+      Uss[0] = a.rs;
+      Uss[1] = a.rs * SM;
+      Uss[2] = a.rs * vss;
+      Uss[3] = a.rs * wss;
+      Uss[4] = fma(sgn_side * sq, (vbs - vbss) * sb, a.es);
+      // F = Ss (Uss - Usa) + Fs
+      double dUss[5];
+      for (int v = 0; v < 5; ++v) {
+        dSs += dF[v] * (Uss[v] - Usa[v]);
+        dUss[v] = Ss * dF[v];
+        dUsa[v] -= Ss * dF[v];
+      }
+      // Uss
+      da.rs += dUss[0] + dUss[1] * SM + dUss[2] * vss + dUss[3] * wss;
+      dSM += dUss[1] * a.rs;
+      double dvss = dUss[2] * a.rs, dwss = dUss[3] * a.rs;
+      da.es += dUss[4];
+      const double dsq = dUss[4] * sgn_side * (vbs - vbss) * sb;
+      const double dvbs = dUss[4] * sgn_side * sq * sb, dvbss = -dvbs;
+      // vbs = SM bn + a.vs a.bys + a.ws a.bzs
+      dSM += dvbs * bn;
+      dbn += dvbs * SM;
+      da.vs += dvbs * a.bys;
+      da.bys += dvbs * a.vs;
+      da.ws += dvbs * a.bzs;
+      da.bzs += dvbs * a.ws;
+      // vbss = SM bn + vss byss + wss bzss
+      dSM += dvbss * bn;
+      dbn += dvbss * SM;
+      dvss += dvbss * byss;
+      const double dbyss = dvbss * vss;
+      dwss += dvbss * bzss;
+      const double dbzss = dvbss * wss;
+      // the four double-star values: X = nX inv
+      const double dnv = dvss * inv, dnw = dwss * inv, dnby = dbyss * inv, dnbz = dbzss * inv;
+      const double dinv2 = dvss * nv + dwss * nw + dbyss * nby + dbzss * nbz;
+      StarAdj dL = {0, 0, 0, 0, 0, 0}, dR = {0, 0, 0, 0, 0, 0};
+      double dsqL = 0.0, dsqR = 0.0, dsLR = 0.0;
+      if (left) dsqL += dsq; else dsqR += dsq;
+      // nv = sqL vsL + sqR vsR + (bysR - bysL) sb
+      dsqL += dnv * sL.vs;
+      dL.vs += dnv * sqL;
+      dsqR += dnv * sR.vs;
+      dR.vs += dnv * sqR;
+      dR.bys += dnv * sb;
+      dL.bys -= dnv * sb;
+      // nw
+      dsqL += dnw * sL.ws;
+      dL.ws += dnw * sqL;
+      dsqR += dnw * sR.ws;
+      dR.ws += dnw * sqR;
+      dR.bzs += dnw * sb;
+      dL.bzs -= dnw * sb;
+      // nby = sqL bysR + sqR bysL + sLR (vsR - vsL) sb
+      dsqL += dnby * sR.bys;
+      dR.bys += dnby * sqL;
+      dsqR += dnby * sL.bys;
+      dL.bys += dnby * sqR;
+      dsLR += dnby * (sR.vs - sL.vs) * sb;
+      dR.vs += dnby * sLR * sb;
+      dL.vs -= dnby * sLR * sb;
+      // nbz
+      dsqL += dnbz * sR.bzs;
+      dR.bzs += dnbz * sqL;
+      dsqR += dnbz * sL.bzs;
+      dL.bzs += dnbz * sqR;
+      dsLR += dnbz * (sR.ws - sL.ws) * sb;
+      dR.ws += dnbz * sLR * sb;
+      dL.ws -= dnbz * sLR * sb;
+      // sLR = sqL sqR; inv = 1/(sqL + sqR)
+      dsqL += dsLR * sqR;
+      dsqR += dsLR * sqL;
+      const double dsum = -dinv2 * inv * inv;
+      dsqL += dsum;
+      dsqR += dsum;
+      // sq = rs i, i = rsqrt(rs)
+      double diL = dsqL * sL.rs, diR = dsqR * sR.rs;
+      dL.rs += dsqL * iL;
+      dR.rs += dsqR * iR;
+      // back to sides a (this side) and b (the other)
+      StarAdj& dA_ = left ? dL : dR;
+      StarAdj& dB_ = left ? dR : dL;
+      const double diA = left ? diL : diR, diB = left ? diR : diL;
+      da.rs += dA_.rs;
+      da.vs += dA_.vs;
+      da.ws += dA_.ws;
+      da.bys += dA_.bys;
+      da.bzs += dA_.bzs;
+      disqa += diA;
+      StarAdj db = dB_;
+      db.es = 0.0;
+      db.rs += diB * (-0.5 * isqb * isqb * isqb);
+      // b = star_state(qo, ., So, SM, ptS, bn, bn2) without its energy (db.es = 0, so neither the
+      // side's flux vectors nor its pt enter)
+      FaceState dqo = {0, 0, 0, 0, 0, 0, 0};
+      double dPoe = 0.0, dPopt = 0.0, dSo = 0.0;
+      star_state_rev(qo, P, So, SM, ptS, bn, bn2, b, db, dqo, dPoe, dPopt, dSo, dSM, dptS, dbn, dbn2);
+      add_side(!left, dsl, dsr, dqo);
+      if (left) dSR += dSo; else dSL += dSo;
+    }
+    // Ss = SM -/+ |bn| isqa
+    dSM += dSs;
+    if (left) { dbn -= dSs * isqa * sgnd(bn); disqa -= dSs * abn; }
+    else { dbn += dSs * isqa * sgnd(bn); disqa += dSs * abn; }
+    // Fs = S (Usa - P.U) + P.F
+    for (int v = 0; v < 5; ++v) {
+      dS += dFs[v] * (Usa[v] - P.U[v]);
+      dUsa[v] += S * dFs[v];
+      dPU[v] = -S * dFs[v];
+    }
+    // Usa = (rs, rs SM, rs vs, rs ws, es)
+    da.rs += dUsa[0] + dUsa[1] * SM + dUsa[2] * a.vs + dUsa[3] * a.ws;
+    dSM += dUsa[1] * a.rs;
+    da.vs += dUsa[2] * a.rs;
+    da.ws += dUsa[3] * a.rs;
+    da.es += dUsa[4];
+    // isqa = rsqrt(a.rs)
+    da.rs += disqa * (-0.5 * isqa * isqa * isqa);
+    star_state_rev(q, P, S, SM, ptS, bn, bn2, a, da, dq, dPe, dPpt, dS, dSM, dptS, dbn, dbn2);
+  }
   double db2 = 0.0, dpt = dPpt;
   phys_flux_rev(q, bn, gm1inv, P, dPU, dFs, dPe, dq, dbn, db2, dpt);
   add_side(left, dsl, dsr, dq);
-  if (left) { dLb2 += db2; dLpt += dpt; dSL += dS; } else { dRb2 += db2; dRpt += dpt; dSR += dS; }
+  if (left) { dLb2 += db2; dLpt += dpt; } else { dRb2 += db2; dRpt += dpt; }
+  if (!fan) return;
+  if (left) dSL += dS; else dSR += dS;
   dbn += 2.0 * bn * dbn2;
   // SM = nSM dinv, ptS = nPT dinv, dinv = 1/(mR - mL)
   const double dnSM = dSM * dinv, dnPT = dptS * dinv;
