@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(128, MHD_FACE_MINB) k_face(Dev D, int dir, int
 // The three face sweeps of a stage as one persistent launch: the segments of the x, y and z
 // sweeps form one work list behind one cursor, so that the grid drains one tail per stage instead
 // of one per direction (a warp takes 32 segments of up to 64 faces at a time, and the last ones
-// run while the other SMs idle).
+// run while the other SMs idle). A warp's 32 segments lie on an 8 x 4 patch of lines where the box
+// allows (sweep_line_at), so that its lanes take the same Riemann-fan branch more often.
 template <int RC, int RS>
 __global__ void __launch_bounds__(128, MHD_FACE_MINB) k_faces(Dev D, int s0, int s1, int s2) {
   const long long t0 = sweep_threads(D, 0, s0), t1 = sweep_threads(D, 1, s1), t2 = sweep_threads(D, 2, s2);
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(128, MHD_FACE_MINB) k_faces(Dev D, int s0, int
     }
     Line ln;
     int m0, m1;
-    if (sweep_line_at(D, dir, seg, t, ln, m0, m1)) face_seg<RC, RS>(D, dir, ln, m0, m1);
+    if (sweep_line_at(D, dir, seg, t, ln, m0, m1, false, true)) face_seg<RC, RS>(D, dir, ln, m0, m1);
   });
 }
 

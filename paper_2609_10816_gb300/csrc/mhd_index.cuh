@@ -47,16 +47,26 @@ __host__ __device__ inline long long sweep_threads(const Dev& D, int dir, int se
 // with seg_fastest the segments of one line take consecutive numbers instead, so that
 // neighbouring threads walk neighbouring stretches of the same line (for sweeps along x, whose
 // neighbouring lines lie nx apart: one thread per line would stream a separate cache line per
-// thread and array).
+// thread and array). With `tiled` (and the two line axes multiples of 8 and 4), each 32 threads
+// from a multiple of 32 walk an 8 x 4 patch of lines instead of a row of 32: the faces a warp
+// solves together then lie within 8 cells of each other, not 32, and fall more often in the
+// same branch of the solver.
 __device__ __forceinline__ bool sweep_line_at(const Dev& D, int dir, int seg, long long tid, Line& ln, int& m0,
-                                              int& m1, bool seg_fastest = false) {
+                                              int& m1, bool seg_fastest = false, bool tiled = false) {
   int t1, t2;
   sweep_axes(dir, t1, t2);
   const int n1 = D.n[t1], n2 = D.n[t2], nd = D.n[dir];
   const int nseg = (nd + seg - 1) / seg;
   if (tid >= (long long)n1 * n2 * nseg) return false;
   int i1, i2, s;
-  if (seg_fastest) {
+  if (tiled && !seg_fastest && (n1 & 7) == 0 && (n2 & 3) == 0) {
+    const long long per = (long long)n1 * n2;  // lines: a multiple of 32
+    s = (int)(tid / per);
+    const long long r = tid - (long long)s * per;
+    const int w = (int)(r >> 5), l = (int)(r & 31), p1 = n1 >> 3;
+    i1 = (w % p1) * 8 + (l & 7);
+    i2 = (w / p1) * 4 + (l >> 3);
+  } else if (seg_fastest) {
     s = (int)(tid % nseg);
     const long long r = tid / nseg;
     i1 = (int)(r % n1);
