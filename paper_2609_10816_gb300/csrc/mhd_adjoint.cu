@@ -680,8 +680,9 @@ __device__ __forceinline__ void riemann_grad_rev(const double* WL, const double*
 template <int RC, int RS>
 __global__ void __launch_bounds__(128) k_adj_faces(AdjDev A, int dir) {
   const Dev& D = A.D;
-  const long long f = aid();
-  if (f >= D.N) return;
+  const long long t = aid();
+  if (t >= D.N) return;
+  const long long f = tiled_cell(D, t);  // a warp's faces on an 8 x 4 patch: fewer divergent fan branches
   const long long N = D.N;
   const int a = (dir + 1) % 3, c = (dir + 2) % 3;
   // the face states as the forward sweep reconstructed them (stored by its recompute)

@@ -121,7 +121,8 @@ __device__ __forceinline__ void sweep_phase(const BatchDev& B, unsigned long lon
     const bool xl = EDGE && dirs[j] == 0;
     Line ln;
     int m0, m1;
-    if (sweep_line_at(D, dirs[j], xl ? edge_sweep_seg(D, 0, B.seg) : B.seg, t - pref[j][k], ln, m0, m1, xl))
+    // (warps on 8 x 4 patches of lines, as in the single-box sweeps)
+    if (sweep_line_at(D, dirs[j], xl ? edge_sweep_seg(D, 0, B.seg) : B.seg, t - pref[j][k], ln, m0, m1, xl, !xl))
       fn(D, j, ln, m0, m1);
   });
 }

@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(128) k_edge_lr(Dev D, int e, int seg) {
 
 // The three edge sweeps of one kind (LR: lines along a = e + 1, else along c = e + 2) as one
 // persistent launch: the segments of the e = 0, 1, 2 sweeps form one work list behind one cursor,
-// so that the grid drains one tail instead of three.
+// so that the grid drains one tail instead of three. Along y and z a warp's segments lie on an
+// 8 x 4 patch of lines where the box allows (sweep_line_at).
 template <int RC, int EMF, bool LR>
 __global__ void __launch_bounds__(128) k_edges(Dev D, int s0, int s1, int s2) {
   const int sg[3] = {s0, s1, s2};
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(128) k_edges(Dev D, int s0, int s1, int s2) {
     const int dir = LR ? (e + 1) % 3 : (e + 2) % 3;
     Line ln;
     int m0, m1;
-    if (sweep_line_at(D, dir, sg[e], t, ln, m0, m1, dir == 0)) {
+    if (sweep_line_at(D, dir, sg[e], t, ln, m0, m1, dir == 0, dir != 0)) {
       if (LR) edge_lr_seg<RC, EMF>(D, e, ln, m0, m1);
       else edge_bt_seg<RC, EMF>(D, e, ln, m0, m1);
     }

@@ -85,6 +85,19 @@ __device__ __forceinline__ bool sweep_line_at(const Dev& D, int dir, int seg, lo
   return true;
 }
 
+// cell of thread t of a per-cell kernel, with each 32 threads from a multiple of 32 on an 8 x 4
+// patch of an x-y plane (when nx and ny are multiples of 8 and 4; else cell t), so that a warp's
+// cells lie within 8 cells of each other
+__device__ __forceinline__ long long tiled_cell(const Dev& D, long long t) {
+  if ((D.n[0] & 7) || (D.n[1] & 3)) return t;
+  const long long per = (long long)D.n[0] * D.n[1];
+  const long long z = t / per;
+  const long long r = t - z * per;
+  const int w = (int)(r >> 5), l = (int)(r & 31), p = D.n[0] >> 3;
+  const int x = (w % p) * 8 + (l & 7), y = (w / p) * 4 + (l >> 3);
+  return z * per + (long long)y * D.n[0] + x;
+}
+
 __device__ __forceinline__ bool sweep_line(const Dev& D, int dir, int seg, Line& ln, int& m0, int& m1,
                                            bool seg_fastest = false) {
   return sweep_line_at(D, dir, seg, (long long)blockIdx.x * blockDim.x + threadIdx.x, ln, m0, m1, seg_fastest);
