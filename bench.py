@@ -45,7 +45,7 @@ ALG_BYTES_PER_CELL_UPDATE = 320  # stage 1: 64 B in + 64 B out; stage 2: 128 B i
 # DRAM traffic of one face-sweep launch (the x, y and z sweeps of a stage; mean of a stage-1 and a
 # stage-2 launch) from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources it was taken on.
-TRAFFIC = {"face": {"bytes_per_launch": 2309.1e6, "cells": 160**3, "src": "43406666ee4fff87"}}
+TRAFFIC = {"face": {"bytes_per_launch": 2305.9e6, "cells": 160**3, "src": "cf90455b07c49ff7"}}
 
 
 # what the face sweep's machine code is compiled from: its kernel, the numerics and indexing
