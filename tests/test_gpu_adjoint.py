@@ -21,7 +21,9 @@ pytestmark = pytest.mark.gpu
                                          ("ppm", "hlld", "b25a"), ("plm_mc", "hll", "b25a"), ("ppm_ep", "hlld", "b25a"),
                                          ("pc", "llf", "b25a")])
 @pytest.mark.parametrize("eta", [0.0, 3e-3])
-@pytest.mark.parametrize("shape", [(10, 8, 6), (7, 4, 2)])  # the second: windows wrap onto themselves
+# the second: windows wrap onto themselves; the third: the reverse face solve's warps on 8 x 4
+# patches of an x-y plane
+@pytest.mark.parametrize("shape", [(10, 8, 6), (7, 4, 2), (16, 8, 6)])
 def test_one_step_adjoint_identity(gpu_lib, recon, rs, emf, eta, shape):
     """<lam, J v> from the oracle's dual numbers equals <J^T lam, v> from the adjoint step (the
     line sweeps of the PPM reverse and the point-wise reverse of the other reconstructions), for

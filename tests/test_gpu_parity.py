@@ -48,6 +48,23 @@ def test_one_step_all_schemes(gpu_lib, recon, rs, emf, shape):
     assert cntg == cnt
 
 
+@pytest.mark.parametrize("shape", [(42, 16, 12), (16, 8, 42), (24, 12, 8)])
+def test_warp_patches_of_lines(gpu_lib, shape):
+    """Sweeps whose warps walk 8 x 4 patches of lines (both line axes multiples of 8 and 4) beside
+    sweeps that cannot (42 cells), with ragged segment tails along 42 cells and several patches per
+    plane: one step against the oracle for each EMF compute scheme, flagged-cell counts equal."""
+    cons, b, info = inputs.random_smooth(shape, seed=13, rough=0.05)
+    for recon, rs, emf in (("ppm", "hlld", "q26"), ("ppm_ep", "hlld", "fs18"), ("plm_mc", "hll", "b25a"),
+                           ("ppm", "llf", "q26")):
+        cfg = oracle.Config(shape=shape, h=info["h"], recon=recon, riemann=rs, emf=emf, eta=1e-3)
+        dt = oracle.max_dt(cfg, cons, b, 0.3)
+        co, bo, cnt = oracle.step(cfg, cons, b, dt)
+        ctx = mhd.Context(shape, info["h"])
+        cg, bg, cntg = gpu_step(ctx, cons, b, dt, mhd.scheme(recon, rs, emf), eta=1e-3)
+        assert_parity(cg, bg, co, bo, what=f"{recon}/{rs}/{emf}/{shape}")
+        assert cntg == cnt
+
+
 @pytest.mark.parametrize("shape", [(16, 1, 1), (1, 12, 3), (2, 5, 9), (130, 3, 2)])
 def test_degenerate_and_ragged_boxes(gpu_lib, shape):
     cons, b, info = inputs.random_smooth(shape, seed=5, rough=0.02)
