@@ -740,12 +740,15 @@ def test_fofc_without_flags_is_plain_rk2():
 # ---------------------------------------------------------------------------------------
 # Time step (Sec. 2.4) and the dual-number derivative
 # ---------------------------------------------------------------------------------------
-def test_flux_jvp_matches_fluxes_and_central_difference():
+@pytest.mark.parametrize("emf", ["q26", "fs18", "b25a"])
+def test_flux_jvp_matches_fluxes_and_central_difference(emf):
     """The dual-number directional derivative of the fluxes and EMFs returns the fluxes themselves
-    and agrees with a central difference on a smooth state."""
+    and agrees with a central difference on a smooth state, for each EMF compute scheme (the
+    reference the adjoint of each is checked against)."""
     shape = (6, 5, 4)
     cons, b, info = inputs.random_smooth(shape, seed=12, rough=0.0)
     cfg = cfg_for(shape, info, recon="ppm", riemann="hlld", eta=2e-3)
+    cfg.emf = emf
     rng = np.random.default_rng(3)
     dc, db = rng.normal(size=cons.shape) * 1e-2, rng.normal(size=b.shape) * 1e-2
     F, E, dF, dE = oracle.fluxes_jvp(cfg, cons, b, dc, db)
@@ -773,10 +776,14 @@ def test_max_dt_closed_form():
     assert oracle.max_dt(cfg, cons, b, 0.3) == pytest.approx(0.3 * h / (2.0 / h), rel=1e-15)
 
 
-def test_dual_number_derivative_matches_central_difference():
+@pytest.mark.parametrize("emf,recon", [("q26", "ppm"), ("fs18", "ppm"), ("b25a", "ppm"), ("b25a", "plm_mc")])
+def test_dual_number_derivative_matches_central_difference(emf, recon):
+    """Two steps' dual-number derivative (in the state and in eta) against a central difference of
+    the oracle's own steps with the same dts, for each EMF compute scheme."""
     shape = (6, 5, 4)
     cons, b, info = inputs.random_smooth(shape, seed=14, rough=0.01)
-    cfg = cfg_for(shape, info, recon="ppm", riemann="hlld", eta=1e-2)
+    cfg = cfg_for(shape, info, recon=recon, riemann="hlld", eta=1e-2)
+    cfg.emf = emf
     dts = [0.5 * oracle.max_dt(cfg, cons, b, 0.3)] * 2
     rng = np.random.default_rng(0)
     dcons = np.zeros_like(cons)
