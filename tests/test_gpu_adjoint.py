@@ -11,6 +11,7 @@ import torch
 
 import oracle
 from paper_2609_10816_gb300 import adjoint, inputs, mhd
+from tests.util import shock_state as _shock_state
 
 pytestmark = pytest.mark.gpu
 
@@ -47,23 +48,6 @@ def test_one_step_adjoint_identity(gpu_lib, recon, rs, emf, eta, shape):
     assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs((rc * vc).sum()) + abs((rb * vb).sum()) + 1e-300), (lhs, rhs)
     # the state is not modified by the adjoint
     assert np.array_equal(st.cons.cpu().numpy(), cons) and np.array_equal(st.b.cpu().numpy(), b)
-
-
-def _shock_state(shape, seed, amp, p0):
-    """A near-vacuum state under a strong expansion: the high-order step leaves cells invalid. The
-    pressure varies smoothly: on a uniform pressure its recomputed cell values differ only by
-    rounding, where the limiters' branches (and so their derivatives) follow rounding noise that
-    two correct implementations need not share."""
-    cons, b, info = inputs.random_smooth(shape, seed=seed, rough=0.0)
-    rng = np.random.default_rng(seed)
-    rho = cons[0]
-    u = [cons[1 + d] / rho for d in range(3)]
-    nx, ny, nz = shape
-    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
-                          indexing="ij")
-    u[0] = u[0] + amp * np.sin(2 * np.pi * x) + 0.1 * amp * rng.uniform(-1, 1, rho.shape)
-    p = p0 * (1.0 + 0.3 * np.sin(2 * np.pi * x + 1.3) * np.cos(2 * np.pi * y - 0.4) + 0.2 * np.sin(2 * np.pi * z + 0.7))
-    return inputs.assemble(rho, u, p, b), b, info
 
 
 # (shape, seed, velocity amplitude, pressure, CFL, reconstruction, EMF compute): a few cells

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_2609_10816_gb300 import inputs
-from tests.util import relerr_pert
+from tests.util import relerr_pert, shock_state
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 G = 5.0 / 3.0
@@ -759,6 +759,40 @@ def test_flux_jvp_matches_fluxes_and_central_difference(emf):
     Fm, Em = oracle.fluxes(cfg, cons - h * dc, b - h * db)
     assert np.abs((Fp - Fm) / (2 * h) - dF).max() <= 1e-6 * np.abs(dF).max()
     assert np.abs((Ep - Em) / (2 * h) - dE).max() <= 1e-6 * np.abs(dE).max()
+
+
+@pytest.mark.parametrize("seed,amp,p0,cfl,recon,emf", [(4, 3.0, 1e-3, 0.3, "ppm", "q26"),
+                                                      (4, 3.0, 1e-3, 0.3, "ppm", "fs18"),
+                                                      (4, 3.0, 1e-3, 0.3, "ppm", "b25a"),
+                                                      (3, 1.0, 1e-2, 0.6, "plm_mc", "b25a")])
+def test_dual_number_derivative_through_flux_correction(seed, amp, p0, cfl, recon, emf):
+    """A step in which flux correction (Sec. 2.5) replaces fluxes in both stages: the dual-number
+    derivative (the flagged cells held as the values give them) agrees with a central difference
+    of the oracle's own step, whose perturbed runs flag as many cells in each stage. The step is
+    1e-9: this near-vacuum state has limiter branch points within 1e-8..1e-5 of it, across which
+    a difference quotient is no derivative (at 1e-7 up to 1% of the derivatives' scale differ;
+    at 1e-9 none by more than 2e-7 of it)."""
+    shape = (10, 8, 6)
+    cons, b, info = shock_state(shape, seed, amp, p0)
+    cfg = cfg_for(shape, info, recon=recon, riemann="hlld", emf=emf)
+    dt = oracle.max_dt(cfg, cons, b, cfl)
+    _, _, cnt = oracle.step(cfg, cons, b, dt)
+    assert cnt[0] > 0 and cnt[1] > 0, cnt
+    rng = np.random.default_rng(5)
+    dcons = np.zeros_like(cons)
+    dcons[1:4] = rng.normal(size=cons[1:4].shape) * cons[0]
+    db = np.zeros_like(b)
+    _, _, tc, tb = oracle.steps_jvp(cfg, cons, b, dcons, db, 0.0, [dt])
+    eps = 1e-9
+    out = []
+    for s in (1, -1):
+        c, bb, cs = oracle.step(cfg, cons + s * eps * dcons, b, dt)
+        assert cs == cnt, (cs, cnt)
+        out.append((c, bb))
+    fd_c = (out[0][0] - out[1][0]) / (2 * eps)
+    fd_b = (out[0][1] - out[1][1]) / (2 * eps)
+    assert np.abs(tc - fd_c).max() <= 1e-5 * np.abs(fd_c).max()
+    assert np.abs(tb - fd_b).max() <= 1e-5 * np.abs(fd_b).max()
 
 
 def test_max_dt_closed_form():

@@ -1,6 +1,8 @@
 """Shared helpers for the tests (no method arithmetic)."""
 import numpy as np
 
+from paper_2609_10816_gb300 import inputs
+
 # Parity bars of the CUDA path against the oracle, per stored field and step:
 #   relative L1 sum|gpu - oracle| / max(sum|oracle|, N * scale) <= L1_TOL, and, element by element,
 #   max|gpu - oracle| / max(mean|oracle|, scale) <= MAX_TOL, so that one wrong cell cannot hide in
@@ -71,3 +73,20 @@ def relerr_pert(c0, b0, c1, b1, cbg, bbg):
         num += (np.abs(s0 - s1).mean() * n) ** 2
         den += (np.abs(s0 - sb).mean() * n) ** 2
     return (num / den) ** 0.5
+
+
+def shock_state(shape, seed, amp, p0):
+    """A near-vacuum state under a strong expansion: the high-order step leaves cells invalid. The
+    pressure varies smoothly: on a uniform pressure its recomputed cell values differ only by
+    rounding, where the limiters' branches (and so their derivatives) follow rounding noise that
+    two correct implementations need not share."""
+    cons, b, info = inputs.random_smooth(shape, seed=seed, rough=0.0)
+    rng = np.random.default_rng(seed)
+    rho = cons[0]
+    u = [cons[1 + d] / rho for d in range(3)]
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                          indexing="ij")
+    u[0] = u[0] + amp * np.sin(2 * np.pi * x) + 0.1 * amp * rng.uniform(-1, 1, rho.shape)
+    p = p0 * (1.0 + 0.3 * np.sin(2 * np.pi * x + 1.3) * np.cos(2 * np.pi * y - 0.4) + 0.2 * np.sin(2 * np.pi * z + 0.7))
+    return inputs.assemble(rho, u, p, b), b, info
