@@ -310,7 +310,7 @@ __device__ __forceinline__ void b25a_edge_vjp(const double* in, double lam, doub
   }
 }
 
-// ---- edges: adjoint of E_e from the 8 reconstructed edge values, the edge speeds, eta j ----
+// ---- edges: adjoint of E_e from the reconstructed edge values, the edge speeds, eta j ------
 template <int RC, int EMF>
 __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
   const Dev& D = A.D;
@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
     const long long Xc = shift(D, X, c, -1), Xa = shift(D, X, a, -1);
     // the reconstructed edge values as the forward edge sweeps formed them. Q26: b_a, u_a* bottom
     // and top (Epart), b_c, u_c* left and right (EdgeC). FS18: b_a bottom and top (Epart), b_c
-    // left and right, the a-then-c partials (Xpart) and the c-then-a ones (EdgeC).
+    // left and right, the a-then-c velocity partials (Xpart) and the c-then-a ones (EdgeC). B25a:
+    // the same with the partials of the cell EMF.
     constexpr int NI = EMF == EMF_FS18 ? 24 : (EMF == EMF_B25A ? 16 : 12);
     double in[NI];
     const double* pa = D.Epart + 4LL * e * N;
@@ -399,11 +400,12 @@ __global__ void __launch_bounds__(128) k_adj_edges(AdjDev A) {
   warp_add(etaacc, A.lEta);
 }
 
-// ---- edge reconstructions: adjoint of the face arrays b_d and u_d* ------------------------
+// ---- edge reconstructions: adjoint of the face arrays reconstructed to the edges -----------
 // Face array of direction d is reconstructed along t1 = d + 1 as the "a" array of e-edges with
-// e = d + 2 (bottom/top slots 0/1 for b, 2/3 for u*), and along t2 = d + 2 as the "c" array of
-// e-edges with e = d + 1 (left/right slots 4/5 for b, 6/7 for u*). Point m's lower value is the
-// top/right value at edge m; its upper value is the bottom/left value at edge m + t.
+// e = d + 2 (Q26: bottom/top slots 0/1 for b, 2/3 for u*), and along t2 = d + 2 as the "c" array
+// of e-edges with e = d + 1 (Q26: left/right slots 4/5 for b, 6/7 for u*; FS18 and B25a: the
+// slots of the lEdge layouts in mhd_internal.cuh). Point m's lower value is the top/right value
+// at edge m; its upper value is the bottom/left value at edge m + t.
 // FS18's velocity sources on the d-faces, as rows of the face states (LR): reconstructed along c of
 // the e-edges with d = a (u_a L, u_a R, u_c L, u_c R: the normal and the first tangential
 // component) and along a of the e-edges with d = c (u_a B, u_a T, u_c B, u_c T: the second
@@ -548,7 +550,8 @@ __device__ __forceinline__ RecSrc face_src(const AdjDev& A, int s, int v) {
 // edge values (k_adj_edge_rec): the arrays reconstructed along s, for the face arrays d = s - 1
 // (s is their "c" direction, e-edges e = s + 1: bottom / top values) and d = s + 1 (s is their "a"
 // direction, e-edges e = s + 2: left / right values). Q26: b_d and u_d^* of each (4 sources);
-// FS18: b_d and the four velocity states of each (10 sources).
+// FS18: b_d and the four velocity states of each (10 sources); B25a: b_d and the two face values
+// of the cell EMF of each (6 sources).
 template <int EMF>
 __device__ __forceinline__ RecSrc edge_src(const AdjDev& A, int s, int v) {
   const long long N = A.D.N;
@@ -1147,7 +1150,8 @@ void launch_adj_fo(const AdjDev& A, const unsigned char* fl1, const unsigned cha
 }
 
 // reverse sweeps of the PPM reconstructions along each direction (one launch per direction, so
-// that every output element has one writer per launch); kind FACE or edge values
+// that every output element has one writer per launch); KIND 0 the edge values, 1 the face states,
+// 2 B25a's cell EMF
 template <int KIND, int EMF = EMF_Q26>
 static void rec_sweeps(const AdjDev& A, cudaStream_t st) {
   const int nsrc = KIND == 1 ? 7 : (KIND == 2 ? 2 : (EMF == EMF_FS18 ? 10 : (EMF == EMF_B25A ? 6 : 4)));
